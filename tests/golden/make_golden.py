@@ -1,0 +1,60 @@
+"""Write the stored expected values under tests/golden/ from the CPU oracle.
+
+Only ``oracle`` (and the seeded generator ``synth``) are called: no value
+here comes from the CUDA path.  Run from the repository root:
+
+    python tests/golden/make_golden.py
+"""
+
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import exact_response, polarizability, tc2_response  # noqa: E402
+from synth import make_chain, make_config  # noqa: E402
+
+
+def chain_case(n_atoms, opa, b, spacing, cutoff, seed, dirs):
+    s = make_chain(n_atoms, opa=opa, b=b, spacing=spacing, cutoff=cutoff, seed=seed, dirs=dirs)
+    h0 = s.h0.to_dense()
+    h1s = [m.to_dense() for m in s.h1]
+    _, p1s, eps, _ = exact_response(h0, h1s, s.n_occ)
+    a = polarizability(p1s, h1s)
+    r = tc2_response(h0, h1s, s.n_occ, b, tau=0.0, tol=1e-12)
+    return {"kind": "chain", "n_atoms": n_atoms, "opa": opa, "b": b, "spacing": spacing,
+            "cutoff": cutoff, "seed": seed, "dirs": list(dirs), "n_occ": s.n_occ,
+            "gap": float(eps[s.n_occ] - eps[s.n_occ - 1]), "alpha": a.tolist(),
+            "tc2_iterations_tau0": r.iterations, "tc2_branches_tau0": r.branches}
+
+
+def main():
+    cases = [
+        # workload 1 (64-atom chain, 4 orbitals, b = 4, x-dipole)
+        chain_case(64, 4, 4, 2.8, 8.0, 0, ("x",)),
+        chain_case(24, 4, 4, 2.8, 8.0, 0, ("x", "y", "z")),
+    ]
+    s = make_config(2, n_atoms=100)
+    h0 = s.h0.to_dense()
+    h1s = [m.to_dense() for m in s.h1]
+    _, p1s, eps, _ = exact_response(h0, h1s, s.n_occ)
+    cases.append({"kind": "cluster-cfg2-generator", "n_atoms": 100, "b": 32,
+                  "n_occ": s.n_occ, "gap": float(eps[s.n_occ] - eps[s.n_occ - 1]),
+                  "alpha": polarizability(p1s, h1s).tolist()})
+    out = {
+        "source": "oracle.dense.exact_response + oracle.dense.polarizability (CPU FP64), "
+                  "oracle.tc2.tc2_response for the iteration counts",
+        "paper": "Sec. 2.2 reports about 25 recursion cycles to a band-energy change of 1e-10 a.u.",
+        "cases": cases,
+    }
+    with open(os.path.join(HERE, "alpha_small.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("wrote", os.path.join(HERE, "alpha_small.json"))
+
+
+if __name__ == "__main__":
+    main()
