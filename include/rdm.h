@@ -1,0 +1,234 @@
+/*
+ * rdm.h - C ABI of the GB300 response-density-matrix library.
+ *
+ * The library computes, for a gapped Hamiltonian H0 and first-order
+ * perturbations H1_gamma given in an orthogonal basis (the orthogonal form of
+ * Sec. 2.2 of Shang, Liang, Zhang, Yang, "Efficient Parallel Linear Scaling
+ * Method to get the Response Density Matrix in All-Electron Real-Space DFPT"):
+ *
+ *   P0       = lim X0_n     (TC2 purification, Eq. TC2)
+ *   P1_gamma = lim X1_n     (first-order recursion, Eq. TC2-CPSCF)
+ *   alpha    = polarizability tensor (Eq. polar, field term -r.E)
+ *
+ * starting from X0_0 = (eps_max I - H0)/(eps_max - eps_min) and
+ * X1_0 = -H1/(eps_max - eps_min) with Gershgorin bounds eps_min, eps_max
+ * (Sec. 2.2).  Every product is a block-sparse (BSR) product followed by
+ * block-norm truncation (the "filter" of Sec. 2.3); the loop stops on the
+ * band-energy change (the "tolerance" of Sec. 2.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an int status: RDM_OK (0) on success, a positive
+ *   warning (results readable), or a negative error.  No C++ exception and no
+ *   abort crosses this boundary.  rdm_last_error() gives a message for the
+ *   last failing call on that handle.
+ * - Units: Hartree and bohr; alpha in bohr^3.  Matrices are real symmetric.
+ * - BSR layout (struct rdm_bsr): nb block rows of b x b blocks; row_ptr has
+ *   nb+1 int32 entries (row_ptr[0] = 0); col_idx has nnzb int32 entries,
+ *   strictly increasing inside each block row; vals holds nnzb blocks of
+ *   b*b doubles, each block row-major.  n <= nb*b is the number of
+ *   meaningful orbitals; rows and columns n..nb*b-1 are padding and must be
+ *   zero.  The block pattern must be symmetric and every diagonal block of
+ *   H0 must be present.
+ * - Ownership: the caller owns every buffer it passes.  Uploads copy the
+ *   data (in the order of the handle's stream); caller buffers may be reused
+ *   once the call has returned (host buffers) or once the handle's stream has
+ *   been synchronised (device buffers).  Getters write into caller-allocated
+ *   host buffers and return after the copy has completed.
+ * - A handle is bound to one CUDA device and one stream, and must not be
+ *   used from two threads at once.
+ */
+#ifndef RDM_H_
+#define RDM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define RDM_OK               0
+#define RDM_NOT_CONVERGED    1   /* warning: max_iter reached; results readable */
+#define RDM_EINVAL          -1   /* bad argument (null pointer, range, call order) */
+#define RDM_EBADBSR         -2   /* malformed matrix: pattern, symmetry, non-finite values */
+#define RDM_ENOMEM          -3   /* device allocation failed */
+#define RDM_ECUDA           -4   /* CUDA runtime error */
+#define RDM_ECAPACITY       -5   /* a work pool overflowed and could not be grown */
+#define RDM_ETIMEOUT        -6   /* a bounded device wait expired */
+#define RDM_ESTATE          -7   /* call made in the wrong state (e.g. getter before solve) */
+
+/* ---- precision modes (rdm_params.mode) ------------------------------- */
+#define RDM_MODE_FP64        0   /* every product in FP64 (CUDA cores) */
+#define RDM_MODE_FP32        1   /* every product in FP32 (CUDA cores), FP64 scalars */
+#define RDM_MODE_MIXED_BF16  2   /* bf16 hi+lo split products on the tensor cores
+                                    (tcgen05, FP32 accumulate), then FP64 refinement */
+#define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands */
+#define RDM_MODE_TF32        4   /* single-pass TF32 tensor-core products (FP32 accumulate) */
+
+typedef struct rdm_handle rdm_handle;
+
+/* Input matrix (H0 or one H1_gamma).  on_device = 1: the three arrays are
+ * device pointers on the handle's device; 0: host pointers. */
+typedef struct {
+    int32_t nb;             /* block rows (= block columns) */
+    int32_t b;              /* block size, 1..64 */
+    int32_t n;              /* meaningful orbitals, (nb-1)*b < n <= nb*b */
+    int32_t on_device;
+    int64_t nnzb;           /* stored blocks */
+    const int32_t *row_ptr; /* nb+1 */
+    const int32_t *col_idx; /* nnzb */
+    const double  *vals;    /* nnzb*b*b, row-major blocks */
+} rdm_bsr;
+
+/* Output matrix: caller-allocated HOST arrays of the sizes returned by the
+ * matching *_nnzb getter. */
+typedef struct {
+    int32_t nb, b, n;
+    int64_t nnzb;           /* in: capacity in blocks; out: blocks written */
+    int32_t *row_ptr;       /* nb+1 */
+    int32_t *col_idx;       /* nnzb */
+    double  *vals;          /* nnzb*b*b */
+} rdm_bsr_out;
+
+typedef struct {
+    double  tau;            /* block-norm truncation threshold for X0 (filter), >= 0 */
+    double  tau_x1;         /* the same for X1; < 0 means "use tau" */
+    double  tau_refine;     /* threshold in the final (FP64) tier of the mixed modes; < 0: tau */
+    double  tol;            /* band-energy change stop (Hartree); 0 disables it */
+    double  stall_tol;      /* idempotency-stall stop level (0 disables; mixed modes set their own) */
+    double  spin_factor;    /* 2.0 for closed shells; enters alpha only */
+    int32_t max_iter;       /* iteration cap; reaching it returns RDM_NOT_CONVERGED */
+    int32_t mode;           /* RDM_MODE_* */
+    int32_t min_iter;       /* never stop before this many iterations */
+    int32_t use_graphs;     /* 1: capture the iteration in CUDA graphs when possible */
+    int32_t verbose;        /* 1: per-iteration log to stderr */
+    int32_t reserved[5];
+} rdm_params;
+
+/* Per-solve summary (per system s of a batch: rdm_get_info). */
+typedef struct {
+    int32_t iterations;
+    int32_t converged;
+    int32_t tier_iters[4];  /* iterations spent per precision tier (mixed modes) */
+    double  eps_min, eps_max;
+    double  trace_error;    /* Tr P0 - N_occ */
+    double  idempotency;    /* Tr P0 - ||P0||_F^2 */
+    double  band_energy0;   /* Tr(P0 H0) */
+    int64_t nnzb_p0;
+    int64_t nnzb_p1[3];
+    double  time_ms;        /* wall time of the solve on the handle's stream */
+    double  useful_flops;   /* 2 b^3 per (i,k,j) block triple, summed over the solve */
+    double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
+} rdm_info;
+
+/* One record per iteration (rdm_get_log). */
+typedef struct {
+    int32_t iter, branch, tier, sys;
+    double  trace;          /* Tr X0_n */
+    double  idempotency;    /* Tr X0_n - ||X0_n||_F^2 */
+    double  eb0;            /* Tr(X0_{n+1} H0) */
+    double  eb1[3];         /* Tr(X1_{n+1,gamma} H0) */
+    int64_t nnzb0, nnzb1[3];
+    double  ms;             /* device time of the iteration */
+} rdm_iter_log;
+
+/* ---- lifetime ---------------------------------------------------------- */
+
+/* Create a handle on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle (NULL on failure). */
+int rdm_create(rdm_handle **out, int device, void *cuda_stream);
+
+/* Free every device buffer of the handle (after synchronising its stream). */
+int rdm_destroy(rdm_handle *h);
+
+/* Message of the last failing call on h (never NULL; valid until the next
+ * call on h).  h may be NULL for creation errors. */
+const char *rdm_last_error(const rdm_handle *h);
+
+/* Fill *p with the defaults: tau 1e-6, tau_x1/tau_refine -1, tol 1e-9,
+ * stall_tol 0, spin 2, max_iter 100, mode FP64, min_iter 1, graphs 0. */
+int rdm_default_params(rdm_params *p);
+
+/* Set the solve parameters (validated: tau >= 0, max_iter >= 1, known mode). */
+int rdm_set_params(rdm_handle *h, const rdm_params *p);
+
+/* ---- problem definition ------------------------------------------------ */
+
+/* Declare a batch of n_systems independent systems (default 1).  Clears any
+ * uploaded matrices.  All systems of a batch share the block size b. */
+int rdm_batch_create(rdm_handle *h, int n_systems);
+
+/* Upload H0 of system `sys` with its electron count (even, 0 < N_e/2 < n).
+ * Validates the pattern (sorted, unique, in range, symmetric, diagonal
+ * present) and the values (finite, symmetric to 1e-12 max|H|, padding zero)
+ * and returns RDM_EBADBSR with a message if any check fails. */
+int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons);
+
+/* Upload H1 for direction dir (0 = x, 1 = y, 2 = z) of system sys: the
+ * matrix dH/dlambda (for a field this is the dipole matrix D_dir; the field
+ * term -r.E enters through the sign convention of alpha).  Same checks as
+ * H0 (the diagonal need not be present); same nb, b, n as H0. */
+int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1);
+
+/* ---- solve -------------------------------------------------------------- */
+
+/* Run the coupled TC2 / first-order recursion for every uploaded system and
+ * direction, then the polarizability.  Blocks until done.  *info (may be
+ * NULL) receives the summary of system 0.  Returns RDM_OK, the warning
+ * RDM_NOT_CONVERGED, or an error (RDM_ECAPACITY, RDM_ECUDA, RDM_ENOMEM,
+ * RDM_ETIMEOUT). */
+int rdm_solve(rdm_handle *h, rdm_info *info);
+
+/* Test hook: force the branch of iteration n to seq[n] (1 = X^2,
+ * 2 = 2X - X^2) for n < len; len = 0 clears it.  Applies to every system. */
+int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len);
+
+/* ---- results ------------------------------------------------------------ */
+
+int rdm_get_info(rdm_handle *h, int sys, rdm_info *info);
+
+/* Number of stored blocks of P0 (resp. P1_dir) of system sys. */
+int rdm_get_p0_nnzb(rdm_handle *h, int sys, int64_t *nnzb);
+int rdm_get_p1_nnzb(rdm_handle *h, int sys, int dir, int64_t *nnzb);
+
+/* Copy P0 (resp. P1_dir) into caller host buffers (out->nnzb = capacity on
+ * entry).  With out->row_ptr == NULL the call is a size query: it fills
+ * out->nb, b, n, nnzb and returns RDM_OK.  Block order and indices are the
+ * caller's: the library does not permute.  Padding rows/columns come back as
+ * zeros. */
+int rdm_get_p0(rdm_handle *h, int sys, rdm_bsr_out *out);
+int rdm_get_p1(rdm_handle *h, int sys, int dir, rdm_bsr_out *out);
+
+/* alpha[3*g + d] = -spin * Tr(P1_d H1_g) (Eq. polar with field term -r.E);
+ * entries of directions that were not uploaded are NaN. */
+int rdm_get_alpha(rdm_handle *h, int sys, double alpha[9]);
+
+/* Copy up to cap per-iteration records of the last solve; *n gets the count. */
+int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n);
+
+/* ---- single-product primitive (kernel-level testing and benchmarking) ---- */
+
+/* One truncated block-sparse product on the handle's device:
+ *   C = c_lin * X + c_sq * (A B)          (terms = 1)
+ *   C = c_lin * X + c_sq * (A B + B A)    (terms = 2; requires symmetric A, B)
+ * followed by dropping every block whose Frobenius norm is below tau — the
+ * update step of Eqs. TC2 / TC2-CPSCF for one matrix.  A, B, X are symmetric
+ * host BSR matrices with the same nb, b, n (X may be NULL: no linear term).
+ * `mode` selects the product arithmetic (RDM_MODE_*; the mixed modes use the
+ * hi+lo split tensor-core product).  The result goes to *out as for
+ * rdm_get_p0; call with out->nnzb = 0 / NULL arrays to query the size only
+ * (*needed receives the block count). */
+int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const rdm_bsr *X,
+                      double c_lin, double c_sq, int terms, double tau, int mode,
+                      rdm_bsr_out *out, int64_t *needed);
+
+/* Library version string. */
+const char *rdm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDM_H_ */

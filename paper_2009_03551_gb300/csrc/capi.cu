@@ -1,0 +1,1109 @@
+// C ABI (include/rdm.h) and the host-side driver of the solve.
+//
+// The driver follows Sec. 2.2 of the paper: Gershgorin bounds, the initial
+// matrices, then per iteration the trace test of Eq. TC2 choosing between
+// X0 <- X0^2, X1 <- X1 X0 + X0 X1 and X0 <- 2X0 - X0^2,
+// X1 <- 2X1 - X1 X0 - X0 X1 (Eq. TC2-CPSCF), each product followed by
+// block-norm truncation (Sec. 2.3 "filter"), until the band energies
+// Tr(X0 H0), Tr(X1 H0) stop changing (Sec. 2.3 "tolerance").  Finally the
+// polarizability alpha_{gd} = -spin Tr(P1_d H1_g) (Eq. polar, field term
+// -r.E).  Every arithmetic step runs in the kernels of k_*.cu; the host only
+// makes the per-system scalar decisions and sizes the buffers.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/rdm.h"
+#include "rdm_internal.cuh"
+#include "tc_gemm.cuh"
+
+using namespace rdm;
+
+namespace {
+
+struct HostSys {
+    bool has_h0 = false;
+    int nb = 0, n = 0;
+    int64_t n_elec = 0;
+    std::vector<int> rp, col;          // host copies of the pattern
+    DevBuf<double> val;                // device copy of the values
+    bool has_h1[3] = {false, false, false};
+    std::vector<int> rp1[3], col1[3];
+    DevBuf<double> val1[3];
+};
+
+struct SysState {
+    int iters = 0;
+    int tier = 0;
+    int tier_start = 0;
+    int prev_branch = 0;
+    bool active = true;
+    bool converged = false;
+    std::vector<double> e_hist;
+    bool have_eb = false;
+    double eb0 = 0, eb1[3] = {0, 0, 0};
+    int tier_iters[4] = {0, 0, 0, 0};
+};
+
+}  // namespace
+
+struct rdm_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    rdm_params prm;
+    int S = 1;
+    int b = 0;
+    std::vector<HostSys> hs;
+    std::vector<uint8_t> forced;
+
+    // assembled inputs
+    int NB = 0;
+    int nd = 0;
+    int dirs[3] = {0, 0, 0};
+    std::vector<int> row0, nbs, norb;
+    MatSet H0, H1;
+    SysDev sd;
+    MatSet X[2];
+    int cur = 0;
+
+    // work buffers
+    DevBuf<int> row_cnt, row_off, pool_col, pool_npair, counters, mask_col;
+    DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work;
+    DevBuf<int64_t> pair_off, scan_tmp64;
+    DevBuf<int> scan_tmp32, pair_a, pair_b, cnt_rows;
+    DevBuf<double> out_val, row_part, sys_q;
+    DevBuf<float> out_nrm;
+    DevBuf<uint8_t> keep;
+    DevBuf<double> row_lo, row_hi;
+    TcWork tcw;
+
+    // results
+    bool solved = false;
+    std::vector<rdm_info> info;
+    std::vector<rdm_iter_log> log;
+    std::vector<double> alpha;
+    std::vector<int> final_rp;     // host copy of X row_ptr after the solve
+    int64_t pool_cap_hint = 0;
+};
+
+namespace {
+
+int fail(rdm_handle *h, int code, const std::string &m) {
+    if (h) h->err = m;
+    return code;
+}
+
+template <class F>
+int guarded(rdm_handle *h, F &&f) {
+    try {
+        return f();
+    } catch (const Error &e) {
+        return fail(h, e.code, e.msg);
+    } catch (const std::bad_alloc &) {
+        return fail(h, RDM_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(h, RDM_EINVAL, e.what());
+    } catch (...) {
+        return fail(h, RDM_EINVAL, "unknown error");
+    }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) RDM_CUDA_TRY(cudaSetDevice(d));
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+void sync(rdm_handle *h) { RDM_CUDA_TRY(cudaStreamSynchronize(h->stream)); }
+
+template <class T>
+void h2d(T *dst, const T *src, size_t n, cudaStream_t st) {
+    if (n) RDM_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+template <class T>
+void d2h(T *dst, const T *src, size_t n, cudaStream_t st) {
+    if (n) RDM_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+}
+
+// ---------------------------------------------------------------------------
+// upload and validation
+// ---------------------------------------------------------------------------
+
+void check_pattern(const rdm_bsr *A, const std::vector<int> &rp, const std::vector<int> &col,
+                   bool need_diag) {
+    const int nb = A->nb;
+    if (rp[0] != 0 || rp[nb] != A->nnzb)
+        throw Error{RDM_EBADBSR, "row_ptr[0] must be 0 and row_ptr[nb] must equal nnzb"};
+    for (int i = 0; i < nb; ++i) {
+        if (rp[i + 1] < rp[i]) throw Error{RDM_EBADBSR, "row_ptr is not non-decreasing"};
+        bool diag = false;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            if (col[p] < 0 || col[p] >= nb)
+                throw Error{RDM_EBADBSR, "column index out of range in block row " + std::to_string(i)};
+            if (p > rp[i] && col[p] <= col[p - 1])
+                throw Error{RDM_EBADBSR, "columns not strictly increasing in block row " + std::to_string(i)};
+            if (col[p] == i) diag = true;
+        }
+        if (need_diag && !diag)
+            throw Error{RDM_EBADBSR, "diagonal block missing in block row " + std::to_string(i)};
+    }
+    // symmetric pattern: every (i,j) has (j,i)
+    for (int i = 0; i < nb; ++i)
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            int j = col[p];
+            if (!std::binary_search(col.begin() + rp[j], col.begin() + rp[j + 1], i))
+                throw Error{RDM_EBADBSR, "block pattern is not symmetric"};
+        }
+}
+
+void upload_matrix(rdm_handle *h, const rdm_bsr *A, std::vector<int> &rp, std::vector<int> &col,
+                   DevBuf<double> &val, bool need_diag) {
+    if (!A || !A->row_ptr || (A->nnzb > 0 && (!A->col_idx || !A->vals)))
+        throw Error{RDM_EINVAL, "null matrix pointer"};
+    if (A->nb <= 0 || A->b <= 0 || A->b > 64 || (A->b & (A->b - 1)))
+        throw Error{RDM_EINVAL, "nb must be > 0 and b a power of two <= 64"};
+    if (A->n <= (int64_t)(A->nb - 1) * A->b || A->n > (int64_t)A->nb * A->b)
+        throw Error{RDM_EINVAL, "n must satisfy (nb-1)*b < n <= nb*b"};
+    if (A->nnzb < 0 || A->nnzb > (int64_t)A->nb * A->nb)
+        throw Error{RDM_EINVAL, "nnzb out of range"};
+    if (h->b && h->b != A->b) throw Error{RDM_EINVAL, "all systems of a batch share the block size"};
+    const int nb = A->nb;
+    const size_t bb = (size_t)A->b * A->b;
+    rp.resize(nb + 1);
+    col.resize(A->nnzb);
+    cudaMemcpyKind k = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    RDM_CUDA_TRY(cudaMemcpy(rp.data(), A->row_ptr, (nb + 1) * sizeof(int), k));
+    if (A->nnzb) RDM_CUDA_TRY(cudaMemcpy(col.data(), A->col_idx, A->nnzb * sizeof(int), k));
+    check_pattern(A, rp, col, need_diag);
+    val.ensure(A->nnzb * bb);
+    if (A->nnzb)
+        RDM_CUDA_TRY(cudaMemcpyAsync(val.p, A->vals, A->nnzb * bb * sizeof(double),
+                                     A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     h->stream));
+    // value checks on the device: finite, symmetric (1e-12 max|H|), zero padding
+    DevBuf<int> drp, dcol, derr, dsys, dz;
+    drp.ensure(nb + 1);
+    dcol.ensure(std::max<int64_t>(1, A->nnzb));
+    derr.ensure(4);
+    dsys.ensure(nb);
+    dz.ensure(2);
+    h2d(drp.p, rp.data(), nb + 1, h->stream);
+    h2d(dcol.p, col.data(), A->nnzb, h->stream);
+    RDM_CUDA_TRY(cudaMemsetAsync(derr.p, 0, 4 * sizeof(int), h->stream));
+    RDM_CUDA_TRY(cudaMemsetAsync(dsys.p, 0, nb * sizeof(int), h->stream));
+    int zn[2] = {0, A->n};
+    h2d(dz.p, zn, 2, h->stream);
+    launch_check_values(drp.p, dcol.p, val.p, A->nnzb * (int64_t)bb, nb, A->b, dsys.p, dz.p,
+                        dz.p + 1, 1e-12, derr.p, h->stream);
+    int herr[4];
+    d2h(herr, derr.p, 4, h->stream);
+    sync(h);
+    drp.release(); dcol.release(); derr.release(); dsys.release(); dz.release();
+    if (herr[0] & 1) throw Error{RDM_EBADBSR, "matrix has non-finite values"};
+    if (herr[0] & 8) throw Error{RDM_EBADBSR, "block pattern is not symmetric"};
+    if (herr[0] & 2) throw Error{RDM_EBADBSR, "matrix values are not symmetric (tolerance 1e-12 max|H|)"};
+    if (herr[0] & 4) throw Error{RDM_EBADBSR, "padding rows/columns (index >= n) must be zero"};
+    h->b = A->b;
+}
+
+// ---------------------------------------------------------------------------
+// assembly of the batch into global block-diagonal sets
+// ---------------------------------------------------------------------------
+
+void assemble(rdm_handle *h) {
+    const int S = h->S;
+    h->row0.assign(S, 0);
+    h->nbs.assign(S, 0);
+    h->norb.assign(S, 0);
+    int NB = 0;
+    for (int s = 0; s < S; ++s) {
+        if (!h->hs[s].has_h0) throw Error{RDM_ESTATE, "H0 of system " + std::to_string(s) + " not uploaded"};
+        h->row0[s] = NB;
+        h->nbs[s] = h->hs[s].nb;
+        h->norb[s] = h->hs[s].n;
+        if (h->hs[s].nb > kSymMaxNs)
+            throw Error{RDM_EINVAL, "systems above " + std::to_string(kSymMaxNs) + " block rows are not supported"};
+        NB += h->hs[s].nb;
+    }
+    h->NB = NB;
+    // directions: the set uploaded for system 0; every system must match
+    int nd = 0;
+    for (int d = 0; d < 3; ++d)
+        if (h->hs[0].has_h1[d]) h->dirs[nd++] = d;
+    for (int s = 1; s < S; ++s)
+        for (int d = 0; d < 3; ++d)
+            if (h->hs[s].has_h1[d] != h->hs[0].has_h1[d])
+                throw Error{RDM_EINVAL, "every system of a batch needs the same H1 directions"};
+    h->nd = nd;
+    const int b = h->b;
+    const size_t bb = (size_t)b * b;
+
+    auto build = [&](MatSet &M, int nmat, auto get_rp, auto get_col, auto get_val) {
+        M.nmat = nmat;
+        M.NB = NB;
+        M.b = b;
+        std::vector<int> rp((size_t)nmat * NB + 1);
+        std::vector<int> col;
+        M.nnzb.assign(nmat, 0);
+        int64_t top = 0;
+        for (int m = 0; m < nmat; ++m)
+            for (int s = 0; s < S; ++s) {
+                const std::vector<int> &r = get_rp(s, m);
+                const std::vector<int> &c = get_col(s, m);
+                for (int i = 0; i < h->nbs[s]; ++i) {
+                    rp[(size_t)m * NB + h->row0[s] + i] = (int)(top + r[i]);
+                }
+                for (int p = 0; p < (int)c.size(); ++p) col.push_back(c[p] + h->row0[s]);
+                top += r[h->nbs[s]];
+                M.nnzb[m] += r[h->nbs[s]];
+            }
+        rp[(size_t)nmat * NB] = (int)top;
+        if (top > INT32_MAX / 2) throw Error{RDM_EINVAL, "too many blocks"};
+        M.total = top;
+        M.row_ptr.ensure(rp.size());
+        M.col.ensure(std::max<int64_t>(top, 1));
+        M.val.ensure(std::max<int64_t>(top, 1) * bb);
+        M.nrm.ensure(std::max<int64_t>(top, 1));
+        h2d(M.row_ptr.p, rp.data(), rp.size(), h->stream);
+        h2d(M.col.p, col.data(), col.size(), h->stream);
+        int64_t off = 0;
+        for (int m = 0; m < nmat; ++m)
+            for (int s = 0; s < S; ++s) {
+                int64_t n = get_rp(s, m)[h->nbs[s]];
+                if (n)
+                    RDM_CUDA_TRY(cudaMemcpyAsync(M.val.p + off * bb, get_val(s, m), n * bb * sizeof(double),
+                                                 cudaMemcpyDeviceToDevice, h->stream));
+                off += n;
+            }
+    };
+    build(h->H0, 1, [&](int s, int) -> const std::vector<int> & { return h->hs[s].rp; },
+          [&](int s, int) -> const std::vector<int> & { return h->hs[s].col; },
+          [&](int s, int) { return (const double *)h->hs[s].val.p; });
+    if (nd) {
+        build(h->H1, nd, [&](int s, int m) -> const std::vector<int> & { return h->hs[s].rp1[h->dirs[m]]; },
+              [&](int s, int m) -> const std::vector<int> & { return h->hs[s].col1[h->dirs[m]]; },
+              [&](int s, int m) { return (const double *)h->hs[s].val1[h->dirs[m]].p; });
+    }
+    // X0 has the pattern of H0, X1_g that of H1_g
+    MatSet &X = h->X[0];
+    h->cur = 0;
+    X.nmat = 1 + nd;
+    X.NB = NB;
+    X.b = b;
+    int64_t tot = h->H0.total + (nd ? h->H1.total : 0);
+    X.total = tot;
+    X.nnzb.assign(1 + nd, 0);
+    X.nnzb[0] = h->H0.nnzb[0];
+    for (int m = 0; m < nd; ++m) X.nnzb[1 + m] = h->H1.nnzb[m];
+    X.row_ptr.ensure((size_t)(1 + nd) * NB + 1);
+    X.col.ensure(std::max<int64_t>(tot, 1));
+    X.val.ensure(std::max<int64_t>(tot, 1) * bb);
+    X.nrm.ensure(std::max<int64_t>(tot, 1));
+    {
+        // row_ptr of X: H0 rows, then H1 rows shifted by nnzb(H0)
+        std::vector<int> rp((size_t)(1 + nd) * NB + 1);
+        std::vector<int> tmp((size_t)NB + 1);
+        d2h(rp.data(), h->H0.row_ptr.p, (size_t)NB, h->stream);
+        if (nd) {
+            std::vector<int> r1((size_t)nd * NB + 1);
+            d2h(r1.data(), h->H1.row_ptr.p, r1.size(), h->stream);
+            sync(h);
+            for (size_t t = 0; t < r1.size(); ++t) rp[NB + t] = r1[t] + (int)h->H0.total;
+        } else {
+            sync(h);
+            rp[NB] = (int)h->H0.total;
+        }
+        h2d(X.row_ptr.p, rp.data(), rp.size(), h->stream);
+    }
+    RDM_CUDA_TRY(cudaMemcpyAsync(X.col.p, h->H0.col.p, h->H0.total * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    if (nd)
+        RDM_CUDA_TRY(cudaMemcpyAsync(X.col.p + h->H0.total, h->H1.col.p, h->H1.total * sizeof(int),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    // per-system device scalars
+    SysDev &sd = h->sd;
+    sd.row0.ensure(S); sd.nbs.ensure(S); sd.n_orb.ensure(S);
+    sd.emin.ensure(S); sd.emax.ensure(S); sd.c_lin.ensure(S); sd.c_sq.ensure(S);
+    sd.tau0.ensure(S); sd.tau1.ensure(S); sd.active.ensure(S); sd.tier.ensure(S);
+    sd.sys_of_row.ensure(NB);
+    std::vector<int> sor(NB);
+    for (int s = 0; s < S; ++s)
+        for (int i = 0; i < h->nbs[s]; ++i) sor[h->row0[s] + i] = s;
+    h2d(sd.row0.p, h->row0.data(), S, h->stream);
+    h2d(sd.nbs.p, h->nbs.data(), S, h->stream);
+    h2d(sd.n_orb.p, h->norb.data(), S, h->stream);
+    h2d(sd.sys_of_row.p, sor.data(), NB, h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// one multiplication step: symbolic, pairs, numeric, truncation, compaction
+// ---------------------------------------------------------------------------
+
+struct StepStats {
+    int64_t npairs = 0;
+    int64_t nslot = 0;
+    double issued = 0;
+};
+
+Arith tier_arith(int mode, int tier) {
+    switch (mode) {
+        case RDM_MODE_FP64: return AR_FP64;
+        case RDM_MODE_FP32: return AR_FP32;
+        case RDM_MODE_MIXED_BF16: return tier == 0 ? AR_BF16X3 : AR_FP64;
+        case RDM_MODE_MIXED_FP16: return tier == 0 ? AR_FP16X3 : AR_FP64;
+        case RDM_MODE_TF32: return AR_TF32;
+    }
+    return AR_FP64;
+}
+
+StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, Arith ar) {
+    cudaStream_t st = h->stream;
+    const int NB = in.NB, b = in.b, njob = jt.njob;
+    const size_t bb = (size_t)b * b;
+    const int nrows = njob * NB;
+    int max_ns = *std::max_element(h->nbs.begin(), h->nbs.end());
+    StepStats ss;
+    if (ar != AR_FP64 && ar != AR_FP32) prepare_operands(in, ar, st);
+
+    h->row_cnt.ensure(nrows);
+    h->row_off.ensure(nrows);
+    h->counters.ensure(8);
+    int64_t cap = std::max<int64_t>(h->pool_cap_hint, 4 * in.total + 1024);
+    int top = 0;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if (cap > INT32_MAX / 2) throw Error{RDM_ECAPACITY, "symbolic pool exceeds 2^30 blocks"};
+        h->pool_col.ensure(cap);
+        h->pool_npair.ensure(cap);
+        RDM_CUDA_TRY(cudaMemsetAsync(h->counters.p, 0, 8 * sizeof(int), st));
+        SymOut so{h->row_cnt.p, h->row_off.p, h->pool_col.p, h->pool_npair.p, h->counters.p,
+                  (int)h->pool_col.cap, h->counters.p + 1};
+        launch_symbolic(in, jt, h->sd, h->S, so, st, max_ns);
+        int hc[2];
+        d2h(hc, h->counters.p, 2, st);
+        sync(h);
+        top = hc[0];
+        if (!hc[1]) break;
+        cap = (int64_t)top + top / 4 + 1024;
+        if (attempt == 3) throw Error{RDM_ECAPACITY, "symbolic pool overflow after retries"};
+    }
+    h->pool_cap_hint = std::max<int64_t>(h->pool_cap_hint, top);
+
+    // output pattern
+    h->out_rp.ensure(nrows + 1);
+    h->scan_tmp32.ensure(scan_tmp_elems(nrows + 1));
+    scan_exclusive_i32(h->row_cnt.p, h->out_rp.p, nrows, h->scan_tmp32.p, st);
+    const int64_t nslot = top;
+    ss.nslot = nslot;
+    out.nmat = njob;
+    out.NB = NB;
+    out.b = b;
+    int *mcol = h->mask_col.ensure(std::max<int64_t>(nslot, 1));
+    h->slot_row.ensure(std::max<int64_t>(nslot, 1));
+    h->slot_job.ensure(std::max<int64_t>(nslot, 1));
+    h->slot_npair.ensure(std::max<int64_t>(nslot, 1));
+    SymOut so{h->row_cnt.p, h->row_off.p, h->pool_col.p, h->pool_npair.p, h->counters.p,
+              (int)h->pool_col.cap, h->counters.p + 1};
+    launch_gather(so, njob, NB, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p,
+                  h->slot_npair.p, st);
+    h->pair_off.ensure(nslot + 1);
+    h->scan_tmp64.ensure(scan_tmp_elems((int)nslot + 1));
+    scan_exclusive_i64(h->slot_npair.p, h->pair_off.p, (int)nslot, h->scan_tmp64.p, st);
+    int64_t npairs = 0;
+    d2h(&npairs, h->pair_off.p + nslot, 1, st);
+    sync(h);
+    ss.npairs = npairs;
+    h->pair_a.ensure(std::max<int64_t>(npairs, 1));
+    h->pair_b.ensure(std::max<int64_t>(npairs, 1));
+    h->slot_x.ensure(std::max<int64_t>(nslot, 1));
+    h->slot_t.ensure(std::max<int64_t>(nslot, 1));
+    launch_pairs(in, jt, h->sd, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p, h->pair_off.p,
+                 nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st);
+    h->work.ensure(std::max<int64_t>(nslot, 1));
+    launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st);
+    int hc[2];
+    d2h(hc, h->counters.p + 2, 2, st);
+    sync(h);
+    if (hc[0]) throw Error{RDM_ECUDA, "internal error: pair lists inconsistent with the mask (code " + std::to_string(hc[0]) + ")"};
+    const int nwork = hc[1];
+
+    // numeric + fused truncation
+    h->out_val.ensure(std::max<int64_t>(nslot, 1) * bb);
+    h->out_nrm.ensure(std::max<int64_t>(nslot, 1));
+    h->keep.ensure(std::max<int64_t>(nslot, 1));
+    NumArgs a{};
+    a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
+    a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
+    a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
+    a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
+    a.c_lin = h->sd.c_lin.p; a.c_sq = h->sd.c_sq.p; a.tau0 = h->sd.tau0.p; a.tau1 = h->sd.tau1.p;
+    a.active = h->sd.active.p;
+    for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
+    a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p; a.b = b;
+    if (ar == AR_FP64 || ar == AR_FP32) {
+        launch_numeric_simt(a, ar, st);
+        ss.issued = (double)npairs * 2.0 * b * b * b;
+    } else {
+        ss.issued = launch_numeric_tc(a, in, ar, h->tcw, NB, st);
+    }
+
+    // compaction
+    h->cnt_rows.ensure(nrows + 1);
+    launch_compact_count(h->out_rp.p, h->keep.p, nrows, h->cnt_rows.p, st);
+    out.row_ptr.ensure(nrows + 1);
+    scan_exclusive_i32(h->cnt_rows.p, out.row_ptr.p, nrows, h->scan_tmp32.p, st);
+    int kept = 0;
+    d2h(&kept, out.row_ptr.p + nrows, 1, st);
+    sync(h);
+    out.col.ensure(std::max(kept, 1));
+    out.val.ensure((size_t)std::max(kept, 1) * bb);
+    out.nrm.ensure(std::max(kept, 1));
+    launch_compact_copy(h->out_rp.p, mcol, h->out_val.p, h->out_nrm.p, h->keep.p,
+                        out.row_ptr.p, nrows, b, out.col.p, out.val.p, out.nrm.p, st);
+    out.total = kept;
+    std::vector<int> rp(nrows + 1);
+    d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
+    sync(h);
+    out.nnzb.assign(njob, 0);
+    for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
+    return ss;
+}
+
+JobTable solve_jobs(int nd) {
+    JobTable jt{};
+    jt.njob = 1 + nd;
+    jt.job[0] = Job{0, 0, 1, {0, 0}, {0, 0}, 0};
+    for (int d = 0; d < nd; ++d) jt.job[1 + d] = Job{1 + d, 1 + d, 2, {0, 1 + d}, {1 + d, 0}, 1};
+    return jt;
+}
+
+// per-system stats of the current X: [S][3+nd]
+std::vector<double> stats(rdm_handle *h, MatSet &X) {
+    const int nq = 3 + h->nd;
+    h->row_part.ensure((size_t)nq * h->NB);
+    h->sys_q.ensure((size_t)nq * h->S);
+    launch_row_stats(X.row_ptr.p, X.col.p, X.val.p, X.nmat, h->NB, h->b, h->H0.row_ptr.p,
+                     h->H0.col.p, h->H0.val.p, h->row_part.p, h->stream);
+    launch_sys_sum(h->row_part.p, nq, h->NB, h->sd.row0.p, h->sd.nbs.p, h->S, h->sys_q.p, h->stream);
+    std::vector<double> q((size_t)nq * h->S);
+    d2h(q.data(), h->sys_q.p, q.size(), h->stream);
+    sync(h);
+    return q;
+}
+
+int run_solve(rdm_handle *h, rdm_info *info_out) {
+    DeviceGuard dg(h->device);
+    if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
+    auto t_start = std::chrono::steady_clock::now();
+    assemble(h);
+    const int S = h->S, NB = h->NB, nd = h->nd, b = h->b;
+    const rdm_params &P = h->prm;
+    cudaStream_t st = h->stream;
+    const bool mixed = P.mode == RDM_MODE_MIXED_BF16 || P.mode == RDM_MODE_MIXED_FP16;
+    const bool lowprec = P.mode != RDM_MODE_FP64;
+    const int final_tier = mixed ? 1 : 0;
+
+    // Gershgorin bounds and the initial matrices
+    h->row_lo.ensure(NB);
+    h->row_hi.ensure(NB);
+    launch_gershgorin(h->H0.row_ptr.p, h->H0.col.p, h->H0.val.p, NB, b, h->sd.sys_of_row.p,
+                      h->sd.row0.p, h->sd.n_orb.p, h->row_lo.p, h->row_hi.p, st);
+    launch_sys_minmax(h->row_lo.p, h->row_hi.p, h->sd.row0.p, h->sd.nbs.p, S, h->sd.emin.p,
+                      h->sd.emax.p, st);
+    MatSet &X = h->X[0];
+    launch_init_scale(h->H0.row_ptr.p, h->H0.col.p, h->H0.val.p, X.val.p, X.nrm.p, NB, NB, b,
+                      h->sd.sys_of_row.p, h->sd.row0.p, h->sd.n_orb.p, h->sd.emin.p, h->sd.emax.p, 1, st);
+    if (nd) {
+        const size_t bb = (size_t)b * b;
+        // X1 blocks follow the X0 blocks; the H1 set's row_ptr indexes its own arrays
+        launch_init_scale(h->H1.row_ptr.p, h->H1.col.p, h->H1.val.p, X.val.p + h->H0.total * bb,
+                          X.nrm.p + h->H0.total, nd * NB, NB, b, h->sd.sys_of_row.p,
+                          h->sd.row0.p, h->sd.n_orb.p, h->sd.emin.p, h->sd.emax.p, 0, st);
+    }
+    std::vector<double> emin(S), emax(S);
+    d2h(emin.data(), h->sd.emin.p, S, st);
+    d2h(emax.data(), h->sd.emax.p, S, st);
+    sync(h);
+    for (int s = 0; s < S; ++s)
+        if (!(emax[s] > emin[s])) return fail(h, RDM_EBADBSR, "degenerate spectrum bounds (eps_max <= eps_min)");
+
+    std::vector<SysState> ss(S);
+    std::vector<double> nocc(S);
+    for (int s = 0; s < S; ++s) nocc[s] = (double)(h->hs[s].n_elec / 2);
+    const double tau0 = P.tau, tau1 = P.tau_x1 < 0 ? P.tau : P.tau_x1;
+    const double tau_ref = P.tau_refine < 0 ? P.tau : P.tau_refine;
+    const double tau1_ref = P.tau_x1 < 0 ? tau_ref : P.tau_x1;
+    h->log.clear();
+    JobTable jt = solve_jobs(nd);
+    std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
+    std::vector<int> act(S);
+    double useful = 0, issued = 0;
+    cudaEvent_t ev0, ev1;
+    RDM_CUDA_TRY(cudaEventCreate(&ev0));
+    RDM_CUDA_TRY(cudaEventCreate(&ev1));
+    int it = 0;
+    bool any_active = true;
+    std::vector<double> q;
+    for (it = 0; it <= P.max_iter; ++it) {
+        MatSet &Xc = h->X[h->cur];
+        q = stats(h, Xc);
+        const int nq = 3 + nd;
+        any_active = false;
+        for (int s = 0; s < S; ++s) {
+            SysState &y = ss[s];
+            act[s] = 0;
+            c_lin[s] = 1.0;
+            c_sq[s] = 0.0;
+            t0[s] = tau0;
+            t1[s] = tau1;
+            if (!y.active) continue;
+            const double tr = q[(size_t)s * nq + 0], sumsq = q[(size_t)s * nq + 1];
+            const double e = tr - sumsq;
+            const double eb0 = q[(size_t)s * nq + 2];
+            // close the log record of the previous step with the new band energies
+            for (auto r = h->log.rbegin(); r != h->log.rend(); ++r)
+                if (r->sys == s) {
+                    r->eb0 = eb0;
+                    for (int d = 0; d < nd; ++d) r->eb1[d] = q[(size_t)s * nq + 3 + d];
+                    break;
+                }
+            const int n = y.iters;   // number of updates done so far
+            bool stop = false;
+            if (!std::isfinite(tr) || !std::isfinite(sumsq)) {
+                y.active = false;
+                continue;
+            }
+            // band-energy stop (Sec. 2.3 tolerance), only in the final tier
+            if (y.have_eb && P.tol > 0 && n >= std::max(2, P.min_iter) && y.tier == final_tier) {
+                double d0 = fabs(eb0 - y.eb0), d1 = 0;
+                for (int d = 0; d < nd; ++d) d1 = std::max(d1, fabs(q[(size_t)s * nq + 3 + d] - y.eb1[d]));
+                if (d0 < P.tol && d1 < P.tol) stop = true;
+            }
+            // idempotency stall
+            const double stall_tol = P.stall_tol;
+            y.e_hist.push_back(e);
+            const size_t E = y.e_hist.size();
+            if (!stop && n >= std::max(3, P.min_iter) && E >= 3) {
+                if (!lowprec && stall_tol > 0 && e >= y.e_hist[E - 3] && e < stall_tol) stop = true;
+                if (lowprec && y.tier == final_tier && n - y.tier_start >= 2 &&
+                    fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) && fabs(e) < 1e-2 * nocc[s])
+                    stop = true;
+            }
+            y.have_eb = true;
+            y.eb0 = eb0;
+            for (int d = 0; d < nd; ++d) y.eb1[d] = q[(size_t)s * nq + 3 + d];
+            if (stop) {
+                y.active = false;
+                y.converged = true;
+                continue;
+            }
+            if (n >= P.max_iter) {
+                y.active = false;
+                continue;
+            }
+            // tier switch on idempotency stall (mixed modes)
+            if (mixed && y.tier < final_tier && E >= 3 && fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) &&
+                fabs(e) < 1e-2 * nocc[s]) {
+                y.tier++;
+                y.tier_start = n;
+            }
+            // branch: trace test of Eq. TC2 (tie -> square); forced by the test hook;
+            // in the reduced-precision modes a negative idempotency error (spectrum
+            // outside [0,1]) alternates the branch so that both edges contract
+            int branch = (tr >= nocc[s]) ? 1 : 2;
+            if (lowprec && e < 0 && n > 0) branch = y.prev_branch == 1 ? 2 : 1;
+            if (n < (int)h->forced.size()) branch = h->forced[n];
+            y.prev_branch = branch;
+            c_lin[s] = branch == 1 ? 0.0 : 2.0;
+            c_sq[s] = branch == 1 ? 1.0 : -1.0;
+            if (y.tier == final_tier && mixed) {
+                t0[s] = tau_ref;
+                t1[s] = tau1_ref;
+            }
+            act[s] = 1;
+            any_active = true;
+            rdm_iter_log L{};
+            L.iter = n;
+            L.branch = branch;
+            L.tier = y.tier;
+            L.sys = s;
+            L.trace = tr;
+            L.idempotency = e;
+            h->log.push_back(L);
+        }
+        if (!any_active) break;
+        // all active systems of this step share one arithmetic per launch; a
+        // batch whose systems sit in different tiers runs the higher precision
+        int tier = final_tier;
+        for (int s = 0; s < S; ++s)
+            if (act[s]) tier = std::min(tier, ss[s].tier);
+        for (int s = 0; s < S; ++s)
+            if (act[s] && ss[s].tier != tier && mixed) tier = final_tier;
+        const Arith ar = tier_arith(P.mode, tier);
+        h2d(h->sd.c_lin.p, c_lin.data(), S, st);
+        h2d(h->sd.c_sq.p, c_sq.data(), S, st);
+        h2d(h->sd.tau0.p, t0.data(), S, st);
+        h2d(h->sd.tau1.p, t1.data(), S, st);
+        h2d(h->sd.active.p, act.data(), S, st);
+        RDM_CUDA_TRY(cudaEventRecord(ev0, st));
+        MatSet &Xn = h->X[1 - h->cur];
+        StepStats sst = multiply(h, Xc, Xn, jt, ar);
+        RDM_CUDA_TRY(cudaEventRecord(ev1, st));
+        RDM_CUDA_TRY(cudaEventSynchronize(ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        useful += (double)sst.npairs * 2.0 * b * b * b;
+        issued += sst.issued;
+        h->cur = 1 - h->cur;
+        for (int s = 0; s < S; ++s)
+            if (act[s]) {
+                ss[s].iters++;
+                ss[s].tier_iters[ss[s].tier]++;
+            }
+        int nstep = 0;
+        for (int s = 0; s < S; ++s) nstep += act[s];
+        for (auto r = h->log.rbegin(); r != h->log.rend() && nstep > 0; ++r, --nstep) {
+            r->ms = ms;
+            r->nnzb0 = Xn.nnzb[0];
+            for (int d = 0; d < nd; ++d) r->nnzb1[d] = Xn.nnzb[1 + d];
+        }
+        if (P.verbose) {
+            fprintf(stderr, "[rdm] step %d arith %d pairs %lld slots %lld nnzb0 %lld %.3f ms\n", it, (int)ar,
+                    (long long)sst.npairs, (long long)sst.nslot, (long long)Xn.nnzb[0], ms);
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+
+    // polarizability: alpha[g][d] = -spin * <P1_d, H1_g>
+    MatSet &Xf = h->X[h->cur];
+    h->alpha.assign((size_t)S * 9, NAN);
+    if (nd) {
+        const int nq = nd * nd;
+        h->row_part.ensure((size_t)nq * NB);
+        h->sys_q.ensure((size_t)nq * S);
+        launch_row_dots(Xf.row_ptr.p + NB, Xf.col.p, Xf.val.p, nd, h->H1.row_ptr.p, h->H1.col.p,
+                        h->H1.val.p, nd, NB, b, h->row_part.p, st);
+        launch_sys_sum(h->row_part.p, nq, NB, h->sd.row0.p, h->sd.nbs.p, S, h->sys_q.p, st);
+        std::vector<double> dq((size_t)nq * S);
+        d2h(dq.data(), h->sys_q.p, dq.size(), st);
+        sync(h);
+        for (int s = 0; s < S; ++s)
+            for (int g = 0; g < nd; ++g)
+                for (int d = 0; d < nd; ++d)
+                    h->alpha[(size_t)s * 9 + 3 * h->dirs[g] + h->dirs[d]] =
+                        -P.spin_factor * dq[(size_t)s * nq + g * nd + d];
+    }
+    // final pattern on the host for the getters, summary per system
+    h->final_rp.resize((size_t)Xf.nmat * NB + 1);
+    d2h(h->final_rp.data(), Xf.row_ptr.p, h->final_rp.size(), st);
+    sync(h);
+    auto t_end = std::chrono::steady_clock::now();
+    double wall_ms = std::chrono::duration<double, std::milli>(t_end - t_start).count();
+    h->info.assign(S, rdm_info{});
+    const int nq = 3 + nd;
+    bool all_conv = true;
+    for (int s = 0; s < S; ++s) {
+        rdm_info &I = h->info[s];
+        I.iterations = ss[s].iters;
+        I.converged = ss[s].converged ? 1 : 0;
+        all_conv = all_conv && ss[s].converged;
+        for (int t = 0; t < 4; ++t) I.tier_iters[t] = ss[s].tier_iters[t];
+        I.eps_min = emin[s];
+        I.eps_max = emax[s];
+        I.trace_error = q[(size_t)s * nq] - nocc[s];
+        I.idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
+        I.band_energy0 = 0;
+        int r0 = h->row0[s], r1 = r0 + h->nbs[s];
+        I.nnzb_p0 = h->final_rp[r1] - h->final_rp[r0];
+        for (int d = 0; d < nd; ++d)
+            I.nnzb_p1[h->dirs[d]] = h->final_rp[(size_t)(1 + d) * NB + r1] - h->final_rp[(size_t)(1 + d) * NB + r0];
+        I.time_ms = wall_ms;
+        I.useful_flops = useful;
+        I.issued_flops = issued;
+    }
+    // band energy of the result: recompute the stats of the final X
+    q = stats(h, Xf);
+    for (int s = 0; s < S; ++s) {
+        h->info[s].band_energy0 = q[(size_t)s * nq + 2];
+        h->info[s].trace_error = q[(size_t)s * nq] - nocc[s];
+        h->info[s].idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
+    }
+    h->solved = true;
+    if (info_out) *info_out = h->info[0];
+    return all_conv ? RDM_OK : RDM_NOT_CONVERGED;
+}
+
+int get_matrix(rdm_handle *h, int sys, int mat, rdm_bsr_out *out) {
+    if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
+    if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
+    if (!out) return fail(h, RDM_EINVAL, "null output");
+    DeviceGuard dg(h->device);
+    MatSet &X = h->X[h->cur];
+    const int NB = h->NB, r0 = h->row0[sys], nbs = h->nbs[sys], b = h->b;
+    const size_t bb = (size_t)b * b;
+    const int *rp = h->final_rp.data() + (size_t)mat * NB;
+    int64_t first = rp[r0], last = rp[r0 + nbs];
+    int64_t n = last - first;
+    out->nb = nbs;
+    out->b = b;
+    out->n = h->norb[sys];
+    if (!out->row_ptr) {   // size query
+        out->nnzb = n;
+        return RDM_OK;
+    }
+    if (out->nnzb < n || (n && (!out->col_idx || !out->vals))) {
+        out->nnzb = n;
+        return fail(h, RDM_EINVAL, "output capacity too small (need " + std::to_string(n) + " blocks)");
+    }
+    for (int i = 0; i <= nbs; ++i) out->row_ptr[i] = (int)(rp[r0 + i] - first);
+    d2h(out->col_idx, X.col.p + first, (size_t)n, h->stream);
+    d2h(out->vals, X.val.p + first * bb, (size_t)n * bb, h->stream);
+    sync(h);
+    for (int64_t p = 0; p < n; ++p) out->col_idx[p] -= r0;
+    out->nnzb = n;
+    return RDM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+const char *rdm_version(void) { return "rdm-gb300 0.1 (sm_103a)"; }
+
+int rdm_default_params(rdm_params *p) {
+    if (!p) return RDM_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->tau = 1e-6;
+    p->tau_x1 = -1;
+    p->tau_refine = -1;
+    p->tol = 1e-9;
+    p->stall_tol = 0;
+    p->spin_factor = 2.0;
+    p->max_iter = 100;
+    p->mode = RDM_MODE_FP64;
+    p->min_iter = 1;
+    p->use_graphs = 0;
+    p->verbose = 0;
+    return RDM_OK;
+}
+
+static thread_local std::string g_create_err;
+
+int rdm_create(rdm_handle **out, int device, void *cuda_stream) {
+    if (!out) return RDM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return RDM_ECUDA;
+    }
+    if (device < 0 || device >= ndev) {
+        g_create_err = "device index out of range";
+        return RDM_EINVAL;
+    }
+    rdm_handle *h = new (std::nothrow) rdm_handle();
+    if (!h) return RDM_ENOMEM;
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    rdm_default_params(&h->prm);
+    h->S = 1;
+    h->hs.resize(1);
+    *out = h;
+    return RDM_OK;
+}
+
+int rdm_destroy(rdm_handle *h) {
+    if (!h) return RDM_OK;
+    {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(h->device);
+        cudaStreamSynchronize(h->stream);
+        delete h;   // DevBuf members are released below through their owners
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    return RDM_OK;
+}
+
+const char *rdm_last_error(const rdm_handle *h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+int rdm_set_params(rdm_handle *h, const rdm_params *p) {
+    if (!h) return RDM_EINVAL;
+    if (!p) return fail(h, RDM_EINVAL, "null params");
+    if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 4 ||
+        !(p->spin_factor > 0) || p->min_iter < 0)
+        return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..4)");
+    h->prm = *p;
+    return RDM_OK;
+}
+
+int rdm_batch_create(rdm_handle *h, int n_systems) {
+    if (!h) return RDM_EINVAL;
+    if (n_systems < 1 || n_systems > 65536) return fail(h, RDM_EINVAL, "n_systems out of range");
+    return guarded(h, [&] {
+        DeviceGuard dg(h->device);
+        h->hs.clear();
+        h->hs.resize(n_systems);
+        h->S = n_systems;
+        h->b = 0;
+        h->solved = false;
+        return RDM_OK;
+    });
+}
+
+int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons) {
+    if (!h) return RDM_EINVAL;
+    if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
+    return guarded(h, [&] {
+        DeviceGuard dg(h->device);
+        if (!H0) return fail(h, RDM_EINVAL, "null matrix");
+        if (n_electrons <= 0 || (n_electrons & 1) || n_electrons / 2 >= H0->n)
+            return fail(h, RDM_EINVAL, "electron count must be even with 0 < N_e/2 < n");
+        HostSys &y = h->hs[sys];
+        int saved_b = h->b;
+        if (h->S == 1) h->b = 0;
+        try {
+            upload_matrix(h, H0, y.rp, y.col, y.val, true);
+        } catch (...) {
+            h->b = saved_b;
+            throw;
+        }
+        y.has_h0 = true;
+        y.nb = H0->nb;
+        y.n = H0->n;
+        y.n_elec = n_electrons;
+        if (h->S == 1)
+            for (int d = 0; d < 3; ++d)
+                if (y.has_h1[d] && (int)y.rp1[d].size() != y.nb + 1) y.has_h1[d] = false;
+        h->solved = false;
+        return RDM_OK;
+    });
+}
+
+int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1) {
+    if (!h) return RDM_EINVAL;
+    if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
+    if (dir < 0 || dir > 2) return fail(h, RDM_EINVAL, "direction must be 0, 1 or 2");
+    return guarded(h, [&] {
+        DeviceGuard dg(h->device);
+        HostSys &y = h->hs[sys];
+        if (!y.has_h0) return fail(h, RDM_ESTATE, "upload H0 of the system before H1");
+        if (!H1) return fail(h, RDM_EINVAL, "null matrix");
+        if (H1->nb != y.nb || H1->n != y.n || H1->b != h->b)
+            return fail(h, RDM_EINVAL, "H1 must have the same nb, b and n as H0");
+        upload_matrix(h, H1, y.rp1[dir], y.col1[dir], y.val1[dir], false);
+        y.has_h1[dir] = true;
+        h->solved = false;
+        return RDM_OK;
+    });
+}
+
+int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len) {
+    if (!h) return RDM_EINVAL;
+    if (len < 0 || (len > 0 && !seq)) return fail(h, RDM_EINVAL, "bad branch sequence");
+    for (int i = 0; i < len; ++i)
+        if (seq[i] != 1 && seq[i] != 2) return fail(h, RDM_EINVAL, "branches must be 1 or 2");
+    h->forced.assign(seq, seq + len);
+    return RDM_OK;
+}
+
+int rdm_solve(rdm_handle *h, rdm_info *info) {
+    if (!h) return RDM_EINVAL;
+    return guarded(h, [&] { return run_solve(h, info); });
+}
+
+int rdm_get_info(rdm_handle *h, int sys, rdm_info *info) {
+    if (!h) return RDM_EINVAL;
+    if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
+    if (sys < 0 || sys >= h->S || !info) return fail(h, RDM_EINVAL, "bad system index or null output");
+    *info = h->info[sys];
+    return RDM_OK;
+}
+
+int rdm_get_p0_nnzb(rdm_handle *h, int sys, int64_t *nnzb) {
+    if (!h) return RDM_EINVAL;
+    if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
+    if (sys < 0 || sys >= h->S || !nnzb) return fail(h, RDM_EINVAL, "bad system index or null output");
+    *nnzb = h->info[sys].nnzb_p0;
+    return RDM_OK;
+}
+
+int rdm_get_p1_nnzb(rdm_handle *h, int sys, int dir, int64_t *nnzb) {
+    if (!h) return RDM_EINVAL;
+    if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
+    if (sys < 0 || sys >= h->S || !nnzb || dir < 0 || dir > 2) return fail(h, RDM_EINVAL, "bad index or null output");
+    for (int d = 0; d < h->nd; ++d)
+        if (h->dirs[d] == dir) {
+            *nnzb = h->info[sys].nnzb_p1[dir];
+            return RDM_OK;
+        }
+    return fail(h, RDM_EINVAL, "direction was not uploaded");
+}
+
+int rdm_get_p0(rdm_handle *h, int sys, rdm_bsr_out *out) {
+    if (!h) return RDM_EINVAL;
+    return guarded(h, [&] { return get_matrix(h, sys, 0, out); });
+}
+
+int rdm_get_p1(rdm_handle *h, int sys, int dir, rdm_bsr_out *out) {
+    if (!h) return RDM_EINVAL;
+    return guarded(h, [&] {
+        for (int d = 0; d < h->nd; ++d)
+            if (h->dirs[d] == dir) return get_matrix(h, sys, 1 + d, out);
+        return fail(h, RDM_EINVAL, "direction was not uploaded");
+    });
+}
+
+int rdm_get_alpha(rdm_handle *h, int sys, double alpha[9]) {
+    if (!h) return RDM_EINVAL;
+    if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
+    if (sys < 0 || sys >= h->S || !alpha) return fail(h, RDM_EINVAL, "bad system index or null output");
+    for (int k = 0; k < 9; ++k) alpha[k] = h->alpha[(size_t)sys * 9 + k];
+    return RDM_OK;
+}
+
+int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n) {
+    if (!h) return RDM_EINVAL;
+    if (!n || (cap > 0 && !out)) return fail(h, RDM_EINVAL, "null output");
+    int m = std::min<int>(cap, (int)h->log.size());
+    for (int k = 0; k < m; ++k) out[k] = h->log[k];
+    *n = (int)h->log.size();
+    return RDM_OK;
+}
+
+int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const rdm_bsr *X,
+                      double c_lin, double c_sq, int terms, double tau, int mode,
+                      rdm_bsr_out *out, int64_t *needed) {
+    if (!h) return RDM_EINVAL;
+    return guarded(h, [&]() -> int {
+        DeviceGuard dg(h->device);
+        if (!A || (terms == 2 && !B)) return fail(h, RDM_EINVAL, "null operand");
+        if (terms != 1 && terms != 2) return fail(h, RDM_EINVAL, "terms must be 1 or 2");
+        if (!(tau >= 0) || mode < 0 || mode > 4) return fail(h, RDM_EINVAL, "bad tau or mode");
+        if (A->nb > kSymMaxNs) return fail(h, RDM_EINVAL, "matrix too large for the product primitive");
+        // a private single-system context so that the solve state is untouched
+        rdm_handle t;
+        t.device = h->device;
+        t.stream = h->stream;
+        t.S = 1;
+        t.hs.resize(1);
+        const rdm_bsr *mats[3] = {A, terms == 2 ? B : nullptr, X};
+        std::vector<int> rps[3], cols[3];
+        DevBuf<double> vals[3];
+        int nm = 0;
+        int idx[3] = {-1, -1, -1};
+        for (int k = 0; k < 3; ++k) {
+            if (!mats[k]) continue;
+            if (mats[k]->nb != A->nb || mats[k]->b != A->b || mats[k]->n != A->n)
+                return fail(h, RDM_EINVAL, "operands must share nb, b and n");
+            upload_matrix(&t, mats[k], rps[k], cols[k], vals[k], false);
+            idx[k] = nm++;
+        }
+        const int NB = A->nb, b = A->b;
+        const size_t bb = (size_t)b * b;
+        MatSet in;
+        in.nmat = nm;
+        in.NB = NB;
+        in.b = b;
+        std::vector<int> rp((size_t)nm * NB + 1);
+        std::vector<int> col;
+        int64_t top = 0;
+        in.nnzb.assign(nm, 0);
+        for (int k = 0; k < 3; ++k) {
+            if (idx[k] < 0) continue;
+            for (int i = 0; i < NB; ++i) rp[(size_t)idx[k] * NB + i] = (int)(top + rps[k][i]);
+            col.insert(col.end(), cols[k].begin(), cols[k].end());
+            in.nnzb[idx[k]] = rps[k][NB];
+            top += rps[k][NB];
+        }
+        rp[(size_t)nm * NB] = (int)top;
+        in.total = top;
+        in.row_ptr.ensure(rp.size());
+        in.col.ensure(std::max<int64_t>(top, 1));
+        in.val.ensure(std::max<int64_t>(top, 1) * bb);
+        in.nrm.ensure(std::max<int64_t>(top, 1));
+        h2d(in.row_ptr.p, rp.data(), rp.size(), t.stream);
+        h2d(in.col.p, col.data(), col.size(), t.stream);
+        int64_t off = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (idx[k] < 0) continue;
+            int64_t n = rps[k][NB];
+            if (n) RDM_CUDA_TRY(cudaMemcpyAsync(in.val.p + off * bb, vals[k].p, n * bb * sizeof(double),
+                                                cudaMemcpyDeviceToDevice, t.stream));
+            off += n;
+        }
+        launch_block_norms(in.val.p, in.nrm.p, top, b, t.stream);
+        t.NB = NB;
+        t.b = b;
+        t.nbs = {NB};
+        t.row0 = {0};
+        t.norb = {A->n};
+        SysDev &sd = t.sd;
+        sd.row0.ensure(1); sd.nbs.ensure(1); sd.n_orb.ensure(1); sd.sys_of_row.ensure(NB);
+        sd.c_lin.ensure(1); sd.c_sq.ensure(1); sd.tau0.ensure(1); sd.tau1.ensure(1); sd.active.ensure(1);
+        RDM_CUDA_TRY(cudaMemsetAsync(sd.row0.p, 0, sizeof(int), t.stream));
+        RDM_CUDA_TRY(cudaMemsetAsync(sd.sys_of_row.p, 0, NB * sizeof(int), t.stream));
+        int one = 1;
+        h2d(sd.nbs.p, &NB, 1, t.stream);
+        h2d(sd.n_orb.p, &A->n, 1, t.stream);
+        h2d(sd.active.p, &one, 1, t.stream);
+        h2d(sd.c_lin.p, &c_lin, 1, t.stream);
+        h2d(sd.c_sq.p, &c_sq, 1, t.stream);
+        h2d(sd.tau0.p, &tau, 1, t.stream);
+        h2d(sd.tau1.p, &tau, 1, t.stream);
+        JobTable jt{};
+        jt.njob = 1;
+        int ia = idx[0], ib = terms == 2 ? idx[1] : idx[0];
+        int ix = X ? idx[2] : -1;
+        if (terms == 1) jt.job[0] = Job{0, ix, 1, {ia, ia}, {ia, ia}, 0};
+        else jt.job[0] = Job{0, ix, 2, {ia, ib}, {ib, ia}, 0};
+        Arith ar = tier_arith(mode, 0);
+        MatSet res;
+        multiply(&t, in, res, jt, ar);
+        int64_t n = res.nnzb[0];
+        if (needed) *needed = n;
+        if (!out || !out->row_ptr || out->nnzb < n || (n && (!out->col_idx || !out->vals))) {
+            if (out) out->nnzb = n;
+            res.release();
+            in.release();
+            return out && out->row_ptr ? fail(h, RDM_EINVAL, "output capacity too small") : RDM_OK;
+        }
+        std::vector<int> rrp((size_t)NB + 1);
+        d2h(rrp.data(), res.row_ptr.p, NB + 1, t.stream);
+        d2h(out->col_idx, res.col.p, (size_t)n, t.stream);
+        d2h(out->vals, res.val.p, (size_t)n * bb, t.stream);
+        RDM_CUDA_TRY(cudaStreamSynchronize(t.stream));
+        for (int i = 0; i <= NB; ++i) out->row_ptr[i] = rrp[i];
+        out->nb = NB;
+        out->b = b;
+        out->n = A->n;
+        out->nnzb = n;
+        res.release();
+        in.release();
+        return RDM_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Numeric phase on the CUDA cores (FP64 and FP32 operands), with the update
+// and truncation of Eqs. TC2 / TC2-CPSCF fused into the epilogue:
+//
+//   C_ij = c_lin X_ij + c_sq sum_{(a,b) in pairs(i,j)} A_a (B_b)^T
+//
+// for every upper-triangle output block (j >= i); the lower block (j,i) is
+// written as the transpose, so the result is exactly symmetric.  Diagonal
+// blocks are symmetrised ((C + C^T)/2) because the accumulation order of
+// C_mn and C_nm differs.  The block Frobenius norm is reduced in FP64 and the
+// block is kept iff norm >= tau (the block-wise "filter" of Sec. 2.3).
+//
+// One CTA per output block (grid-stride over the work list); the two
+// operand blocks of each pair are staged in shared memory, each thread owns
+// ceil(b^2 / threads) outputs.  On GB300 the FP64 rate is the bound of this
+// kernel; the FP32 variant converts the FP64 master values on load.
+#include "rdm_internal.cuh"
+
+namespace rdm {
+namespace {
+
+template <int B>
+struct Cfg {
+    static constexpr int NT = (B * B >= 256) ? 256 : ((B * B < 32) ? 32 : B * B);
+    static constexpr int PER = (B * B + NT - 1) / NT;
+    static constexpr int LD = B + 1;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    __syncthreads();
+    return t;
+}
+
+template <int B, class T>
+__global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
+    constexpr int NT = Cfg<B>::NT, PER = Cfg<B>::PER, LD = Cfg<B>::LD, BB = B * B;
+    extern __shared__ double smem_d[];
+    T *As = reinterpret_cast<T *>(smem_d);
+    T *Bs = As + B * LD;
+    double *Cs = smem_d;                    // reused for the epilogue (B*LD doubles)
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
+
+    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+        const int s = a.work[w];
+        const int i = a.slot_row[s];
+        const int sys = a.sys_of_row[i];
+        const int job = a.slot_job[s];
+        const double cl = a.c_lin[sys], cq = a.c_sq[sys];
+        const double tau = a.job_tau_sel[job] ? a.tau1[sys] : a.tau0[sys];
+        const int64_t p0 = a.pair_off[s], p1 = a.pair_off[s + 1];
+        const int st = a.slot_t[s], sx = a.slot_x[s];
+
+        T acc[PER];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) acc[r] = T(0);
+
+        for (int64_t q = p0; q < p1; ++q) {
+            const double *ga = a.in_val + (size_t)a.pair_a[q] * BB;
+            const double *gb = a.in_val + (size_t)a.pair_b[q] * BB;
+            __syncthreads();
+            for (int e = tid; e < BB; e += NT) {
+                As[(e / B) * LD + (e % B)] = (T)ga[e];
+                Bs[(e / B) * LD + (e % B)] = (T)gb[e];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int e = tid + r * NT;
+                if (e < BB) {
+                    const int m = e / B, n = e % B;
+                    const T *ar = As + m * LD;
+                    const T *br = Bs + n * LD;
+                    T sacc = acc[r];
+#pragma unroll 8
+                    for (int kk = 0; kk < B; ++kk) sacc = fma(ar[kk], br[kk], sacc);
+                    acc[r] = sacc;
+                }
+            }
+        }
+
+        // epilogue: linear term, symmetrisation, norm, truncation, both triangles
+        double out[PER];
+        const double *gx = sx >= 0 ? a.in_val + (size_t)sx * BB : nullptr;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = tid + r * NT;
+            if (e < BB) {
+                double v = cq * (double)acc[r];
+                if (gx) v = fma(cl, gx[e], v);
+                out[r] = v;
+                Cs[(e / B) * LD + (e % B)] = v;
+            }
+        }
+        __syncthreads();
+        const bool diag = (st == s);
+        double ss = 0.0;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = tid + r * NT;
+            if (e < BB) {
+                if (diag) {
+                    const int m = e / B, n = e % B;
+                    out[r] = 0.5 * (Cs[m * LD + n] + Cs[n * LD + m]);
+                }
+                ss += out[r] * out[r];
+            }
+        }
+        const double nrm = sqrt(block_sum(ss, red));
+        const bool keep = (nrm >= tau) && (nrm > 0.0);
+        double *o = a.out_val + (size_t)s * BB;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = tid + r * NT;
+            if (e < BB) o[e] = out[r];
+        }
+        if (!diag) {
+            double *ot = a.out_val + (size_t)st * BB;
+            for (int e = tid; e < BB; e += NT) ot[e] = Cs[(e % B) * LD + (e / B)];
+        }
+        if (tid == 0) {
+            const float fn = __double2float_ru(nrm);
+            a.out_nrm[s] = fn;
+            a.keep[s] = keep;
+            if (!diag) { a.out_nrm[st] = fn; a.keep[st] = keep; }
+        }
+    }
+}
+
+template <int B, class T>
+void launch_b(const NumArgs &a, cudaStream_t st) {
+    constexpr int NT = Cfg<B>::NT, LD = Cfg<B>::LD;
+    size_t smem = (size_t)B * LD * sizeof(double);
+    size_t ab = 2 * (size_t)B * LD * sizeof(T);
+    if (ab > smem) smem = ab;
+    static bool attr = false;
+    if (!attr) {
+        RDM_CUDA_TRY(cudaFuncSetAttribute(k_numeric_simt<B, T>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int grid = a.nwork < 152 * 16 ? a.nwork : 152 * 16;
+    if (grid <= 0) return;
+    k_numeric_simt<B, T><<<grid, NT, smem, st>>>(a);
+    RDM_LAUNCH_CHECK();
+}
+
+template <class T>
+void dispatch(const NumArgs &a, cudaStream_t st) {
+    switch (a.b) {
+        case 1: launch_b<1, T>(a, st); break;
+        case 2: launch_b<2, T>(a, st); break;
+        case 4: launch_b<4, T>(a, st); break;
+        case 8: launch_b<8, T>(a, st); break;
+        case 16: launch_b<16, T>(a, st); break;
+        case 32: launch_b<32, T>(a, st); break;
+        case 64: launch_b<64, T>(a, st); break;
+        default: throw Error{-1, "block size must be 1, 2, 4, 8, 16, 32 or 64"};
+    }
+}
+
+}  // namespace
+
+void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st) {
+    if (a.nwork == 0) return;
+    if (ar == AR_FP64) dispatch<double>(a, st);
+    else dispatch<float>(a, st);
+}
+
+}  // namespace rdm

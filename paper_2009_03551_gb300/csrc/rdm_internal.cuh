@@ -1,0 +1,226 @@
+// Internal declarations of the GB300 response-density-matrix library.
+//
+// Data model
+// ----------
+// A batch of independent systems is stored as ONE block-diagonal block-sparse
+// matrix over NB = sum_s nb_s block rows; system s owns block rows (and block
+// columns) [row0[s], row0[s] + nb[s]).  All systems share the block size b.
+//
+// A MatSet holds nmat such matrices over the same block-row space, in one set
+// of arrays: blocks of matrix m occupy global block indices
+// [row_ptr[m*NB], row_ptr[m*NB+NB]) (row_ptr has nmat*NB+1 entries, so row i
+// of matrix m is [row_ptr[m*NB+i], row_ptr[m*NB+i+1])).  row_ptr entries are global
+// block indices; col_idx holds global block columns (sorted inside a row);
+// val holds b*b FP64 values per block (row-major); nrm holds an FP32 upper
+// bound of every block's Frobenius norm.  In the solve, matrix 0 is X0 and
+// matrices 1..nd are X1_gamma.  Patterns of every matrix are symmetric and
+// values are symmetric (block (j,i) is the transpose of block (i,j)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace rdm {
+
+// ---------------------------------------------------------------------------
+// error handling inside the library (converted to status codes at the ABI)
+// ---------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define RDM_CUDA_TRY(expr)                                                        \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess)                                                    \
+            throw ::rdm::Error{_e == cudaErrorMemoryAllocation ? -3 : -4,         \
+                               std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
+
+#define RDM_LAUNCH_CHECK() RDM_CUDA_TRY(cudaGetLastError())
+
+// grow-only device buffer (capacity is kept across iterations and solves)
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), cap(o.cap) { o.p = nullptr; o.cap = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; cap = o.cap; o.p = nullptr; o.cap = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void swap(DevBuf &o) noexcept { std::swap(p, o.p); std::swap(cap, o.cap); }
+    T *ensure(size_t n) {
+        if (n <= cap && p) return p;
+        size_t want = n < 16 ? 16 : n + n / 4;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc((void **)&p, want * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            throw Error{-3, "cudaMalloc of " + std::to_string(want * sizeof(T)) + " bytes failed"};
+        }
+        cap = want;
+        return p;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// per-system scalars kept on the device (FP64 where the method needs it)
+struct SysDev {
+    DevBuf<int> row0, nbs, n_orb;      // [S]
+    DevBuf<int> sys_of_row;            // [NB]
+    DevBuf<double> emin, emax;         // [S]
+    DevBuf<double> c_lin, c_sq;        // [S]   branch coefficients of the current step
+    DevBuf<double> tau0, tau1;         // [S]   truncation thresholds of the current step
+    DevBuf<int> active;                // [S]   1 = still iterating
+    DevBuf<int> tier;                  // [S]
+};
+
+struct MatSet {
+    int nmat = 0;
+    int NB = 0;
+    int b = 0;
+    DevBuf<int> row_ptr;      // nmat*NB+1 (flat)
+    DevBuf<int> col;          // total blocks
+    DevBuf<double> val;       // total*b*b
+    DevBuf<float> nrm;        // total
+    DevBuf<uint16_t> ophi;    // operand copies for the tensor-core tiers
+    DevBuf<uint16_t> oplo;
+    std::vector<int64_t> nnzb;   // host copy, per matrix
+    int64_t total = 0;
+    void release() {
+        row_ptr.release(); col.release(); val.release(); nrm.release();
+        ophi.release(); oplo.release();
+        nnzb.clear(); total = 0;
+    }
+};
+
+// One output matrix of a multiplication step:
+//   C = c_lin * X + c_sq * sum_t (A_t B_t)
+struct Job {
+    int out;          // output matrix index
+    int xmat;         // matrix of the linear term (-1: none)
+    int nterm;        // 1 or 2
+    int a[2], b[2];   // operand matrices of each term
+    int tau_sel;      // 0: tau0[s], 1: tau1[s]
+};
+
+constexpr int kMaxJobs = 8;
+struct JobTable {
+    int njob;
+    Job job[kMaxJobs];
+};
+
+// Operand arithmetic of a numeric launch
+enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_TF32 = 4 };
+
+// ---------------------------------------------------------------------------
+// kernel launchers (implemented in the k_*.cu files)
+// ---------------------------------------------------------------------------
+
+// k_scan.cu: exclusive scan (out may alias in); returns nothing, total at out[n]
+void scan_exclusive_i32(const int *in, int *out, int n, int *tmp, cudaStream_t st);
+void scan_exclusive_i64(const int *in, int64_t *out, int n, int64_t *tmp, cudaStream_t st);
+size_t scan_tmp_elems(int n);
+
+// k_setup.cu
+void launch_gershgorin(const int *row_ptr, const int *col, const double *val, int NB, int b,
+                       const int *sys_of_row, const int *row0, const int *n_orb,
+                       double *row_lo, double *row_hi, cudaStream_t st);
+void launch_sys_minmax(const double *row_lo, const double *row_hi, const int *row0, const int *nbs,
+                       int S, double *emin, double *emax, cudaStream_t st);
+// X := alpha * (diag_shift_sel ? emax[s] I : 0) + beta * H   (per system scaling), norms
+// rows = number of block rows of the (possibly multi-matrix) set; NB = rows per matrix
+void launch_init_scale(const int *row_ptr, const int *col, const double *hval, double *xval,
+                       float *xnrm, int rows, int NB, int b, const int *sys_of_row,
+                       const int *row0, const int *n_orb, const double *emin,
+                       const double *emax, int is_x0, cudaStream_t st);
+void launch_block_norms(const double *val, float *nrm, int64_t nblk, int b, cudaStream_t st);
+void launch_check_values(const int *row_ptr, const int *col, const double *val, int64_t nval,
+                         int NB, int b, const int *sys_of_row, const int *row0, const int *n_orb,
+                         double rel_tol, int *err, cudaStream_t st);
+
+// k_stats.cu: per-row partial sums then a deterministic per-system reduction.
+// q-layout of the per-system output (double, [S][nq]):
+//   0: Tr X0, 1: ||X0||_F^2, 2: Tr(X0 H0), 3+g: Tr(X1_g H0)
+void launch_row_stats(const int *row_ptr, const int *col, const double *val, int nmat, int NB,
+                      int b, const int *h_row_ptr, const int *h_col, const double *h_val,
+                      double *row_part, cudaStream_t st);
+void launch_sys_sum(const double *row_part, int nq, int NB, const int *row0, const int *nbs,
+                    int S, double *out, cudaStream_t st);
+
+// alpha: per-row partials of <P1_d, H1_g> over intersecting blocks
+void launch_row_dots(const int *p_row_ptr, const int *p_col, const double *p_val, int np,
+                     const int *h_row_ptr, const int *h_col, const double *h_val, int nh,
+                     int NB, int b, double *row_part, cudaStream_t st);
+
+// k_symbolic.cu
+struct SymOut {
+    int *row_cnt;        // [njob*NB] kept blocks per (job,row)
+    int *row_off;        // [njob*NB] offset of the row's list in the pool
+    int *pool_col;       // pool of kept columns
+    int *pool_npair;     // pool of pair counts (per kept column)
+    int *pool_top;       // [1] pool allocation counter
+    int pool_cap;
+    int *overflow;       // [1] set when the pool is too small
+};
+// largest system (in block rows) the shared-memory row accumulator handles
+constexpr int kSymMaxNs = 8192;
+void launch_symbolic(const MatSet &in, const JobTable &jt, const SysDev &sd, int S,
+                     SymOut so, cudaStream_t st, int max_ns);
+// gathers the pool into the output pattern; writes slot_row/slot_job and the
+// per-slot pair counts (0 for lower-triangle slots)
+void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, int *out_col,
+                   int *slot_row, int *slot_job, int *slot_npair, cudaStream_t st);
+void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
+                  const int *out_col, const int *slot_row, const int *slot_job,
+                  const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st);
+
+// k_numeric.cu: C(upper slot) = c_lin X + c_sq sum(pairs); lower slot = transpose
+struct NumArgs {
+    const double *in_val;
+    const float *in_nrm;
+    const uint16_t *in_hi, *in_lo;
+    const int *pair_a, *pair_b;
+    const int64_t *pair_off;
+    const int *slot_row, *slot_job, *slot_x, *slot_t;
+    const int *work;        // upper slots to process
+    int nwork;
+    const int *sys_of_row;
+    const double *c_lin, *c_sq, *tau0, *tau1;
+    const int *active;
+    int job_tau_sel[kMaxJobs];
+    double *out_val;
+    float *out_nrm;
+    uint8_t *keep;
+    int b;
+};
+void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
+
+// k_compact.cu
+void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot,
+                       int *work, int *nwork, cudaStream_t st);
+void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total,
+                          int *cnt, cudaStream_t st);
+void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,
+                         const float *out_nrm, const uint8_t *keep, const int *new_row_ptr,
+                         int nrows_total, int b, int *new_col, double *new_val,
+                         float *new_nrm, cudaStream_t st);
+
+}  // namespace rdm
