@@ -1,0 +1,383 @@
+"""Benchmark of the response-density-matrix solve on one or more GB300s.
+
+One step = one full solve (Gershgorin bounds, initial matrices, every TC2 /
+first-order iteration with its block-sparse products and truncation, the
+polarizability) of the 2,000-atom random-packed cluster (8 orbitals per atom,
+N = 16,000, 32 x 32 blocks, truncation 1e-6, H1 for x, y and z).  Inputs are
+resident in HBM before the timed region; the working set (X0, X1 for three
+directions, ~1 GB in FP64) is far larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode M] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
+copy of the workload (independent problems, weak scaling, no collective on
+the data path).  ``--impl reference`` times the CPU oracle (dense FP64 TC2)
+on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s per P1 solve (block-SpGEMM TFLOP/s alongside), FP64 vs mixed, at |dalpha|/alpha <= 1e-6"
+WORKLOAD = "cluster-2000-atoms-N16000-b32-tau1e-6-xyz"
+# TC2 iterations of the oracle's stopping rule on this workload, predicted by
+# tests/golden/make_golden.py from the spectrum of H0 (oracle only)
+ORACLE_ITERS_FILE = os.path.join(ROOT, "tests", "golden", "cfg2_oracle.json")
+FP64_PEAK_NOTE = ("GB300 FP64: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
+                  "(nominal 1.25 TFLOP/s)")
+FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.5 TFLOP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default=os.environ.get("RDM_BENCH_MODE", "fp32"))
+    ap.add_argument("--atoms", type=int, default=2000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_iterations():
+    try:
+        with open(ORACLE_ITERS_FILE) as f:
+            return int(json.load(f)["tc2_iterations"])
+    except Exception:
+        return 17
+
+
+def oracle_sample(sys_, reps: int = 1):
+    """Time the oracle's dominant operation on this workload: one dense FP64
+    product X0 X0 of the full N x N matrix (numpy / threaded BLAS), then scale
+    to one solve = (1 + 2 * n_dirs) products per iteration x iterations."""
+    from oracle.tc2 import gershgorin_bounds
+    h0 = sys_.h0.to_dense()
+    lo, hi = gershgorin_bounds(h0)
+    x0 = (hi * np.eye(h0.shape[0]) - h0) / (hi - lo)
+    del h0
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        _ = x0 @ x0
+        times.append(time.perf_counter() - t)
+    iters = oracle_iterations()
+    per_product = min(times)
+    n_prod = 1 + 2 * len(sys_.h1)
+    return per_product, per_product * n_prod * iters, iters, n_prod
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, sys_, rank):
+    if rank != 0:
+        return
+    t_w = []
+    for _ in range(args.warmup):
+        oracle_sample(sys_)
+    vals = []
+    for _ in range(args.steps):
+        per_prod, per_solve, iters, n_prod = oracle_sample(sys_)
+        vals.append(per_solve)
+    v = float(np.mean(vals))
+    sample = (f"one dense FP64 {sys_.n}x{sys_.n} product X0*X0 per step (numpy, threaded BLAS), "
+              f"scaled by {n_prod} products/iteration x {iters} iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": args.atoms, "N": sys_.n, "b": sys_.b, "tau": 1e-6,
+                       "directions": 3},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del t_w
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def to_device(sys_, torch, dev):
+    class M:
+        pass
+
+    def conv(m):
+        o = M()
+        o.nb, o.b, o.n = m.nb, m.b, m.n
+        o.row_ptr = torch.from_numpy(m.row_ptr).to(dev)
+        o.col_idx = torch.from_numpy(m.col_idx).to(dev)
+        o.vals = torch.from_numpy(m.vals).to(dev)
+        return o
+
+    class S:
+        pass
+
+    s = S()
+    s.h0 = conv(sys_.h0)
+    s.h1 = [conv(m) for m in sys_.h1]
+    s.dirs = sys_.dirs
+    s.n_electrons = sys_.n_electrons
+    return s
+
+
+def run_ours(args, sys_, rank, world, torch, dist):
+    from paper_2009_03551_gb300 import rdm
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    dsys = to_device(sys_, torch, dev)
+    torch.cuda.synchronize()
+
+    sol = rdm.Solver(dev.index, stream.cuda_stream)
+    params = dict(tau=1e-6, tol=1e-9, mode=args.mode, max_iter=100)
+    sol.set_params(**params)
+    sol.load(dsys)
+    for _ in range(args.warmup):
+        sol.solve()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        code, info = sol.solve()
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    t_local = ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    s_per_solve = t_max / (args.steps * world)
+    alpha_m = sol.alpha()
+    last = infos[-1]
+    useful = float(np.mean([i.useful_flops for i in infos]))
+    num_ms = float(np.mean([i.kernel_ms[1] for i in infos]))
+    num_launch = int(infos[-1].numeric_launches)
+    launches = int(sum(i.kernel_launches for i in infos))
+
+    # FP64 comparison solve (context for the metric's "FP64 vs mixed")
+    fp64 = None
+    if not args.no_fp64 and args.mode != "fp64":
+        s64 = rdm.Solver(dev.index, stream.cuda_stream)
+        s64.set_params(tau=1e-6, tol=1e-9, mode="fp64", max_iter=100)
+        s64.load(dsys)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        _, i64 = s64.solve()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t64 = a0.elapsed_time(a1) / 1e3
+        alpha64 = s64.alpha()
+        rel = float(np.max(np.abs(alpha_m - alpha64)) / np.max(np.abs(alpha64)))
+        fp64 = {"s_per_solve": t64, "steps": 1, "warmup": 0, "iterations": i64.iterations,
+                "tflops": i64.useful_flops / t64 / 1e12, "alpha_rel_diff_mixed_vs_fp64": rel,
+                "speedup_mixed_vs_fp64": t64 / s_per_solve}
+        s64.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for m in [sys_.h0, *sys_.h1])
+        se = rdm.Solver(dev.index, stream.cuda_stream)
+        se.set_params(**params)
+        se.load(sys_)
+        se.solve()   # warm-up of the host path
+        torch.cuda.synchronize()
+        d2h = 0
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            se.load(sys_)
+            se.solve()
+            d2h = 72
+            for d in range(len(sys_.h1)):
+                p = se.p1(0, d)
+                d2h += p.row_ptr.nbytes + p.col_idx.nbytes + p.vals.nbytes
+            _ = se.alpha()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t) / args.e2e_steps
+        e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        se.close()
+
+    peaks, peak_kind = load_peaks()
+    mode = args.mode
+    if mode == "fp64":
+        peak, bound, unit = 1.26e12, "alu", "TFLOP/s"
+        peak_note = FP64_PEAK_NOTE + " (derived; not in MEASURED_PEAKS.json)"
+    elif mode == "fp32":
+        peak, bound, unit = 80.5e12, "alu", "TFLOP/s"
+        peak_note = FP32_PEAK_NOTE + " (derived; not in MEASURED_PEAKS.json)"
+    else:
+        peak, bound, unit = peaks["bf16_tflops"] * 1e12, "tensor", "TFLOP/s"
+        peak_note = f"bf16 dense, {peak_kind} (MEASURED_PEAKS.json bf16_tflops burst)"
+    achieved = useful / (num_ms / 1e3) if num_ms > 0 else 0.0
+    roofline = {"kernel": "numeric block-SpGEMM + fused truncation", "bound": bound,
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "flops_per_launch": useful / max(num_launch, 1),
+                "avg_launch_ms": num_ms / max(num_launch, 1), "launches_per_solve": num_launch,
+                "peak_source": peak_note,
+                "share_of_solve": num_ms / (s_per_solve * 1e3)}
+
+    line = {"metric": METRIC, "value": s_per_solve, "unit": "s", "higher_is_better": False,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_solve * 1e3,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(mode, "bf16x3+f64"),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": mode, "atoms": args.atoms, "N": sys_.n, "b": sys_.b,
+                       "tau": 1e-6, "tol": 1e-9, "directions": 3, "iterations": last.iterations,
+                       "nnzb_p0": last.nnzb_p0, "nnzb_p1": list(last.nnzb_p1),
+                       "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
+            "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
+            "block_spgemm_tflops": achieved / 1e12,
+            "alpha_diag": [float(alpha_m[k, k]) for k in range(3)],
+            "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
+            "kernel_ms_per_solve": {"symbolic_pairs": float(np.mean([i.kernel_ms[0] for i in infos])),
+                                    "numeric": num_ms,
+                                    "compaction": float(np.mean([i.kernel_ms[2] for i in infos])),
+                                    "other": float(np.mean([i.kernel_ms[3] for i in infos]))},
+            "clocks": clocks}
+    sol.close()
+    return line
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    from synth import make_config
+    sys_ = make_config(2, n_atoms=args.atoms)
+
+    if args.impl == "reference":
+        run_reference(args, sys_, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    from paper_2009_03551_gb300 import build as b
+    if rank == 0 or world == 1:
+        b.build()
+    if dist is not None:
+        dist.barrier()
+    line = run_ours(args, sys_, rank, world, torch, dist)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per_prod, per_solve, iters, n_prod = oracle_sample(sys_)
+        line["cpu_baseline"] = {"value": per_solve, "unit": "s", "cores": cores(), "kind": "oracle",
+                                "sample": f"one dense FP64 {sys_.n}x{sys_.n} product of the oracle's TC2 "
+                                          f"({per_prod:.2f} s), scaled by {n_prod} products x {iters} iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -120,6 +120,14 @@ typedef struct {
     double  time_ms;        /* wall time of the solve on the handle's stream */
     double  useful_flops;   /* 2 b^3 per (i,k,j) block triple, summed over the solve */
     double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
+    double  kernel_ms[4];   /* device time per kernel class (CUDA events on the handle's stream):
+                               0 symbolic + pair lists, 1 numeric products, 2 truncation
+                               compaction, 3 reductions / set-up */
+    int64_t kernel_launches;   /* kernels launched by the solve */
+    int32_t numeric_launches;  /* launches of the numeric product kernels */
+    int32_t pad0;
+    double  numeric_bytes;  /* algorithmic bytes of the numeric launches:
+                               (operand blocks read once + output blocks written) * b^2 * 8 */
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */

@@ -26,6 +26,8 @@
 
 using namespace rdm;
 
+long long rdm::g_kernel_launches = 0;
+
 namespace {
 
 struct HostSys {
@@ -84,6 +86,15 @@ struct rdm_handle {
     DevBuf<uint8_t> keep;
     DevBuf<double> row_lo, row_hi;
     TcWork tcw;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void ensure_events() {
+        for (auto &e : ev)
+            if (!e) RDM_CUDA_TRY(cudaEventCreate(&e));
+    }
+    ~rdm_handle() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 
     // results
     bool solved = false;
@@ -357,6 +368,9 @@ struct StepStats {
     int64_t npairs = 0;
     int64_t nslot = 0;
     double issued = 0;
+    double bytes = 0;
+    double ms[3] = {0, 0, 0};
+    int numeric_launches = 0;
 };
 
 Arith tier_arith(int mode, int tier) {
@@ -377,6 +391,8 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     const int nrows = njob * NB;
     int max_ns = *std::max_element(h->nbs.begin(), h->nbs.end());
     StepStats ss;
+    h->ensure_events();
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
     if (ar != AR_FP64 && ar != AR_FP32) prepare_operands(in, ar, st);
 
     h->row_cnt.ensure(nrows);
@@ -426,14 +442,22 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     d2h(&npairs, h->pair_off.p + nslot, 1, st);
     sync(h);
     ss.npairs = npairs;
-    h->pair_a.ensure(std::max<int64_t>(npairs, 1));
-    h->pair_b.ensure(std::max<int64_t>(npairs, 1));
+    const bool tc = !(ar == AR_FP64 || ar == AR_FP32);
+    if (!tc) {
+        h->pair_a.ensure(std::max<int64_t>(npairs, 1));
+        h->pair_b.ensure(std::max<int64_t>(npairs, 1));
+    }
     h->slot_x.ensure(std::max<int64_t>(nslot, 1));
     h->slot_t.ensure(std::max<int64_t>(nslot, 1));
     launch_pairs(in, jt, h->sd, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p, h->pair_off.p,
-                 nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st);
+                 nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st,
+                 tc ? 0 : 1);
     h->work.ensure(std::max<int64_t>(nslot, 1));
-    launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st);
+    // tensor-core path: the SIMT kernel only copies the blocks of converged systems
+    launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
+                      h->sd.active.p, tc ? 1 : 0);
+    TcPlan plan{};
+    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, st);
     int hc[2];
     d2h(hc, h->counters.p + 2, 2, st);
     sync(h);
@@ -453,12 +477,19 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     a.active = h->sd.active.p;
     for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
     a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p; a.b = b;
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
+    const long long l0 = g_kernel_launches;
     if (ar == AR_FP64 || ar == AR_FP32) {
         launch_numeric_simt(a, ar, st);
         ss.issued = (double)npairs * 2.0 * b * b * b;
+        ss.bytes = ((double)in.total * 8.0 + (double)nslot * 8.0) * (double)bb;
     } else {
-        ss.issued = launch_numeric_tc(a, in, ar, h->tcw, NB, st);
+        ss.issued = launch_numeric_tc(a, in, ar, h->tcw, NB, plan, st);
+        ss.bytes = ((double)in.total * 4.0 + (double)nslot * 8.0) * (double)bb;
+        if (nwork) launch_numeric_simt(a, AR_FP32, st);   // copies of converged systems
     }
+    ss.numeric_launches = (int)(g_kernel_launches - l0);
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[2], st));
 
     // compaction
     h->cnt_rows.ensure(nrows + 1);
@@ -467,16 +498,29 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     scan_exclusive_i32(h->cnt_rows.p, out.row_ptr.p, nrows, h->scan_tmp32.p, st);
     int kept = 0;
     d2h(&kept, out.row_ptr.p + nrows, 1, st);
+    int tc_err = 0;
+    if (tc) d2h(&tc_err, h->tcw.counters.p, 1, st);
     sync(h);
+    if (tc_err)
+        throw Error{tc_err & 1 ? RDM_ETIMEOUT : RDM_ECUDA,
+                    "tensor-core product kernel failed (code " + std::to_string(tc_err) + ")"};
     out.col.ensure(std::max(kept, 1));
     out.val.ensure((size_t)std::max(kept, 1) * bb);
     out.nrm.ensure(std::max(kept, 1));
     launch_compact_copy(h->out_rp.p, mcol, h->out_val.p, h->out_nrm.p, h->keep.p,
                         out.row_ptr.p, nrows, b, out.col.p, out.val.p, out.nrm.p, st);
     out.total = kept;
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[3], st));
     std::vector<int> rp(nrows + 1);
     d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
     sync(h);
+    float m01 = 0, m12 = 0, m23 = 0;
+    cudaEventElapsedTime(&m01, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&m12, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);
+    ss.ms[0] = m01;
+    ss.ms[1] = m12;
+    ss.ms[2] = m23;
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -508,6 +552,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     DeviceGuard dg(h->device);
     if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
     auto t_start = std::chrono::steady_clock::now();
+    const long long launches0 = g_kernel_launches;
     assemble(h);
     const int S = h->S, NB = h->NB, nd = h->nd, b = h->b;
     const rdm_params &P = h->prm;
@@ -550,7 +595,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     JobTable jt = solve_jobs(nd);
     std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
     std::vector<int> act(S);
-    double useful = 0, issued = 0;
+    double useful = 0, issued = 0, nbytes = 0;
+    double kms[3] = {0, 0, 0};
+    int num_launches = 0;
     cudaEvent_t ev0, ev1;
     RDM_CUDA_TRY(cudaEventCreate(&ev0));
     RDM_CUDA_TRY(cudaEventCreate(&ev1));
@@ -667,6 +714,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         cudaEventElapsedTime(&ms, ev0, ev1);
         useful += (double)sst.npairs * 2.0 * b * b * b;
         issued += sst.issued;
+        nbytes += sst.bytes;
+        num_launches += sst.numeric_launches;
+        for (int k = 0; k < 3; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
             if (act[s]) {
@@ -734,6 +784,11 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.time_ms = wall_ms;
         I.useful_flops = useful;
         I.issued_flops = issued;
+        for (int k = 0; k < 3; ++k) I.kernel_ms[k] = kms[k];
+        I.kernel_ms[3] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2]);
+        I.kernel_launches = g_kernel_launches - launches0;
+        I.numeric_launches = num_launches;
+        I.numeric_bytes = nbytes;
     }
     // band energy of the result: recompute the stats of the final X
     q = stats(h, Xf);

@@ -11,10 +11,12 @@ namespace {
 // ballot-ordered, block-level offsets through one atomic per warp; the order
 // of the list does not affect results)
 __global__ void k_build_work(const int *__restrict__ slot_row, const int *__restrict__ out_col,
-                             int64_t nslot, int *work, int *nwork) {
+                             int64_t nslot, int *work, int *nwork, const int *__restrict__ sys_of_row,
+                             const int *__restrict__ active, int only_inactive) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lane = threadIdx.x & 31;
     bool up = s < nslot && out_col[s] >= slot_row[s];
+    if (up && only_inactive) up = !active[sys_of_row[slot_row[s]]];
     unsigned m = __ballot_sync(0xffffffffu, up);
     int base = 0;
     if (lane == 0 && m) base = atomicAdd(nwork, __popc(m));
@@ -70,10 +72,12 @@ __global__ void k_compact_copy(const int *__restrict__ rp, const int *__restrict
 }  // namespace
 
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot, int *work,
-                       int *nwork, cudaStream_t st) {
+                       int *nwork, cudaStream_t st, const int *sys_of_row, const int *active,
+                       int only_inactive) {
     if (nslot == 0) return;
     int64_t grid = (nslot + 255) / 256;
-    k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, nslot, work, nwork);
+    k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, nslot, work, nwork, sys_of_row,
+                                                 active, only_inactive);
     RDM_LAUNCH_CHECK();
 }
 

@@ -1,17 +1,611 @@
-// Tensor-core numeric phase (tcgen05, sm_103a).
+// Tensor-core numeric phase (tcgen05 + TMEM, sm_103a) for 32 x 32 blocks.
+//
+// Work decomposition.  Output blocks are grouped in 128 x 128 super-tiles
+// (block rows 4I..4I+3 x block columns 4J..4J+3, J >= I).  A super-tile is
+// one MMA accumulator: D[128 x 128] = sum over K-steps of A[128 x 32] B[128 x 32]^T
+// where a K-step is one block index k at which some row of the tile's A rows
+// and some row of its B rows have a stored block (Gustavson's row merge,
+// Algorithm 1, lifted to a 4 x 4 block tile).  Missing blocks are zero.  The
+// X1 products (X0 X1 + X1 X0) simply concatenate the K-steps of both terms.
+//
+// Split precision.  Every operand block is stored as a hi and a lo plane
+// (bf16 or fp16, hi = rn(x), lo = rn(x - hi)); one K-step issues the products
+// hi*hi + hi*lo + lo*hi (2 MMAs of K = 16 each), all accumulated in FP32 in
+// tensor memory.  The operand planes are laid out in global memory in the
+// canonical K-major core-matrix order of the MMA (8 rows x 16 bytes per core
+// matrix, core matrices adjacent along K 128 bytes apart, 8-row groups 512
+// bytes apart), so one 2 KB bulk copy per block lands ready for the MMA.
+//
+// Warp roles (192 threads, one CTA per SM, persistent over a static tile
+// schedule): warp 0 issues the bulk copies into a 4-stage ring, warp 1 owns
+// the tensor-memory allocation and one thread issues the MMAs, warps 2-5
+// (one per TMEM lane quarter = one block row of the tile) run the epilogue:
+// C = c_lin X + c_sq D, diagonal blocks symmetrised, block Frobenius norm,
+// truncation flag, FP64 store of the block and of its transpose.  The
+// accumulator is double-buffered in TMEM (2 x 128 columns) so the epilogue of
+// one tile overlaps the MMAs of the next.  Every mbarrier wait is bounded: on
+// timeout the kernel raises an error flag, drains what it issued and frees its
+// tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "tc_gemm.cuh"
 
 namespace rdm {
+namespace {
+
+constexpr int TB = 32;                       // block size handled here
+constexpr int TBL = 4;                       // blocks per tile edge
+constexpr int kStages = 4;
+constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
+constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
+constexpr int kTilePlaneBytes = TBL * kPlaneBytes;      // 8 KB: 4 blocks stacked
+constexpr int kStageBytes = 4 * kTilePlaneBytes;        // A_hi, A_lo, B_hi, B_lo
+constexpr int kThreads = 192;
+constexpr int kTileInts = 20;                // p, I, J, nsteps, slot[16]
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    // K-major, no swizzle; version 1 (tcgen05) in bits 46-47
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// ---------------------------------------------------------------------------
+// operand planes: hi/lo split in the K-major core-matrix layout
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int core_offset(int r, int c) {
+    // element (r, c) of a 32 x 32 block: core matrix (r/8, c/8) at 64-element
+    // granularity, 4 core matrices per 8-row group
+    return (((r >> 3) * 4 + (c >> 3)) << 6) + ((r & 7) << 3) + (c & 7);
+}
+
+template <bool BF16>
+__global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
+                               uint16_t *__restrict__ lo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = nblk * kPlaneElems;
+    if (e >= n) return;
+    int64_t p = e / kPlaneElems;
+    int rc = (int)(e % kPlaneElems);
+    float x = (float)val[e];
+    uint16_t h, l;
+    if (BF16) {
+        __nv_bfloat16 bh = __float2bfloat16_rn(x);
+        __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
+        h = __bfloat16_as_ushort(bh);
+        l = __bfloat16_as_ushort(bl);
+    } else {
+        __half hh = __float2half_rn(x);
+        __half hl = __float2half_rn(x - __half2float(hh));
+        h = __half_as_ushort(hh);
+        l = __half_as_ushort(hl);
+    }
+    int64_t o = p * kPlaneElems + core_offset(rc >> 5, rc & 31);
+    hi[o] = h;
+    lo[o] = l;
+}
+
+// ---------------------------------------------------------------------------
+// tile lists
+// ---------------------------------------------------------------------------
+struct TileBuild {
+    const int *rp;       // input set row_ptr (flat)
+    const int *col;
+    int NB, NB4;
+    JobTable jt;
+    const int *out_rp;   // mask row_ptr (flat, njob*NB+1)
+    const int *mcol;     // mask columns
+    const int *sys_of_row, *active;
+    int *tile_cnt;       // [njob*NB4]
+    const int *tile_off; // scanned
+    int *tiles;          // [ntile * kTileInts]
+    int *step_cnt;       // [ntile]
+    const int64_t *step_off;
+    int *steps;          // [nsteps * 8]
+    int ntile;
+};
+
+// one thread per (job, super-row): the union of super-columns J of the upper
+// mask blocks in block rows 4I..4I+3 (count or fill)
+__global__ void k_tile_rows(TileBuild T, int fill) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int njob = T.jt.njob;
+    if (t >= njob * T.NB4) return;
+    int p = t / T.NB4, I = t % T.NB4;
+    int cur[TBL], end[TBL];
+    for (int m = 0; m < TBL; ++m) {
+        int i = 4 * I + m;
+        cur[m] = end[m] = 0;
+        if (i >= T.NB) continue;
+        int lo = T.out_rp[p * T.NB + i], hi = T.out_rp[p * T.NB + i + 1];
+        // first column >= i (upper triangle)
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (T.mcol[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        cur[m] = lo;
+        end[m] = T.out_rp[p * T.NB + i + 1];
+        // converged systems keep their blocks through the copy path of the
+        // numeric phase; their rows produce no tiles
+        if (!T.active[T.sys_of_row[i]]) cur[m] = end[m];
+    }
+    int n = 0;
+    int base = fill ? T.tile_off[t] : 0;
+    while (true) {
+        int jmin = 0x7fffffff;
+        for (int m = 0; m < TBL; ++m)
+            if (cur[m] < end[m]) jmin = min(jmin, T.mcol[cur[m]] >> 2);
+        if (jmin == 0x7fffffff) break;
+        if (fill) {
+            int *d = T.tiles + (size_t)(base + n) * kTileInts;
+            d[0] = p; d[1] = I; d[2] = jmin; d[3] = 0;
+            for (int q = 0; q < 16; ++q) d[4 + q] = -1;
+            for (int m = 0; m < TBL; ++m)
+                while (cur[m] < end[m] && (T.mcol[cur[m]] >> 2) == jmin) {
+                    d[4 + m * 4 + (T.mcol[cur[m]] & 3)] = cur[m];
+                    ++cur[m];
+                }
+        } else {
+            for (int m = 0; m < TBL; ++m)
+                while (cur[m] < end[m] && (T.mcol[cur[m]] >> 2) == jmin) ++cur[m];
+        }
+        ++n;
+    }
+    if (!fill) T.tile_cnt[t] = n;
+}
+
+// one thread per tile: K-steps = union over the tile's A rows intersected with
+// the union over its B rows, for each term (count or fill)
+__global__ void k_tile_steps(TileBuild T, int fill) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T.ntile) return;
+    const int *d = T.tiles + (size_t)t * kTileInts;
+    const int p = d[0], I = d[1], J = d[2];
+    const Job &job = T.jt.job[p];
+    int64_t w = fill ? T.step_off[t] : 0;
+    int n = 0;
+    for (int term = 0; term < job.nterm; ++term) {
+        const int am = job.a[term], bm = job.b[term];
+        int cur[2 * TBL], end[2 * TBL];
+        for (int q = 0; q < TBL; ++q) {
+            int i = 4 * I + q, j = 4 * J + q;
+            cur[q] = end[q] = 0;
+            cur[TBL + q] = end[TBL + q] = 0;
+            if (i < T.NB) { cur[q] = T.rp[am * T.NB + i]; end[q] = T.rp[am * T.NB + i + 1]; }
+            if (j < T.NB) { cur[TBL + q] = T.rp[bm * T.NB + j]; end[TBL + q] = T.rp[bm * T.NB + j + 1]; }
+        }
+        while (true) {
+            int kmin = 0x7fffffff;
+            for (int q = 0; q < 2 * TBL; ++q)
+                if (cur[q] < end[q]) kmin = min(kmin, T.col[cur[q]]);
+            if (kmin == 0x7fffffff) break;
+            bool anyA = false, anyB = false;
+            int idx[2 * TBL];
+            for (int q = 0; q < 2 * TBL; ++q) {
+                idx[q] = -1;
+                if (cur[q] < end[q] && T.col[cur[q]] == kmin) {
+                    idx[q] = cur[q];
+                    ++cur[q];
+                    if (q < TBL) anyA = true; else anyB = true;
+                }
+            }
+            if (anyA && anyB) {
+                if (fill && w + n < T.step_off[t + 1]) {
+                    int *s = T.steps + (size_t)(w + n) * 8;
+                    for (int q = 0; q < 8; ++q) s[q] = idx[q];
+                }
+                ++n;
+            }
+        }
+    }
+    if (!fill) T.step_cnt[t] = n;
+    else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
+}
+
+__global__ void k_set_nsteps(int *tiles, const int *step_cnt, int ntile) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntile) tiles[(size_t)t * kTileInts + 3] = step_cnt[t];
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core product kernel
+// ---------------------------------------------------------------------------
+struct TcArgs {
+    const uint16_t *hi, *lo;      // operand planes of the input set
+    const uint16_t *zero;         // one zero plane
+    const int *tiles;
+    const int64_t *step_off;
+    const int *steps;
+    int ntile;
+    uint32_t idesc;
+    // epilogue
+    const double *in_val;
+    const int *slot_row, *slot_job, *slot_x, *slot_t;
+    const int *sys_of_row;
+    const double *c_lin, *c_sq, *tau0, *tau1;
+    int job_tau_sel[kMaxJobs];
+    double *out_val;
+    float *out_nrm;
+    uint8_t *keep;
+    int *err;
+};
+
+struct __align__(8) SmemCtl {
+    uint64_t full[kStages], empty[kStages];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *stages = smem_raw;                                       // kStages * 32 KB
+    float *stage_ep = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes);   // 4 warps x 32 x 33
+    double *stage_x = reinterpret_cast<double *>(stage_ep + 4 * 32 * 33);           // 4 warps x 32 x 33
+    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_x + 4 * 32 * 33);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abort_flag = &ctl->abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->acc_full[b], 1); mbar_init(&ctl->acc_empty[b], 4); }
+        mbar_init(&ctl->drain, 1);
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&ctl->tmem_base)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ---------------- producer: bulk copies of the operand blocks ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
+                const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
+                for (int64_t q = s0; q < s1; ++q, ++it) {
+                    const int st = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1;
+                    if (!mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag)) break;
+                    mbar_expect_tx(&ctl->full[st], kStageBytes);
+                    uint8_t *dst = stages + st * kStageBytes;
+                    const int *ix = A.steps + q * 8;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int b = ix[m];
+                        const uint16_t *h = b >= 0 ? A.hi + (size_t)b * kPlaneElems : A.zero;
+                        const uint16_t *l = b >= 0 ? A.lo + (size_t)b * kPlaneElems : A.zero;
+                        // A planes: [0, 8K) hi, [8K, 16K) lo; B planes: [16K, 24K) hi, [24K, 32K) lo
+                        const int side = m >> 2, r = m & 3;
+                        bulk_g2s(dst + side * 2 * kTilePlaneBytes + r * kPlaneBytes, h, kPlaneBytes, &ctl->full[st]);
+                        bulk_g2s(dst + side * 2 * kTilePlaneBytes + kTilePlaneBytes + r * kPlaneBytes, l, kPlaneBytes,
+                                 &ctl->full[st]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t it = 0, lt = 0;
+            bool issued = false;
+            for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                const uint32_t use = lt >> 1;
+                if (!mbar_wait(&ctl->acc_empty[buf], (use & 1) ^ 1, abort_flag)) break;
+                fence_after();
+                const uint32_t d_tmem = tmem + buf * 128;
+                const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
+                bool ok = true;
+                for (int64_t q = s0; q < s1; ++q, ++it) {
+                    const int st = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1;
+                    if (!mbar_wait(&ctl->full[st], ph, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t base = smem_u32(stages + st * kStageBytes);
+                    const uint32_t a_hi = base, a_lo = base + kTilePlaneBytes;
+                    const uint32_t b_hi = base + 2 * kTilePlaneBytes, b_lo = base + 3 * kTilePlaneBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t ko = kk * 256;
+                        const uint32_t first = (q == s0 && kk == 0) ? 0u : 1u;
+                        mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, first);
+                        mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_lo + ko, 128, 512), A.idesc, 1u);
+                        mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, 1u);
+                    }
+                    issued = true;
+                    mma_commit(&ctl->empty[st]);
+                }
+                if (!ok) break;
+                if (s1 > s0) mma_commit(&ctl->acc_full[buf]);
+                else mbar_arrive(&ctl->acc_full[buf]);
+            }
+            if (*abort_flag && issued) {
+                // drain: wait (bounded) until every MMA this thread issued has completed
+                mma_commit(&ctl->drain);
+                long long t0 = clock64();
+                while (!mbar_try_wait(&ctl->drain, 0) && clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quarter = block row ----------------
+        const int eq = warp & 3;                       // lanes 32*eq .. 32*eq+31
+        float *S = stage_ep + (warp - 2) * 32 * 33;
+        double *SX = stage_x + (warp - 2) * 32 * 33;
+        uint32_t lt = 0;
+        for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            const uint32_t use = lt >> 1;
+            if (!mbar_wait(&ctl->acc_full[buf], use & 1, abort_flag)) break;
+            fence_after();
+            const int *d = A.tiles + (size_t)t * kTileInts;
+            const int nst = d[3];
+            if (nst < 0 && lane == 0) atomicOr(A.err, 4);
+            for (int n = 0; n < TBL; ++n) {
+                const int s = d[4 + eq * 4 + n];
+                if (s < 0) continue;
+                float acc[32];
+                __syncwarp();
+                if (nst > 0) tmem_ld32(tmem + ((uint32_t)(32 * eq) << 16) + buf * 128 + n * 32, acc);
+                else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+                }
+                const int i = A.slot_row[s];
+                const int sys = A.sys_of_row[i];
+                const int job = A.slot_job[s];
+                const float cl = (float)A.c_lin[sys], cq = (float)A.c_sq[sys];
+                const double tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
+                const int sx = A.slot_x[s], stt = A.slot_t[s];
+                const bool diag = (stt == s);
+                // linear term: stage X_old coalesced, each lane then owns its row
+                if (sx >= 0 && cl != 0.f) {
+                    const double *gx = A.in_val + (size_t)sx * kPlaneElems;
+                    for (int r = 0; r < 32; ++r) SX[r * 33 + lane] = gx[r * 32 + lane];
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] = fmaf(cl, (float)SX[lane * 33 + c], cq * acc[c]);
+                    __syncwarp();
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] = cq * acc[c];
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
+                __syncwarp();
+                if (diag) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] = 0.5f * (S[lane * 33 + c] + S[c * 33 + lane]);
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
+                    __syncwarp();
+                }
+                float ss = 0.f;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) ss = fmaf(acc[c], acc[c], ss);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
+                const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
+                double *o = A.out_val + (size_t)s * kPlaneElems;
+                for (int r = 0; r < 32; ++r) o[r * 32 + lane] = (double)S[r * 33 + lane];
+                if (!diag) {
+                    double *ot = A.out_val + (size_t)stt * kPlaneElems;
+                    for (int r = 0; r < 32; ++r) ot[r * 32 + lane] = (double)S[lane * 33 + r];
+                }
+                if (lane == 0) {
+                    A.out_nrm[s] = nrm;
+                    A.keep[s] = kp;
+                    if (!diag) { A.out_nrm[stt] = nrm; A.keep[stt] = kp; }
+                }
+                __syncwarp();
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->acc_empty[buf]);
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && ctl->abort_flag) atomicOr(A.err, 1);
+    if (warp == 1) {
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 4 * 32 * 33 * sizeof(float) +
+                              4 * 32 * 33 * sizeof(double) + sizeof(SmemCtl) + 1024;
+
+}  // namespace
 
 void prepare_operands(MatSet &in, Arith ar, cudaStream_t st) {
-    (void)in; (void)ar; (void)st;
-    throw Error{-1, "tensor-core arithmetic is not available in this build"};
+    if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
+    const int64_t n = in.total * kPlaneElems;
+    in.ophi.ensure(std::max<int64_t>(n, 1));
+    in.oplo.ensure(std::max<int64_t>(n, 1));
+    if (n == 0) return;
+    const int64_t grid = (n + 255) / 256;
+    if (ar == AR_BF16X3) k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p);
+    else if (ar == AR_FP16X3) k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p);
+    else throw Error{-1, "tensor-core arithmetic not available"};
+    RDM_LAUNCH_CHECK();
 }
 
 double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w, int NB,
-                         cudaStream_t st) {
-    (void)a; (void)in; (void)ar; (void)w; (void)NB; (void)st;
-    throw Error{-1, "tensor-core arithmetic is not available in this build"};
+                         const TcPlan &plan, cudaStream_t st) {
+    if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
+    if (plan.ntile == 0) return 0.0;
+    if (!w.zero.p) {
+        w.zero.ensure(kPlaneElems);
+        RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, kPlaneElems * sizeof(uint16_t), st));
+    }
+    TcArgs A{};
+    A.hi = in.ophi.p; A.lo = in.oplo.p; A.zero = w.zero.p;
+    A.tiles = w.tiles.p; A.step_off = w.step_off.p; A.steps = w.steps.p; A.ntile = plan.ntile;
+    // kind::f16: D = F32 (bit 4), A/B = BF16 (1) or F16 (0), K-major, N = 128, M = 128
+    const uint32_t ab = ar == AR_BF16X3 ? 1u : 0u;
+    A.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    A.in_val = a.in_val; A.slot_row = a.slot_row; A.slot_job = a.slot_job; A.slot_x = a.slot_x;
+    A.slot_t = a.slot_t; A.sys_of_row = a.sys_of_row; A.c_lin = a.c_lin; A.c_sq = a.c_sq;
+    A.tau0 = a.tau0; A.tau1 = a.tau1;
+    for (int p = 0; p < kMaxJobs; ++p) A.job_tau_sel[p] = a.job_tau_sel[p];
+    A.out_val = a.out_val; A.out_nrm = a.out_nrm; A.keep = a.keep; A.err = w.counters.p;
+    static bool attr = false;
+    if (!attr) {
+        RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+        attr = true;
+    }
+    int dev = 0, nsm = 0;
+    RDM_CUDA_TRY(cudaGetDevice(&dev));
+    RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = plan.ntile < nsm ? plan.ntile : nsm;
+    k_tc_bf16x3<<<grid, kThreads, kSmemBytes, st>>>(A);
+    RDM_LAUNCH_CHECK();
+    (void)NB;
+    return (double)plan.nsteps * 3.0 * 2.0 * 128.0 * 128.0 * 32.0;
+}
+
+TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
+                     const int *mcol, TcWork &w, cudaStream_t st) {
+    TcPlan plan{};
+    const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL, njob = jt.njob;
+    const int nrow4 = njob * NB4;
+    w.counters.ensure(8);
+    RDM_CUDA_TRY(cudaMemsetAsync(w.counters.p, 0, 8 * sizeof(int), st));
+    w.tile_cnt.ensure(nrow4 + 1);
+    w.tile_off.ensure(nrow4 + 1);
+    w.scan32.ensure(scan_tmp_elems(nrow4 + 1));
+    TileBuild T{};
+    T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NB4 = NB4; T.jt = jt;
+    T.out_rp = out_rp; T.mcol = mcol; T.sys_of_row = sd.sys_of_row.p; T.active = sd.active.p;
+    T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
+    k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 0);
+    RDM_LAUNCH_CHECK();
+    scan_exclusive_i32(w.tile_cnt.p, w.tile_off.p, nrow4, w.scan32.p, st);
+    int ntile = 0;
+    RDM_CUDA_TRY(cudaMemcpyAsync(&ntile, w.tile_off.p + nrow4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RDM_CUDA_TRY(cudaStreamSynchronize(st));
+    plan.ntile = ntile;
+    if (ntile == 0) return plan;
+    w.tiles.ensure((size_t)ntile * kTileInts);
+    T.tiles = w.tiles.p;
+    k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 1);
+    RDM_LAUNCH_CHECK();
+    w.step_cnt.ensure(ntile + 1);
+    w.step_off.ensure(ntile + 1);
+    w.scan64.ensure(scan_tmp_elems(ntile + 1));
+    T.ntile = ntile;
+    T.step_cnt = w.step_cnt.p;
+    k_tile_steps<<<(ntile + 127) / 128, 128, 0, st>>>(T, 0);
+    RDM_LAUNCH_CHECK();
+    scan_exclusive_i64(w.step_cnt.p, w.step_off.p, ntile, w.scan64.p, st);
+    int64_t nsteps = 0;
+    RDM_CUDA_TRY(cudaMemcpyAsync(&nsteps, w.step_off.p + ntile, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RDM_CUDA_TRY(cudaStreamSynchronize(st));
+    plan.nsteps = nsteps;
+    w.steps.ensure(std::max<int64_t>(nsteps, 1) * 8);
+    T.step_off = w.step_off.p;
+    T.steps = w.steps.p;
+    k_set_nsteps<<<(ntile + 127) / 128, 128, 0, st>>>(w.tiles.p, w.step_cnt.p, ntile);
+    RDM_LAUNCH_CHECK();
+    k_tile_steps<<<(ntile + 127) / 128, 128, 0, st>>>(T, 1);
+    RDM_LAUNCH_CHECK();
+    return plan;
 }
 
 }  // namespace rdm

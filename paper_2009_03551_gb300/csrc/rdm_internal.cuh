@@ -41,7 +41,14 @@ struct Error {
                                std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
     } while (0)
 
-#define RDM_LAUNCH_CHECK() RDM_CUDA_TRY(cudaGetLastError())
+// every kernel launch of the library goes through RDM_LAUNCH_CHECK, which
+// also counts it (the count is reported per solve in rdm_info)
+extern long long g_kernel_launches;
+#define RDM_LAUNCH_CHECK()                      \
+    do {                                        \
+        ++::rdm::g_kernel_launches;             \
+        RDM_CUDA_TRY(cudaGetLastError());       \
+    } while (0)
 
 // grow-only device buffer (capacity is kept across iterations and solves)
 template <class T>
@@ -190,7 +197,7 @@ void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, i
 void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
                   const int *out_col, const int *slot_row, const int *slot_job,
                   const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
-                  int *slot_x, int *slot_t, int *err, cudaStream_t st);
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st, int fill = 1);
 
 // k_numeric.cu: C(upper slot) = c_lin X + c_sq sum(pairs); lower slot = transpose
 struct NumArgs {
@@ -214,8 +221,10 @@ struct NumArgs {
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
 
 // k_compact.cu
+// only_inactive = 1: keep only the slots of converged systems (copied blocks)
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot,
-                       int *work, int *nwork, cudaStream_t st);
+                       int *work, int *nwork, cudaStream_t st, const int *sys_of_row = nullptr,
+                       const int *active = nullptr, int only_inactive = 0);
 void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total,
                           int *cnt, cudaStream_t st);
 void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,

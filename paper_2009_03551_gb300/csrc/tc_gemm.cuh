@@ -5,23 +5,36 @@
 
 namespace rdm {
 
-// work buffers of the tensor-core path (tile lists, per-tile step lists)
+// work buffers of the tensor-core path (tile lists, per-tile K-step lists)
 struct TcWork {
-    DevBuf<int> tiles;        // per tile: descriptor ints
-    DevBuf<int> steps;        // per tile step: operand block indices
-    DevBuf<int> counters;
+    DevBuf<uint16_t> zero;      // one zero operand plane
+    DevBuf<int> tiles;          // per tile: job, I, J, nsteps, slot[16]
+    DevBuf<int> tile_cnt, tile_off;
+    DevBuf<int> step_cnt;
     DevBuf<int64_t> step_off;
+    DevBuf<int> steps;          // per K-step: 4 A block indices, 4 B block indices (-1 = zero)
+    DevBuf<int> counters;       // [0]: error bits of the product kernel
     DevBuf<int> scan32;
     DevBuf<int64_t> scan64;
 };
 
-// Convert the FP64 master values of `in` into the operand planes of
-// arithmetic `ar` (hi/lo halves in the shared-memory layout of the MMA).
+struct TcPlan {
+    int ntile;
+    int64_t nsteps;
+};
+
+// Convert the FP64 master values of `in` into hi/lo operand planes of
+// arithmetic `ar` in the K-major core-matrix layout of the MMA.
 void prepare_operands(MatSet &in, Arith ar, cudaStream_t st);
 
-// Numeric phase on the tensor cores; same contract as launch_numeric_simt.
-// Returns the number of flops issued to the tensor cores.
+// Tile lists of one multiplication step from the output mask.
+TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
+                     const int *mcol, TcWork &w, cudaStream_t st);
+
+// Numeric phase on the tensor cores; same output contract as
+// launch_numeric_simt for the slots of active systems.  Returns the flops
+// issued to the tensor cores.
 double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w, int NB,
-                         cudaStream_t st);
+                         const TcPlan &plan, cudaStream_t st);
 
 }  // namespace rdm

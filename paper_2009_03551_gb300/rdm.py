@@ -68,7 +68,9 @@ class rdm_info(C.Structure):
                 ("eps_min", C.c_double), ("eps_max", C.c_double), ("trace_error", C.c_double),
                 ("idempotency", C.c_double), ("band_energy0", C.c_double),
                 ("nnzb_p0", C.c_int64), ("nnzb_p1", C.c_int64 * 3), ("time_ms", C.c_double),
-                ("useful_flops", C.c_double), ("issued_flops", C.c_double)]
+                ("useful_flops", C.c_double), ("issued_flops", C.c_double),
+                ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64),
+                ("numeric_launches", C.c_int32), ("pad0", C.c_int32), ("numeric_bytes", C.c_double)]
 
 
 class rdm_iter_log(C.Structure):
