@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default=os.environ.get("RDM_BENCH_MODE", "fp32"))
+    ap.add_argument("--mode", default=os.environ.get("RDM_BENCH_MODE", "mixed_fp16"),
+                    choices=["fp64", "fp32", "mixed_bf16", "mixed_fp16"])
     ap.add_argument("--atoms", type=int, default=2000)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -254,8 +255,8 @@ def run_ours(args, sys_, rank, world, torch, dist):
     alpha_m = sol.alpha()
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
-    num_ms = float(np.mean([i.kernel_ms[1] for i in infos]))
-    num_launch = int(infos[-1].numeric_launches)
+    kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(6)]
+    kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(2)]
     launches = int(sum(i.kernel_launches for i in infos))
 
     # FP64 comparison solve (context for the metric's "FP64 vs mixed")
@@ -305,40 +306,52 @@ def run_ours(args, sys_, rank, world, torch, dist):
 
     peaks, peak_kind = load_peaks()
     mode = args.mode
-    if mode == "fp64":
-        peak, bound, unit = 1.26e12, "alu", "TFLOP/s"
-        peak_note = FP64_PEAK_NOTE + " (derived; not in MEASURED_PEAKS.json)"
-    elif mode == "fp32":
-        peak, bound, unit = 80.5e12, "alu", "TFLOP/s"
-        peak_note = FP32_PEAK_NOTE + " (derived; not in MEASURED_PEAKS.json)"
+    # dominant kernel of the solve (by device time): the tensor-core product
+    # kernel or the CUDA-core (FP64 / FP32) product kernel
+    tc_ms, simt_ms = kms[1], kms[2]
+    if tc_ms >= simt_ms:
+        kname, k_ms, k_fl, k_launch = "k_tc_bf16x3 (tcgen05 split-precision block SpGEMM + fused truncation)", \
+            tc_ms, kfl[0], int(last.tc_launches)
+        # a split product issues 3 MMAs per useful product: the tensor peak for
+        # useful flops is a third of the dense bf16/fp16 peak
+        peak = peaks["bf16_tflops"] * 1e12 / 3.0
+        bound, peak_note = "tensor", (f"measured bf16 dense burst / 3 split products ({peak_kind}, "
+                                      "MEASURED_PEAKS.json bf16_tflops; fp16 has the same nominal rate)")
     else:
-        peak, bound, unit = peaks["bf16_tflops"] * 1e12, "tensor", "TFLOP/s"
-        peak_note = f"bf16 dense, {peak_kind} (MEASURED_PEAKS.json bf16_tflops burst)"
-    achieved = useful / (num_ms / 1e3) if num_ms > 0 else 0.0
-    roofline = {"kernel": "numeric block-SpGEMM + fused truncation", "bound": bound,
-                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
-                "frac": achieved / peak if peak else None, "traffic": None,
-                "flops_per_launch": useful / max(num_launch, 1),
-                "avg_launch_ms": num_ms / max(num_launch, 1), "launches_per_solve": num_launch,
-                "peak_source": peak_note,
-                "share_of_solve": num_ms / (s_per_solve * 1e3)}
+        kname, k_ms, k_fl, k_launch = "k_numeric_simt (CUDA-core block SpGEMM + fused truncation)", \
+            simt_ms, kfl[1], int(last.simt_launches)
+        fp64_like = mode in ("fp64", "mixed_bf16", "mixed_fp16")
+        peak = 1.26e12 if fp64_like else 80.5e12
+        bound = "alu"
+        peak_note = (FP64_PEAK_NOTE if fp64_like else FP32_PEAK_NOTE) + " (derived from unit counts and clock)"
+    achieved = k_fl / (k_ms / 1e3) if k_ms > 0 else 0.0
+    roofline = {"kernel": kname, "bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                "flops_per_launch": k_fl / max(k_launch, 1), "avg_launch_ms": k_ms / max(k_launch, 1),
+                "launches_per_solve": k_launch, "peak_source": peak_note,
+                "share_of_solve": k_ms / (s_per_solve * 1e3)}
+    num_ms = tc_ms + simt_ms
+    achieved_all = useful / (num_ms / 1e3) if num_ms > 0 else 0.0
 
     line = {"metric": METRIC, "value": s_per_solve, "unit": "s", "higher_is_better": False,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_solve * 1e3,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(mode, "bf16x3+f64"),
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed_bf16": "bf16x3+f64",
+                                                                "mixed_fp16": "fp16x3+f64"}[mode],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": mode, "atoms": args.atoms, "N": sys_.n, "b": sys_.b,
                        "tau": 1e-6, "tol": 1e-9, "directions": 3, "iterations": last.iterations,
                        "nnzb_p0": last.nnzb_p0, "nnzb_p1": list(last.nnzb_p1),
                        "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
             "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
-            "block_spgemm_tflops": achieved / 1e12,
+            "block_spgemm_tflops": achieved_all / 1e12,
+            "tensor_core_tflops": kfl[0] / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
+            "cuda_core_tflops": kfl[1] / (simt_ms / 1e3) / 1e12 if simt_ms > 0 else None,
             "alpha_diag": [float(alpha_m[k, k]) for k in range(3)],
             "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
-            "kernel_ms_per_solve": {"symbolic_pairs": float(np.mean([i.kernel_ms[0] for i in infos])),
-                                    "numeric": num_ms,
-                                    "compaction": float(np.mean([i.kernel_ms[2] for i in infos])),
-                                    "other": float(np.mean([i.kernel_ms[3] for i in infos]))},
+            "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
+                                    "cuda_core_products": kms[2], "compaction": kms[3],
+                                    "reductions_setup_host": kms[4]},
+            "tier_iterations": list(last.tier_iters)[:2],
             "clocks": clocks}
     sol.close()
     return line

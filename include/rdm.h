@@ -62,9 +62,18 @@ extern "C" {
 #define RDM_MODE_FP64        0   /* every product in FP64 (CUDA cores) */
 #define RDM_MODE_FP32        1   /* every product in FP32 (CUDA cores), FP64 scalars */
 #define RDM_MODE_MIXED_BF16  2   /* bf16 hi+lo split products on the tensor cores
-                                    (tcgen05, FP32 accumulate), then FP64 refinement */
-#define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands */
-#define RDM_MODE_TF32        4   /* single-pass TF32 tensor-core products (FP32 accumulate) */
+                                    (tcgen05, FP32 accumulate) until the idempotency
+                                    error stalls, then a final tier with X0^2 in FP64
+                                    (CUDA cores) and the first-order products split */
+#define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
+                                    by a power of two into fp16's normal range
+                                    (22-bit products instead of 16-bit) */
+
+/* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
+#define RDM_REFINE_DEFAULT   0   /* FP32 for RDM_MODE_MIXED_FP16, FP64 for RDM_MODE_MIXED_BF16 */
+#define RDM_REFINE_FP64      1
+#define RDM_REFINE_SPLIT     2   /* keep the tensor-core split product */
+#define RDM_REFINE_FP32      3   /* FP32 on the CUDA cores (round-to-nearest accumulation) */
 
 typedef struct rdm_handle rdm_handle;
 
@@ -103,7 +112,9 @@ typedef struct {
     int32_t min_iter;       /* never stop before this many iterations */
     int32_t use_graphs;     /* 1: capture the iteration in CUDA graphs when possible */
     int32_t verbose;        /* 1: per-iteration log to stderr */
-    int32_t reserved[5];
+    int32_t refine_x1;      /* mixed modes, final tier, arithmetic of the first-order products
+                               (RDM_REFINE_*); X0^2 is always FP64 there */
+    int32_t reserved[4];
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -120,14 +131,19 @@ typedef struct {
     double  time_ms;        /* wall time of the solve on the handle's stream */
     double  useful_flops;   /* 2 b^3 per (i,k,j) block triple, summed over the solve */
     double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
-    double  kernel_ms[4];   /* device time per kernel class (CUDA events on the handle's stream):
-                               0 symbolic + pair lists, 1 numeric products, 2 truncation
-                               compaction, 3 reductions / set-up */
+    double  kernel_ms[6];   /* device time per kernel class (CUDA events on the handle's stream):
+                               0 symbolic mask + pair / tile lists, 1 tensor-core products,
+                               2 CUDA-core products (FP64 / FP32, and copies of converged
+                               systems), 3 truncation compaction, 4 reductions and set-up
+                               (the remainder of the solve), 5 reserved */
+    double  kernel_flops[2];   /* useful flops (2 b^3 per block triple) of the tensor-core (0)
+                                  and CUDA-core (1) product launches */
     int64_t kernel_launches;   /* kernels launched by the solve */
-    int32_t numeric_launches;  /* launches of the numeric product kernels */
-    int32_t pad0;
-    double  numeric_bytes;  /* algorithmic bytes of the numeric launches:
-                               (operand blocks read once + output blocks written) * b^2 * 8 */
+    int32_t tc_launches;       /* launches of the tensor-core product kernel */
+    int32_t simt_launches;     /* launches of the CUDA-core product kernel */
+    double  numeric_bytes;  /* algorithmic bytes of the product launches: operand blocks read
+                               once (8 bytes/element FP64, 4 bytes hi+lo planes) + output
+                               blocks written (8 bytes/element) */
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */

@@ -78,7 +78,7 @@ struct rdm_handle {
 
     // work buffers
     DevBuf<int> row_cnt, row_off, pool_col, pool_npair, counters, mask_col;
-    DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work;
+    DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work, work2;
     DevBuf<int64_t> pair_off, scan_tmp64;
     DevBuf<int> scan_tmp32, pair_a, pair_b, cnt_rows;
     DevBuf<double> out_val, row_part, sys_q;
@@ -86,7 +86,7 @@ struct rdm_handle {
     DevBuf<uint8_t> keep;
     DevBuf<double> row_lo, row_hi;
     TcWork tcw;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void ensure_events() {
         for (auto &e : ev)
             if (!e) RDM_CUDA_TRY(cudaEventCreate(&e));
@@ -367,33 +367,71 @@ void assemble(rdm_handle *h) {
 struct StepStats {
     int64_t npairs = 0;
     int64_t nslot = 0;
-    double issued = 0;
+    int64_t pairs_tc = 0, pairs_simt = 0;   // block triples per kernel class
+    double issued_tc = 0;
     double bytes = 0;
-    double ms[3] = {0, 0, 0};
-    int numeric_launches = 0;
+    double ms[5] = {0, 0, 0, 0, 0};         // symbolic, tc, simt, compaction, (unused)
+    int numeric_launches = 0, simt_launches = 0;
 };
 
-Arith tier_arith(int mode, int tier) {
-    switch (mode) {
-        case RDM_MODE_FP64: return AR_FP64;
-        case RDM_MODE_FP32: return AR_FP32;
-        case RDM_MODE_MIXED_BF16: return tier == 0 ? AR_BF16X3 : AR_FP64;
-        case RDM_MODE_MIXED_FP16: return tier == 0 ? AR_FP16X3 : AR_FP64;
-        case RDM_MODE_TF32: return AR_TF32;
+bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
+
+// Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
+// Mixed modes: tier 0 runs every product as a split product on the tensor
+// cores.  In the final tier the purification X0^2 is refined in FP64 on the
+// CUDA cores; the first-order products use `refine_x1` (RDM_REFINE_*): the
+// default is FP32 on the CUDA cores for the fp16 mode and FP64 for the bf16
+// mode.  (Split products in the final tier leave ~1e-6 of the tensor cores'
+// accumulation error in alpha; FP32 with round-to-nearest accumulation does
+// not.)
+void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0) {
+    if (refine_x1 == RDM_REFINE_DEFAULT)
+        refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32 : RDM_REFINE_FP64;
+    for (int p = 0; p < njob; ++p) {
+        Arith split = mode == RDM_MODE_MIXED_BF16 ? AR_BF16X3 : AR_FP16X3;
+        switch (mode) {
+            case RDM_MODE_FP64: ar[p] = AR_FP64; break;
+            case RDM_MODE_FP32: ar[p] = AR_FP32; break;
+            case RDM_MODE_MIXED_BF16:
+            case RDM_MODE_MIXED_FP16:
+                if (tier == 0) ar[p] = split;
+                else if (p == 0 || refine_x1 == RDM_REFINE_FP64) ar[p] = AR_FP64;
+                else ar[p] = refine_x1 == RDM_REFINE_SPLIT ? split : AR_FP32;
+                break;
+            default: ar[p] = AR_FP64;
+        }
     }
-    return AR_FP64;
 }
 
-StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, Arith ar) {
+StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, const Arith *ar_job) {
     cudaStream_t st = h->stream;
     const int NB = in.NB, b = in.b, njob = jt.njob;
     const size_t bb = (size_t)b * b;
     const int nrows = njob * NB;
     int max_ns = *std::max_element(h->nbs.begin(), h->nbs.end());
     StepStats ss;
+    unsigned tc_mask = 0, m64 = 0, m32 = 0;
+    Arith tc_ar = AR_FP16X3;
+    for (int p = 0; p < njob; ++p) {
+        if (is_tc(ar_job[p])) {
+            tc_mask |= 1u << p;
+            tc_ar = ar_job[p];
+        } else if (ar_job[p] == AR_FP64) {
+            m64 |= 1u << p;
+        } else {
+            m32 |= 1u << p;
+        }
+    }
+    const unsigned simt_mask = m64 | m32;
+    // first CUDA-core launch: the FP64 jobs (else the FP32 ones) plus the copies
+    // of converged systems; second launch: the FP32 jobs when both kinds exist
+    const Arith simt_ar = m64 ? AR_FP64 : AR_FP32;
+    const unsigned first_mask = m64 ? m64 : m32;
+    const unsigned second_mask = (m64 && m32) ? m32 : 0u;
+    const bool tc = tc_mask != 0;
     h->ensure_events();
     RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
-    if (ar != AR_FP64 && ar != AR_FP32) prepare_operands(in, ar, st);
+    if (tc) prepare_operands(in, tc_ar, h->tcw, st);
 
     h->row_cnt.ensure(nrows);
     h->row_off.ensure(nrows);
@@ -440,29 +478,46 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     scan_exclusive_i64(h->slot_npair.p, h->pair_off.p, (int)nslot, h->scan_tmp64.p, st);
     int64_t npairs = 0;
     d2h(&npairs, h->pair_off.p + nslot, 1, st);
+    // block triples per job: slots of job p are [out_rp[p NB], out_rp[(p+1) NB])
+    std::vector<int> job_slot(njob + 1);
+    for (int p = 0; p <= njob; ++p) d2h(&job_slot[p], h->out_rp.p + (size_t)p * NB, 1, st);
+    sync(h);
+    std::vector<int64_t> job_pair(njob + 1);
+    for (int p = 0; p <= njob; ++p) d2h(&job_pair[p], h->pair_off.p + job_slot[p], 1, st);
     sync(h);
     ss.npairs = npairs;
-    const bool tc = !(ar == AR_FP64 || ar == AR_FP32);
-    if (!tc) {
+    for (int p = 0; p < njob; ++p) {
+        const int64_t np = job_pair[p + 1] - job_pair[p];
+        if (is_tc(ar_job[p])) ss.pairs_tc += np; else ss.pairs_simt += np;
+    }
+    if (simt_mask) {
         h->pair_a.ensure(std::max<int64_t>(npairs, 1));
         h->pair_b.ensure(std::max<int64_t>(npairs, 1));
     }
     h->slot_x.ensure(std::max<int64_t>(nslot, 1));
     h->slot_t.ensure(std::max<int64_t>(nslot, 1));
+    // pair lists only for the jobs on the CUDA cores (the tensor-core kernel
+    // builds its own K-steps); slot_x / slot_t for every job
     launch_pairs(in, jt, h->sd, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p, h->pair_off.p,
                  nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st,
-                 tc ? 0 : 1);
+                 simt_mask);
     h->work.ensure(std::max<int64_t>(nslot, 1));
-    // tensor-core path: the SIMT kernel only copies the blocks of converged systems
+    // CUDA-core work: the jobs in simt_mask and the copies of converged systems
     launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
-                      h->sd.active.p, tc ? 1 : 0);
+                      h->sd.active.p, h->slot_job.p, first_mask, 1);
+    if (second_mask) {
+        h->work2.ensure(std::max<int64_t>(nslot, 1));
+        launch_build_work(h->slot_row.p, mcol, nslot, h->work2.p, h->counters.p + 4, st, h->sd.sys_of_row.p,
+                          h->sd.active.p, h->slot_job.p, second_mask, 0);
+    }
     TcPlan plan{};
-    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, st);
-    int hc[2];
-    d2h(hc, h->counters.p + 2, 2, st);
+    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tc_mask, st);
+    int hc[3];
+    d2h(hc, h->counters.p + 2, 3, st);
     sync(h);
     if (hc[0]) throw Error{RDM_ECUDA, "internal error: pair lists inconsistent with the mask (code " + std::to_string(hc[0]) + ")"};
     const int nwork = hc[1];
+    const int nwork2 = second_mask ? hc[2] : 0;
 
     // numeric + fused truncation
     h->out_val.ensure(std::max<int64_t>(nslot, 1) * bb);
@@ -479,16 +534,18 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p; a.b = b;
     RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
     const long long l0 = g_kernel_launches;
-    if (ar == AR_FP64 || ar == AR_FP32) {
-        launch_numeric_simt(a, ar, st);
-        ss.issued = (double)npairs * 2.0 * b * b * b;
-        ss.bytes = ((double)in.total * 8.0 + (double)nslot * 8.0) * (double)bb;
-    } else {
-        ss.issued = launch_numeric_tc(a, in, ar, h->tcw, NB, plan, st);
-        ss.bytes = ((double)in.total * 4.0 + (double)nslot * 8.0) * (double)bb;
-        if (nwork) launch_numeric_simt(a, AR_FP32, st);   // copies of converged systems
+    if (nwork) launch_numeric_simt(a, simt_ar, st);
+    if (nwork2) {
+        NumArgs a2 = a;
+        a2.work = h->work2.p;
+        a2.nwork = nwork2;
+        launch_numeric_simt(a2, AR_FP32, st);
     }
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[4], st));
+    ss.simt_launches = (int)(g_kernel_launches - l0);
+    if (tc) ss.issued_tc = launch_numeric_tc(a, in, jt, tc_ar, h->tcw, NB, plan, st);
     ss.numeric_launches = (int)(g_kernel_launches - l0);
+    ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (double)nslot * 8.0) * (double)bb;
     RDM_CUDA_TRY(cudaEventRecord(h->ev[2], st));
 
     // compaction
@@ -514,13 +571,15 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, A
     std::vector<int> rp(nrows + 1);
     d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
     sync(h);
-    float m01 = 0, m12 = 0, m23 = 0;
+    float m01 = 0, m14 = 0, m42 = 0, m23 = 0;
     cudaEventElapsedTime(&m01, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&m12, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&m14, h->ev[1], h->ev[4]);
+    cudaEventElapsedTime(&m42, h->ev[4], h->ev[2]);
     cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);
     ss.ms[0] = m01;
-    ss.ms[1] = m12;
-    ss.ms[2] = m23;
+    ss.ms[1] = m42;   // tensor-core products
+    ss.ms[2] = m14;   // CUDA-core products
+    ss.ms[3] = m23;
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -595,9 +654,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     JobTable jt = solve_jobs(nd);
     std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
     std::vector<int> act(S);
-    double useful = 0, issued = 0, nbytes = 0;
-    double kms[3] = {0, 0, 0};
-    int num_launches = 0;
+    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_simt = 0;
+    double kms[4] = {0, 0, 0, 0};
+    int tc_launches = 0, simt_launches = 0;
     cudaEvent_t ev0, ev1;
     RDM_CUDA_TRY(cudaEventCreate(&ev0));
     RDM_CUDA_TRY(cudaEventCreate(&ev1));
@@ -647,6 +706,11 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                 if (!lowprec && stall_tol > 0 && e >= y.e_hist[E - 3] && e < stall_tol) stop = true;
                 if (lowprec && y.tier == final_tier && n - y.tier_start >= 2 &&
                     fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) && fabs(e) < 1e-2 * nocc[s])
+                    stop = true;
+                // mixed modes: X0 refined in FP64 has reached the rounding floor of
+                // the idempotency error and the band energy no longer moves
+                if (mixed && y.tier == final_tier && n - y.tier_start >= 2 && y.have_eb &&
+                    fabs(e) <= 1e-12 * std::max(1.0, nocc[s]) && fabs(eb0 - y.eb0) < std::max(P.tol, 1e-12))
                     stop = true;
             }
             y.have_eb = true;
@@ -699,7 +763,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             if (act[s]) tier = std::min(tier, ss[s].tier);
         for (int s = 0; s < S; ++s)
             if (act[s] && ss[s].tier != tier && mixed) tier = final_tier;
-        const Arith ar = tier_arith(P.mode, tier);
+        Arith ar[kMaxJobs];
+        tier_arith(P.mode, tier, jt.njob, ar, P.refine_x1);
         h2d(h->sd.c_lin.p, c_lin.data(), S, st);
         h2d(h->sd.c_sq.p, c_sq.data(), S, st);
         h2d(h->sd.tau0.p, t0.data(), S, st);
@@ -712,11 +777,15 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         RDM_CUDA_TRY(cudaEventSynchronize(ev1));
         float ms = 0;
         cudaEventElapsedTime(&ms, ev0, ev1);
-        useful += (double)sst.npairs * 2.0 * b * b * b;
-        issued += sst.issued;
+        const double fpb = 2.0 * b * b * b;
+        useful += (double)sst.npairs * fpb;
+        flops_tc += (double)sst.pairs_tc * fpb;
+        flops_simt += (double)sst.pairs_simt * fpb;
+        issued += sst.issued_tc + (double)sst.pairs_simt * fpb;
         nbytes += sst.bytes;
-        num_launches += sst.numeric_launches;
-        for (int k = 0; k < 3; ++k) kms[k] += sst.ms[k];
+        tc_launches += sst.numeric_launches - sst.simt_launches;
+        simt_launches += sst.simt_launches;
+        for (int k = 0; k < 4; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
             if (act[s]) {
@@ -731,8 +800,11 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             for (int d = 0; d < nd; ++d) r->nnzb1[d] = Xn.nnzb[1 + d];
         }
         if (P.verbose) {
-            fprintf(stderr, "[rdm] step %d arith %d pairs %lld slots %lld nnzb0 %lld %.3f ms\n", it, (int)ar,
-                    (long long)sst.npairs, (long long)sst.nslot, (long long)Xn.nnzb[0], ms);
+            fprintf(stderr,
+                    "[rdm] step %d arith %d/%d pairs %lld slots %lld nnzb0 %lld %.3f ms (sym %.2f tc %.2f simt %.2f "
+                    "cmp %.2f)\n",
+                    it, (int)ar[0], (int)ar[jt.njob - 1], (long long)sst.npairs, (long long)sst.nslot,
+                    (long long)Xn.nnzb[0], ms, sst.ms[0], sst.ms[1], sst.ms[2], sst.ms[3]);
         }
     }
     cudaEventDestroy(ev0);
@@ -784,10 +856,14 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.time_ms = wall_ms;
         I.useful_flops = useful;
         I.issued_flops = issued;
-        for (int k = 0; k < 3; ++k) I.kernel_ms[k] = kms[k];
-        I.kernel_ms[3] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2]);
+        for (int k = 0; k < 4; ++k) I.kernel_ms[k] = kms[k];
+        I.kernel_ms[4] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3]);
+        I.kernel_ms[5] = 0;
+        I.kernel_flops[0] = flops_tc;
+        I.kernel_flops[1] = flops_simt;
         I.kernel_launches = g_kernel_launches - launches0;
-        I.numeric_launches = num_launches;
+        I.tc_launches = tc_launches;
+        I.simt_launches = simt_launches;
         I.numeric_bytes = nbytes;
     }
     // band energy of the result: recompute the stats of the final X
@@ -907,9 +983,9 @@ const char *rdm_last_error(const rdm_handle *h) {
 int rdm_set_params(rdm_handle *h, const rdm_params *p) {
     if (!h) return RDM_EINVAL;
     if (!p) return fail(h, RDM_EINVAL, "null params");
-    if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 4 ||
+    if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 3 ||
         !(p->spin_factor > 0) || p->min_iter < 0)
-        return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..4)");
+        return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3)");
     h->prm = *p;
     return RDM_OK;
 }
@@ -1056,7 +1132,7 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         DeviceGuard dg(h->device);
         if (!A || (terms == 2 && !B)) return fail(h, RDM_EINVAL, "null operand");
         if (terms != 1 && terms != 2) return fail(h, RDM_EINVAL, "terms must be 1 or 2");
-        if (!(tau >= 0) || mode < 0 || mode > 4) return fail(h, RDM_EINVAL, "bad tau or mode");
+        if (!(tau >= 0) || mode < 0 || mode > 3) return fail(h, RDM_EINVAL, "bad tau or mode");
         if (A->nb > kSymMaxNs) return fail(h, RDM_EINVAL, "matrix too large for the product primitive");
         // a private single-system context so that the solve state is untouched
         rdm_handle t;
@@ -1134,7 +1210,8 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         int ix = X ? idx[2] : -1;
         if (terms == 1) jt.job[0] = Job{0, ix, 1, {ia, ia}, {ia, ia}, 0};
         else jt.job[0] = Job{0, ix, 2, {ia, ib}, {ib, ia}, 0};
-        Arith ar = tier_arith(mode, 0);
+        Arith ar[kMaxJobs];
+        tier_arith(mode, 0, jt.njob, ar);
         MatSet res;
         multiply(&t, in, res, jt, ar);
         int64_t n = res.nnzb[0];

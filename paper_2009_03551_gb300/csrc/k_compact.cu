@@ -10,13 +10,19 @@ namespace {
 // work list: slots with col >= row, in slot order (one warp per 32 slots,
 // ballot-ordered, block-level offsets through one atomic per warp; the order
 // of the list does not affect results)
+// keeps the upper slots of the active systems' jobs in job_mask and, with
+// with_inactive, every upper slot of a converged system (those are copied)
 __global__ void k_build_work(const int *__restrict__ slot_row, const int *__restrict__ out_col,
                              int64_t nslot, int *work, int *nwork, const int *__restrict__ sys_of_row,
-                             const int *__restrict__ active, int only_inactive) {
+                             const int *__restrict__ active, const int *__restrict__ slot_job,
+                             unsigned job_mask, int with_inactive) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lane = threadIdx.x & 31;
     bool up = s < nslot && out_col[s] >= slot_row[s];
-    if (up && only_inactive) up = !active[sys_of_row[slot_row[s]]];
+    if (up) {
+        const bool act = active[sys_of_row[slot_row[s]]] != 0;
+        up = act ? ((job_mask >> slot_job[s]) & 1u) != 0 : with_inactive != 0;
+    }
     unsigned m = __ballot_sync(0xffffffffu, up);
     int base = 0;
     if (lane == 0 && m) base = atomicAdd(nwork, __popc(m));
@@ -73,11 +79,11 @@ __global__ void k_compact_copy(const int *__restrict__ rp, const int *__restrict
 
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot, int *work,
                        int *nwork, cudaStream_t st, const int *sys_of_row, const int *active,
-                       int only_inactive) {
+                       const int *slot_job, unsigned job_mask, int with_inactive) {
     if (nslot == 0) return;
     int64_t grid = (nslot + 255) / 256;
     k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, nslot, work, nwork, sys_of_row,
-                                                 active, only_inactive);
+                                                 active, slot_job, job_mask, with_inactive);
     RDM_LAUNCH_CHECK();
 }
 

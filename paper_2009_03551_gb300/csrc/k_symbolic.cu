@@ -225,7 +225,7 @@ struct PairParams {
     int64_t nslot;
     int *pair_a, *pair_b, *slot_x, *slot_t, *err;
     const int *sys_of_row, *active;
-    int fill;     // 0: only slot_x / slot_t (the tensor-core path builds its own K-steps)
+    unsigned fill;   // jobs whose pair lists are filled (others: only slot_x / slot_t)
 };
 
 // one warp per output slot; only upper-triangle slots (j >= i) do work
@@ -249,7 +249,7 @@ __global__ void k_pairs(PairParams P) {
         P.slot_x[s] = x;
     }
     // a converged system's blocks are copied: the symbolic phase gave them no pairs
-    if (!P.fill || !P.active[P.sys_of_row[i]]) return;
+    if (!((P.fill >> p) & 1u) || !P.active[P.sys_of_row[i]]) return;
     int64_t w = P.pair_off[s];
     const int64_t wend = P.pair_off[s + 1];
     for (int t = 0; t < job.nterm; ++t) {
@@ -314,7 +314,7 @@ void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, i
 void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
                   const int *out_col, const int *slot_row, const int *slot_job,
                   const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
-                  int *slot_x, int *slot_t, int *err, cudaStream_t st, int fill) {
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st, unsigned fill) {
     if (nslot == 0) return;
     PairParams P;
     P.fill = fill;

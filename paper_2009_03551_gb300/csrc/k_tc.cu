@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "tc_gemm.cuh"
 
 namespace rdm {
@@ -138,15 +140,44 @@ __device__ __forceinline__ int core_offset(int r, int c) {
     return (((r >> 3) * 4 + (c >> 3)) << 6) + ((r & 7) << 3) + (c & 7);
 }
 
+// per matrix m: scale[m] = 2^floor(log2(2^14 / max block norm)) for fp16 (the
+// largest element then sits below 2^14, far from fp16 overflow, and values
+// down to ~1e-9 of it stay normal); 1 for bf16, whose exponent range is FP32's
+__global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__restrict__ mat_first, int nmat,
+                                int fp16, float *__restrict__ scale) {
+    const int m = blockIdx.x;
+    if (m >= nmat) return;
+    float mx = 0.f;
+    for (int p = mat_first[m] + threadIdx.x; p < mat_first[m + 1]; p += blockDim.x) mx = fmaxf(mx, nrm[p]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ float sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmaxf(mx, sh[k]);
+        mx = fmaxf(mx, sh[0]);
+        float s = 1.f;
+        if (fp16 && mx > 0.f) {
+            int e = (int)floorf(log2f(16384.f / mx));
+            e = max(-60, min(60, e));
+            s = ldexpf(1.f, e);
+        }
+        scale[m] = s;
+    }
+}
+
 template <bool BF16>
 __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
-                               uint16_t *__restrict__ lo) {
+                               uint16_t *__restrict__ lo, const float *__restrict__ scale,
+                               const int *__restrict__ mat_first, int nmat) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = nblk * kPlaneElems;
     if (e >= n) return;
     int64_t p = e / kPlaneElems;
     int rc = (int)(e % kPlaneElems);
-    float x = (float)val[e];
+    int m = 0;
+    while (m + 1 < nmat && p >= mat_first[m + 1]) ++m;
+    float x = (float)val[e] * scale[m];
     uint16_t h, l;
     if (BF16) {
         __nv_bfloat16 bh = __float2bfloat16_rn(x);
@@ -175,6 +206,7 @@ struct TileBuild {
     const int *out_rp;   // mask row_ptr (flat, njob*NB+1)
     const int *mcol;     // mask columns
     const int *sys_of_row, *active;
+    unsigned job_mask;   // jobs computed on the tensor cores
     int *tile_cnt;       // [njob*NB4]
     const int *tile_off; // scanned
     int *tiles;          // [ntile * kTileInts]
@@ -205,8 +237,9 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
         cur[m] = lo;
         end[m] = T.out_rp[p * T.NB + i + 1];
         // converged systems keep their blocks through the copy path of the
-        // numeric phase; their rows produce no tiles
-        if (!T.active[T.sys_of_row[i]]) cur[m] = end[m];
+        // numeric phase, and jobs on the CUDA cores have their own launch:
+        // neither produces tiles
+        if (!T.active[T.sys_of_row[i]] || !((T.job_mask >> p) & 1u)) cur[m] = end[m];
     }
     int n = 0;
     int base = fill ? T.tile_off[t] : 0;
@@ -297,6 +330,8 @@ struct TcArgs {
     const int *steps;
     int ntile;
     uint32_t idesc;
+    const float *scale;           // per matrix operand scale
+    int job_a[kMaxJobs], job_b[kMaxJobs];
     // epilogue
     const double *in_val;
     const int *slot_row, *slot_job, *slot_x, *slot_t;
@@ -445,7 +480,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 const int i = A.slot_row[s];
                 const int sys = A.sys_of_row[i];
                 const int job = A.slot_job[s];
-                const float cl = (float)A.c_lin[sys], cq = (float)A.c_sq[sys];
+                const float cl = (float)A.c_lin[sys];
+                // undo the operand scaling: every term of a job has the same scale product
+                const float cq = (float)A.c_sq[sys] / (A.scale[A.job_a[job]] * A.scale[A.job_b[job]]);
                 const double tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
                 const int sx = A.slot_x[s], stt = A.slot_t[s];
                 const bool diag = (stt == s);
@@ -513,21 +550,33 @@ constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 4 * 32 * 33 * size
 
 }  // namespace
 
-void prepare_operands(MatSet &in, Arith ar, cudaStream_t st) {
+void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
     if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
+    if (ar != AR_BF16X3 && ar != AR_FP16X3) throw Error{-1, "tensor-core arithmetic not available"};
+    const int nmat = in.nmat;
+    std::vector<int> first(nmat + 1, 0);
+    for (int m = 0; m < nmat; ++m) first[m + 1] = first[m] + (int)in.nnzb[m];
+    w.mat_first.ensure(nmat + 1);
+    w.scale.ensure(std::max(nmat, 1));
+    RDM_CUDA_TRY(cudaMemcpyAsync(w.mat_first.p, first.data(), (nmat + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_matrix_scales<<<nmat, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
+    RDM_LAUNCH_CHECK();
     const int64_t n = in.total * kPlaneElems;
     in.ophi.ensure(std::max<int64_t>(n, 1));
     in.oplo.ensure(std::max<int64_t>(n, 1));
     if (n == 0) return;
     const int64_t grid = (n + 255) / 256;
-    if (ar == AR_BF16X3) k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p);
-    else if (ar == AR_FP16X3) k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p);
-    else throw Error{-1, "tensor-core arithmetic not available"};
+    if (ar == AR_BF16X3)
+        k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p, w.scale.p,
+                                                             w.mat_first.p, nmat);
+    else
+        k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p, w.scale.p,
+                                                              w.mat_first.p, nmat);
     RDM_LAUNCH_CHECK();
 }
 
-double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w, int NB,
-                         const TcPlan &plan, cudaStream_t st) {
+double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
+                         int NB, const TcPlan &plan, cudaStream_t st) {
     if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
     if (plan.ntile == 0) return 0.0;
     if (!w.zero.p) {
@@ -540,6 +589,11 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w
     // kind::f16: D = F32 (bit 4), A/B = BF16 (1) or F16 (0), K-major, N = 128, M = 128
     const uint32_t ab = ar == AR_BF16X3 ? 1u : 0u;
     A.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    A.scale = w.scale.p;
+    for (int p = 0; p < kMaxJobs; ++p) {
+        A.job_a[p] = p < jt.njob ? jt.job[p].a[0] : 0;
+        A.job_b[p] = p < jt.njob ? jt.job[p].b[0] : 0;
+    }
     A.in_val = a.in_val; A.slot_row = a.slot_row; A.slot_job = a.slot_job; A.slot_x = a.slot_x;
     A.slot_t = a.slot_t; A.sys_of_row = a.sys_of_row; A.c_lin = a.c_lin; A.c_sq = a.c_sq;
     A.tau0 = a.tau0; A.tau1 = a.tau1;
@@ -561,7 +615,7 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w
 }
 
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, cudaStream_t st) {
+                     const int *mcol, TcWork &w, unsigned job_mask, cudaStream_t st) {
     TcPlan plan{};
     const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL, njob = jt.njob;
     const int nrow4 = njob * NB4;
@@ -573,6 +627,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     TileBuild T{};
     T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NB4 = NB4; T.jt = jt;
     T.out_rp = out_rp; T.mcol = mcol; T.sys_of_row = sd.sys_of_row.p; T.active = sd.active.p;
+    T.job_mask = job_mask;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
     k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();

@@ -197,7 +197,7 @@ void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, i
 void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
                   const int *out_col, const int *slot_row, const int *slot_job,
                   const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
-                  int *slot_x, int *slot_t, int *err, cudaStream_t st, int fill = 1);
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st, unsigned fill = ~0u);
 
 // k_numeric.cu: C(upper slot) = c_lin X + c_sq sum(pairs); lower slot = transpose
 struct NumArgs {
@@ -221,10 +221,11 @@ struct NumArgs {
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
 
 // k_compact.cu
-// only_inactive = 1: keep only the slots of converged systems (copied blocks)
+// upper slots of the active systems' jobs in job_mask, plus (with_inactive)
+// all upper slots of converged systems
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot,
-                       int *work, int *nwork, cudaStream_t st, const int *sys_of_row = nullptr,
-                       const int *active = nullptr, int only_inactive = 0);
+                       int *work, int *nwork, cudaStream_t st, const int *sys_of_row,
+                       const int *active, const int *slot_job, unsigned job_mask, int with_inactive);
 void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total,
                           int *cnt, cudaStream_t st);
 void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,

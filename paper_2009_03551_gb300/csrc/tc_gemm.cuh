@@ -16,6 +16,8 @@ struct TcWork {
     DevBuf<int> counters;       // [0]: error bits of the product kernel
     DevBuf<int> scan32;
     DevBuf<int64_t> scan64;
+    DevBuf<float> scale;        // per matrix: power-of-two scale of its operand planes
+    DevBuf<int> mat_first;      // per matrix: first global block index (nmat+1)
 };
 
 struct TcPlan {
@@ -24,17 +26,21 @@ struct TcPlan {
 };
 
 // Convert the FP64 master values of `in` into hi/lo operand planes of
-// arithmetic `ar` in the K-major core-matrix layout of the MMA.
-void prepare_operands(MatSet &in, Arith ar, cudaStream_t st);
+// arithmetic `ar` in the K-major core-matrix layout of the MMA.  For fp16
+// every matrix is first scaled by a power of two (from its largest block
+// norm) so that its values sit in the normal range of fp16; the product
+// kernel divides the scale back out per job.
+void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st);
 
-// Tile lists of one multiplication step from the output mask.
+// Tile lists of one multiplication step from the output mask, for the jobs
+// whose bit is set in job_mask.
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, cudaStream_t st);
+                     const int *mcol, TcWork &w, unsigned job_mask, cudaStream_t st);
 
 // Numeric phase on the tensor cores; same output contract as
 // launch_numeric_simt for the slots of active systems.  Returns the flops
 // issued to the tensor cores.
-double launch_numeric_tc(const NumArgs &a, const MatSet &in, Arith ar, TcWork &w, int NB,
-                         const TcPlan &plan, cudaStream_t st);
+double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
+                         int NB, const TcPlan &plan, cudaStream_t st);
 
 }  // namespace rdm

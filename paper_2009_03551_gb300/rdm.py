@@ -34,8 +34,7 @@ MODE_FP64 = 0
 MODE_FP32 = 1
 MODE_MIXED_BF16 = 2
 MODE_MIXED_FP16 = 3
-MODE_TF32 = 4
-MODES = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3, "tf32": 4}
+MODES = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
 
 EXPORTED = (
     "rdm_create", "rdm_destroy", "rdm_last_error", "rdm_default_params", "rdm_set_params",
@@ -60,7 +59,8 @@ class rdm_params(C.Structure):
     _fields_ = [("tau", C.c_double), ("tau_x1", C.c_double), ("tau_refine", C.c_double),
                 ("tol", C.c_double), ("stall_tol", C.c_double), ("spin_factor", C.c_double),
                 ("max_iter", C.c_int32), ("mode", C.c_int32), ("min_iter", C.c_int32),
-                ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class rdm_info(C.Structure):
@@ -69,8 +69,9 @@ class rdm_info(C.Structure):
                 ("idempotency", C.c_double), ("band_energy0", C.c_double),
                 ("nnzb_p0", C.c_int64), ("nnzb_p1", C.c_int64 * 3), ("time_ms", C.c_double),
                 ("useful_flops", C.c_double), ("issued_flops", C.c_double),
-                ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64),
-                ("numeric_launches", C.c_int32), ("pad0", C.c_int32), ("numeric_bytes", C.c_double)]
+                ("kernel_ms", C.c_double * 6), ("kernel_flops", C.c_double * 2),
+                ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
+                ("numeric_bytes", C.c_double)]
 
 
 class rdm_iter_log(C.Structure):

@@ -126,6 +126,24 @@ def test_mixed_solve_vs_oracle(rdm, cluster150, oracle150, mode):
     assert abs(info.idempotency) < 1e-8 and abs(info.trace_error) < 1e-8
 
 
+@pytest.mark.parametrize("refine,tol", [(1, 1e-6), (3, 1e-6), (2, 5e-6)])
+def test_final_tier_first_order_arithmetic(rdm, cluster150, oracle150, refine, tol):
+    """Final tier of the fp16 ladder: X0^2 in FP64, X1 products in FP64 (1),
+    FP32 on the CUDA cores (3), or kept on the tensor cores (2).  The last
+    keeps the tensor cores' FP32 accumulation error (a few 1e-6 in alpha)."""
+    s = cluster150
+    ob, h1s = oracle150
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x1=refine)
+    sol.load(s)
+    code, info = sol.solve()
+    assert code == rdm.RDM_OK and info.converged
+    a = sol.alpha()
+    ao = polarizability(ob.p1s, h1s)
+    assert np.max(np.abs(a - ao)) / np.max(np.abs(ao)) <= tol
+    assert abs(info.idempotency) < 1e-8
+
+
 def test_mixed_batch_with_converged_copies(rdm):
     systems = [make_chain(40, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=21, dirs=("x", "y", "z")),
                make_cluster(90, opa=8, b=32, cutoff=10.0, seed=22, dirs=("x", "y", "z"))]
@@ -135,8 +153,8 @@ def test_mixed_batch_with_converged_copies(rdm):
     code, info = sol.solve()
     assert code == rdm.RDM_OK
     # the chain's alpha carries the dipole range (|x| up to 55 bohr) as an error
-    # amplifier: the 16-bit split reaches 3e-6 there (the CPU emulation of the
-    # same split gives 2.9e-6), the cluster 1e-6
+    # amplifier: the 16-bit bf16 split reaches ~3e-6 there (the CPU emulation
+    # of the same split gives 2.9e-6), the cluster 1e-6
     tol = [5e-6, 1e-6]
     for k, s in enumerate(systems):
         one = rdm.Solver(0)
@@ -146,3 +164,14 @@ def test_mixed_batch_with_converged_copies(rdm):
         a1, a0 = sol.alpha(k), one.alpha()
         assert np.max(np.abs(a1 - a0)) / np.max(np.abs(a0)) <= tol[k]
         assert np.allclose(sol.p0(k).to_dense(), one.p0().to_dense(), atol=1e-5)
+    # the scaled fp16 split with the FP32 refinement of X1 meets 1e-6 on both
+    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100)
+    code, info = sol.solve()
+    assert code == rdm.RDM_OK
+    for k, s in enumerate(systems):
+        one = rdm.Solver(0)
+        one.set_params(tau=1e-6, tol=1e-9, mode="fp64", max_iter=100)
+        one.load(s)
+        one.solve()
+        a1, a0 = sol.alpha(k), one.alpha()
+        assert np.max(np.abs(a1 - a0)) / np.max(np.abs(a0)) <= 1e-6
