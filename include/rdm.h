@@ -248,6 +248,28 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
                       double c_lin, double c_sq, int terms, double tau, int mode,
                       rdm_bsr_out *out, int64_t *needed);
 
+/* ---- allocation-free inner product (no counterpart in the paper) ---------- */
+
+/* <A, B> = sum over the blocks (i,j) stored in both A and B of the
+ * elementwise products (Tr(A B) for symmetric A, B: the reduction behind the
+ * polarizability trace), written as one double to out_device, in the order
+ * of the CUDA stream `cuda_stream` (NULL = legacy default stream), on the
+ * current device.  For callers that must not allocate device memory: a
+ * framework whose caching pool owns the free HBM, or a latency-critical loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.
+ * The call allocates nothing: its scratch (one double per block row) is a
+ * file-scope device array of at most 262,144 block rows, held by every GPU
+ * that loads the library until exit.
+ *  - A and B: device BSR (on_device = 1) with the same nb and b; nb above
+ *    262,144 returns RDM_EINVAL, as do null pointers and host matrices.
+ *  - The first call on a device looks up the array's device address (once,
+ *    with that device current); make it before any stream capture.
+ *  - All calls share the array: calls whose kernels overlap on the GPU race
+ *    and must be serialised by the caller.  Nothing in the array has to start
+ *    at zero (every call writes each partial it reads).
+ * Returns RDM_OK, RDM_EINVAL or RDM_ECUDA (launch failure). */
+int rdm_bsr_dot_noalloc(const rdm_bsr *A, const rdm_bsr *B, double *out_device, void *cuda_stream);
+
 /* Library version string. */
 const char *rdm_version(void);
 

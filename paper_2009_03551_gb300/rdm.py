@@ -40,7 +40,7 @@ EXPORTED = (
     "rdm_create", "rdm_destroy", "rdm_last_error", "rdm_default_params", "rdm_set_params",
     "rdm_batch_create", "rdm_upload_h0", "rdm_upload_h1", "rdm_solve", "rdm_force_branches",
     "rdm_get_info", "rdm_get_p0_nnzb", "rdm_get_p1_nnzb", "rdm_get_p0", "rdm_get_p1",
-    "rdm_get_alpha", "rdm_get_log", "rdm_block_product", "rdm_version",
+    "rdm_get_alpha", "rdm_get_log", "rdm_block_product", "rdm_version", "rdm_bsr_dot_noalloc",
 )
 
 
@@ -109,6 +109,7 @@ def _load():
                                         C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
                                         C.POINTER(rdm_bsr_out), C.POINTER(C.c_int64)]),
         "rdm_version": (C.c_char_p, []),
+        "rdm_bsr_dot_noalloc": (C.c_int, [C.POINTER(rdm_bsr), C.POINTER(rdm_bsr), C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -320,6 +321,18 @@ def rdm_block_product(h, A, B, X, c_lin: float, c_sq: float, terms: int, tau: fl
     _check(h, _lib.rdm_block_product(h, pa, pb, px, c_lin, c_sq, terms, tau, mode, C.byref(out), None))
     del ka, kb, kx
     return BsrResult(nb, b, int(A.n), rp, ci[:nnz].copy(), va[:nnz].copy())
+
+
+def rdm_bsr_dot_noalloc(A, B, out_ptr: int, stream=None) -> None:
+    """<A, B> of two device BSR matrices into the device double at out_ptr,
+    without any device allocation (see include/rdm.h)."""
+    sa, ka = to_bsr(A)
+    sb, kb = to_bsr(B)
+    code = _lib.rdm_bsr_dot_noalloc(C.byref(sa), C.byref(sb), C.c_void_p(out_ptr), stream)
+    del ka, kb
+    if code != RDM_OK:
+        raise RdmError(code, "rdm_bsr_dot_noalloc failed (device matrices with equal nb, b required; "
+                             "nb <= 262144)")
 
 
 # ---- convenience wrapper ---------------------------------------------------
