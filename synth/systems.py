@@ -72,13 +72,10 @@ class Bsr:
         return np.repeat(np.arange(self.nb, dtype=np.int64), np.diff(self.row_ptr))
 
     def to_dense(self, padded: bool = False) -> np.ndarray:
-        nbb = self.nb * self.b
-        a = np.zeros((nbb, nbb), dtype=np.float64)
-        rows = self.row_of_block()
         b = self.b
-        for p in range(self.nnzb):
-            i, j = rows[p], self.col_idx[p]
-            a[i * b:(i + 1) * b, j * b:(j + 1) * b] = self.vals[p]
+        a = np.zeros((self.nb, b, self.nb, b), dtype=np.float64)
+        a[self.row_of_block(), :, self.col_idx.astype(np.int64), :] = self.vals
+        a = a.reshape(self.nb * b, self.nb * b)
         return a if padded else a[: self.n, : self.n]
 
     @staticmethod
