@@ -256,7 +256,7 @@ def run_ours(args, sys_, rank, world, torch, dist):
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
     kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(6)]
-    kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(2)]
+    kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(3)]
     launches = int(sum(i.kernel_launches for i in infos))
 
     # FP64 comparison solve (context for the metric's "FP64 vs mixed")
@@ -306,31 +306,29 @@ def run_ours(args, sys_, rank, world, torch, dist):
 
     peaks, peak_kind = load_peaks()
     mode = args.mode
-    # dominant kernel of the solve (by device time): the tensor-core product
-    # kernel or the CUDA-core (FP64 / FP32) product kernel
-    tc_ms, simt_ms = kms[1], kms[2]
-    if tc_ms >= simt_ms:
-        kname, k_ms, k_fl, k_launch = "k_tc_bf16x3 (tcgen05 split-precision block SpGEMM + fused truncation)", \
-            tc_ms, kfl[0], int(last.tc_launches)
-        # a split product issues 3 MMAs per useful product: the tensor peak for
-        # useful flops is a third of the dense bf16/fp16 peak
-        peak = peaks["bf16_tflops"] * 1e12 / 3.0
-        bound, peak_note = "tensor", (f"measured bf16 dense burst / 3 split products ({peak_kind}, "
-                                      "MEASURED_PEAKS.json bf16_tflops; fp16 has the same nominal rate)")
-    else:
-        kname, k_ms, k_fl, k_launch = "k_numeric_simt (CUDA-core block SpGEMM + fused truncation)", \
-            simt_ms, kfl[1], int(last.simt_launches)
-        fp64_like = mode in ("fp64", "mixed_bf16", "mixed_fp16")
-        peak = 1.26e12 if fp64_like else 80.5e12
-        bound = "alu"
-        peak_note = (FP64_PEAK_NOTE if fp64_like else FP32_PEAK_NOTE) + " (derived from unit counts and clock)"
+    # dominant kernel of the solve (by device time) among the three product
+    # kernels: tensor-core split products, FP64 and FP32 CUDA-core products
+    tc_ms, f64_ms, f32_ms = kms[1], kms[2], kms[3]
+    classes = {
+        "tc": ("k_tc_bf16x3 (tcgen05 split-precision block SpGEMM + fused truncation)", tc_ms, kfl[0],
+               peaks["bf16_tflops"] * 1e12 / 3.0, "tensor",
+               f"measured bf16 dense burst / 3 (a split product issues 3 MMAs per useful product; {peak_kind}, "
+               "MEASURED_PEAKS.json bf16_tflops; fp16 has the same nominal rate)"),
+        "fp64": ("k_numeric_simt<32,double> (FP64 block SpGEMM + fused truncation)", f64_ms, kfl[1], 1.26e12,
+                 "alu", FP64_PEAK_NOTE + " (derived from unit counts and clock)"),
+        "fp32": ("k_numeric_f32_b32 (FP32 block SpGEMM + fused truncation)", f32_ms, kfl[2], 80.5e12, "alu",
+                 FP32_PEAK_NOTE + " (derived from unit counts and clock)"),
+    }
+    dom = max(classes, key=lambda k: classes[k][1])
+    kname, k_ms, k_fl, peak, bound, peak_note = classes[dom]
     achieved = k_fl / (k_ms / 1e3) if k_ms > 0 else 0.0
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
-                "flops_per_launch": k_fl / max(k_launch, 1), "avg_launch_ms": k_ms / max(k_launch, 1),
-                "launches_per_solve": k_launch, "peak_source": peak_note,
-                "share_of_solve": k_ms / (s_per_solve * 1e3)}
-    num_ms = tc_ms + simt_ms
+                "ms_per_solve": k_ms, "peak_source": peak_note, "share_of_solve": k_ms / (s_per_solve * 1e3),
+                "per_class": {k: {"ms": v[1], "tflops": (v[2] / (v[1] / 1e3) / 1e12) if v[1] > 0 else None,
+                                  "frac": ((v[2] / (v[1] / 1e3)) / v[3]) if v[1] > 0 else None}
+                              for k, v in classes.items()}}
+    num_ms = tc_ms + f64_ms + f32_ms
     achieved_all = useful / (num_ms / 1e3) if num_ms > 0 else 0.0
 
     line = {"metric": METRIC, "value": s_per_solve, "unit": "s", "higher_is_better": False,
@@ -344,13 +342,11 @@ def run_ours(args, sys_, rank, world, torch, dist):
                        "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
             "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
             "block_spgemm_tflops": achieved_all / 1e12,
-            "tensor_core_tflops": kfl[0] / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
-            "cuda_core_tflops": kfl[1] / (simt_ms / 1e3) / 1e12 if simt_ms > 0 else None,
             "alpha_diag": [float(alpha_m[k, k]) for k in range(3)],
             "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
-                                    "cuda_core_products": kms[2], "compaction": kms[3],
-                                    "reductions_setup_host": kms[4]},
+                                    "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
+                                    "reductions_setup_host": kms[5]},
             "tier_iterations": list(last.tier_iters)[:2],
             "clocks": clocks}
     sol.close()

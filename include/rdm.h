@@ -133,11 +133,11 @@ typedef struct {
     double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
     double  kernel_ms[6];   /* device time per kernel class (CUDA events on the handle's stream):
                                0 symbolic mask + pair / tile lists, 1 tensor-core products,
-                               2 CUDA-core products (FP64 / FP32, and copies of converged
-                               systems), 3 truncation compaction, 4 reductions and set-up
-                               (the remainder of the solve), 5 reserved */
-    double  kernel_flops[2];   /* useful flops (2 b^3 per block triple) of the tensor-core (0)
-                                  and CUDA-core (1) product launches */
+                               2 FP64 CUDA-core products, 3 FP32 CUDA-core products (and copies
+                               of converged systems), 4 truncation compaction, 5 reductions,
+                               set-up and host decisions (the remainder of the solve) */
+    double  kernel_flops[3];   /* useful flops (2 b^3 per block triple) of the tensor-core (0),
+                                  FP64 (1) and FP32 (2) product launches */
     int64_t kernel_launches;   /* kernels launched by the solve */
     int32_t tc_launches;       /* launches of the tensor-core product kernel */
     int32_t simt_launches;     /* launches of the CUDA-core product kernel */

@@ -86,7 +86,7 @@ struct rdm_handle {
     DevBuf<uint8_t> keep;
     DevBuf<double> row_lo, row_hi;
     TcWork tcw;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void ensure_events() {
         for (auto &e : ev)
             if (!e) RDM_CUDA_TRY(cudaEventCreate(&e));
@@ -367,10 +367,10 @@ void assemble(rdm_handle *h) {
 struct StepStats {
     int64_t npairs = 0;
     int64_t nslot = 0;
-    int64_t pairs_tc = 0, pairs_simt = 0;   // block triples per kernel class
+    int64_t pairs_tc = 0, pairs_64 = 0, pairs_32 = 0;   // block triples per kernel class
     double issued_tc = 0;
     double bytes = 0;
-    double ms[5] = {0, 0, 0, 0, 0};         // symbolic, tc, simt, compaction, (unused)
+    double ms[5] = {0, 0, 0, 0, 0};         // symbolic, tc, fp64, fp32, compaction
     int numeric_launches = 0, simt_launches = 0;
 };
 
@@ -432,6 +432,10 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     h->ensure_events();
     RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
+    if (m32) {
+        in.opf32.ensure(std::max<int64_t>(in.total, 1) * bb);
+        launch_to_f32(in.val.p, in.opf32.p, in.total * (int64_t)bb, st);
+    }
 
     h->row_cnt.ensure(nrows);
     h->row_off.ensure(nrows);
@@ -488,7 +492,9 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     ss.npairs = npairs;
     for (int p = 0; p < njob; ++p) {
         const int64_t np = job_pair[p + 1] - job_pair[p];
-        if (is_tc(ar_job[p])) ss.pairs_tc += np; else ss.pairs_simt += np;
+        if (is_tc(ar_job[p])) ss.pairs_tc += np;
+        else if (ar_job[p] == AR_FP64) ss.pairs_64 += np;
+        else ss.pairs_32 += np;
     }
     if (simt_mask) {
         h->pair_a.ensure(std::max<int64_t>(npairs, 1));
@@ -525,6 +531,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     h->keep.ensure(std::max<int64_t>(nslot, 1));
     NumArgs a{};
     a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
+    a.in_f32 = m32 ? in.opf32.p : nullptr;
     a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
     a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
     a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
@@ -535,6 +542,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
     const long long l0 = g_kernel_launches;
     if (nwork) launch_numeric_simt(a, simt_ar, st);
+    RDM_CUDA_TRY(cudaEventRecord(h->ev[5], st));
     if (nwork2) {
         NumArgs a2 = a;
         a2.work = h->work2.p;
@@ -571,15 +579,17 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     std::vector<int> rp(nrows + 1);
     d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
     sync(h);
-    float m01 = 0, m14 = 0, m42 = 0, m23 = 0;
+    float m01 = 0, m15 = 0, m54 = 0, m42 = 0, m23 = 0;
     cudaEventElapsedTime(&m01, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&m14, h->ev[1], h->ev[4]);
+    cudaEventElapsedTime(&m15, h->ev[1], h->ev[5]);   // first CUDA-core launch
+    cudaEventElapsedTime(&m54, h->ev[5], h->ev[4]);   // second (FP32) CUDA-core launch
     cudaEventElapsedTime(&m42, h->ev[4], h->ev[2]);
     cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);
     ss.ms[0] = m01;
-    ss.ms[1] = m42;   // tensor-core products
-    ss.ms[2] = m14;   // CUDA-core products
-    ss.ms[3] = m23;
+    ss.ms[1] = m42;                                   // tensor-core products
+    ss.ms[2] = simt_ar == AR_FP64 ? m15 : 0.f;        // FP64 products
+    ss.ms[3] = (simt_ar == AR_FP64 ? 0.f : m15) + m54;  // FP32 products (and copies)
+    ss.ms[4] = m23;
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -654,8 +664,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     JobTable jt = solve_jobs(nd);
     std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
     std::vector<int> act(S);
-    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_simt = 0;
-    double kms[4] = {0, 0, 0, 0};
+    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0;
+    double kms[5] = {0, 0, 0, 0, 0};
     int tc_launches = 0, simt_launches = 0;
     cudaEvent_t ev0, ev1;
     RDM_CUDA_TRY(cudaEventCreate(&ev0));
@@ -708,9 +718,10 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                     fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) && fabs(e) < 1e-2 * nocc[s])
                     stop = true;
                 // mixed modes: X0 refined in FP64 has reached the rounding floor of
-                // the idempotency error and the band energy no longer moves
-                if (mixed && y.tier == final_tier && n - y.tier_start >= 2 && y.have_eb &&
-                    fabs(e) <= 1e-12 * std::max(1.0, nocc[s]) && fabs(eb0 - y.eb0) < std::max(P.tol, 1e-12))
+                // the idempotency error (every eigenvalue within ~1e-12 of 0 or 1;
+                // one more step would only repeat the band energy)
+                if (mixed && y.tier == final_tier && n - y.tier_start >= 2 &&
+                    fabs(e) <= 1e-12 * std::max(1.0, nocc[s]))
                     stop = true;
             }
             y.have_eb = true;
@@ -780,12 +791,13 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         const double fpb = 2.0 * b * b * b;
         useful += (double)sst.npairs * fpb;
         flops_tc += (double)sst.pairs_tc * fpb;
-        flops_simt += (double)sst.pairs_simt * fpb;
-        issued += sst.issued_tc + (double)sst.pairs_simt * fpb;
+        flops_64 += (double)sst.pairs_64 * fpb;
+        flops_32 += (double)sst.pairs_32 * fpb;
+        issued += sst.issued_tc + (double)(sst.pairs_64 + sst.pairs_32) * fpb;
         nbytes += sst.bytes;
         tc_launches += sst.numeric_launches - sst.simt_launches;
         simt_launches += sst.simt_launches;
-        for (int k = 0; k < 4; ++k) kms[k] += sst.ms[k];
+        for (int k = 0; k < 5; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
             if (act[s]) {
@@ -804,7 +816,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                     "[rdm] step %d arith %d/%d pairs %lld slots %lld nnzb0 %lld %.3f ms (sym %.2f tc %.2f simt %.2f "
                     "cmp %.2f)\n",
                     it, (int)ar[0], (int)ar[jt.njob - 1], (long long)sst.npairs, (long long)sst.nslot,
-                    (long long)Xn.nnzb[0], ms, sst.ms[0], sst.ms[1], sst.ms[2], sst.ms[3]);
+                    (long long)Xn.nnzb[0], ms, sst.ms[0], sst.ms[1], sst.ms[2] + sst.ms[3], sst.ms[4]);
         }
     }
     cudaEventDestroy(ev0);
@@ -856,11 +868,11 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.time_ms = wall_ms;
         I.useful_flops = useful;
         I.issued_flops = issued;
-        for (int k = 0; k < 4; ++k) I.kernel_ms[k] = kms[k];
-        I.kernel_ms[4] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3]);
-        I.kernel_ms[5] = 0;
+        for (int k = 0; k < 5; ++k) I.kernel_ms[k] = kms[k];
+        I.kernel_ms[5] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3] - kms[4]);
         I.kernel_flops[0] = flops_tc;
-        I.kernel_flops[1] = flops_simt;
+        I.kernel_flops[1] = flops_64;
+        I.kernel_flops[2] = flops_32;
         I.kernel_launches = g_kernel_launches - launches0;
         I.tc_launches = tc_launches;
         I.simt_launches = simt_launches;

@@ -135,6 +135,156 @@ __global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 products of 32 x 32 blocks, tuned: 64 threads per output block, each a
+// 4 x 4 register tile at rows r0 + 8i and columns c0 + 8j (r0 = t/8,
+// c0 = t%8), so that the 16-byte shared-memory reads of a quarter warp hit 8
+// different banks (B rows) or broadcast (A rows).  Operand blocks come from
+// the FP32 copy of the master values, double-buffered with cp.async.
+// ---------------------------------------------------------------------------
+constexpr int kF32Ld = 36;   // padded row stride in floats (144 B, 16-byte aligned)
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
+    __shared__ __align__(16) float sA[2][32 * kF32Ld];
+    __shared__ __align__(16) float sB[2][32 * kF32Ld];
+    __shared__ float sC[32 * 33];
+    __shared__ float red[2];
+    const int tid = threadIdx.x;
+    const int r0 = tid >> 3, c0 = tid & 7;
+
+    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+        const int s = a.work[w];
+        const int i = a.slot_row[s];
+        const int sys = a.sys_of_row[i];
+        const int job = a.slot_job[s];
+        const float cl = (float)a.c_lin[sys], cq = (float)a.c_sq[sys];
+        const double tau = a.job_tau_sel[job] ? a.tau1[sys] : a.tau0[sys];
+        const int64_t p0 = a.pair_off[s], p1 = a.pair_off[s + 1];
+        const int st = a.slot_t[s], sx = a.slot_x[s];
+
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+
+        auto issue = [&](int64_t q, int buf) {
+            const float *ga = a.in_f32 + (size_t)a.pair_a[q] * 1024;
+            const float *gb = a.in_f32 + (size_t)a.pair_b[q] * 1024;
+#pragma unroll
+            for (int c = tid; c < 256; c += 64) {
+                const int row = c >> 3, col4 = (c & 7) * 4;
+                cp_async16(&sA[buf][row * kF32Ld + col4], ga + row * 32 + col4);
+                cp_async16(&sB[buf][row * kF32Ld + col4], gb + row * 32 + col4);
+            }
+            cp_async_commit();
+        };
+        __syncthreads();
+        if (p0 < p1) issue(p0, 0);
+        for (int64_t q = p0; q < p1; ++q) {
+            const int buf = (int)((q - p0) & 1);
+            if (q + 1 < p1) {
+                issue(q + 1, buf ^ 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncthreads();
+            const float *A_ = sA[buf];
+            const float *B_ = sB[buf];
+#pragma unroll
+            for (int kk = 0; kk < 32; kk += 4) {
+                float4 av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const float4 *>(&A_[(r0 + 8 * u) * kF32Ld + kk]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) bv[v] = *reinterpret_cast<const float4 *>(&B_[(c0 + 8 * v) * kF32Ld + kk]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float t = acc[u][v];
+                        t = fmaf(av[u].x, bv[v].x, t);
+                        t = fmaf(av[u].y, bv[v].y, t);
+                        t = fmaf(av[u].z, bv[v].z, t);
+                        t = fmaf(av[u].w, bv[v].w, t);
+                        acc[u][v] = t;
+                    }
+            }
+            __syncthreads();
+        }
+
+        // epilogue: C = c_lin X + c_sq acc, symmetrised on the diagonal, norm, truncation
+        const double *gx = sx >= 0 ? a.in_val + (size_t)sx * 1024 : nullptr;
+        const bool diag = (st == s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int r = r0 + 8 * u, c = c0 + 8 * v;
+                float x = cq * acc[u][v];
+                if (gx) x = fmaf(cl, (float)gx[r * 32 + c], x);
+                sC[r * 33 + c] = x;
+            }
+        __syncthreads();
+        float ss = 0.f;
+        if (diag) {
+            float sym[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = r0 + 8 * u, c = c0 + 8 * v;
+                    sym[u][v] = 0.5f * (sC[r * 33 + c] + sC[c * 33 + r]);
+                }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sC[(r0 + 8 * u) * 33 + c0 + 8 * v] = sym[u][v];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float x = sC[(r0 + 8 * u) * 33 + c0 + 8 * v];
+                ss = fmaf(x, x, ss);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if ((tid & 31) == 0) red[tid >> 5] = ss;
+        __syncthreads();
+        const float nrm = sqrtf(red[0] + red[1]) * (1.0f + 1e-6f);
+        const bool keep = ((double)nrm >= tau) && (nrm > 0.f);
+        double *o = a.out_val + (size_t)s * 1024;
+        for (int e = tid; e < 1024; e += 64) o[e] = (double)sC[(e >> 5) * 33 + (e & 31)];
+        if (!diag) {
+            double *ot = a.out_val + (size_t)st * 1024;
+            for (int e = tid; e < 1024; e += 64) ot[e] = (double)sC[(e & 31) * 33 + (e >> 5)];
+        }
+        if (tid == 0) {
+            a.out_nrm[s] = nrm;
+            a.keep[s] = keep;
+            if (!diag) { a.out_nrm[st] = nrm; a.keep[st] = keep; }
+        }
+    }
+}
+
+__global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ f, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) f[e] = (float)v[e];
+}
+
 template <int B, class T>
 void launch_b(const NumArgs &a, cudaStream_t st) {
     constexpr int NT = Cfg<B>::NT, LD = Cfg<B>::LD;
@@ -171,8 +321,21 @@ void dispatch(const NumArgs &a, cudaStream_t st) {
 
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st) {
     if (a.nwork == 0) return;
-    if (ar == AR_FP64) dispatch<double>(a, st);
-    else dispatch<float>(a, st);
+    if (ar == AR_FP64) {
+        dispatch<double>(a, st);
+    } else if (a.b == 32 && a.in_f32) {
+        const int grid = a.nwork < 152 * 32 ? a.nwork : 152 * 32;
+        k_numeric_f32_b32<<<grid, 64, 0, st>>>(a);
+        RDM_LAUNCH_CHECK();
+    } else {
+        dispatch<float>(a, st);
+    }
+}
+
+void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(val, f32, n);
+    RDM_LAUNCH_CHECK();
 }
 
 }  // namespace rdm

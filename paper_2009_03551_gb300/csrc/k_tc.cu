@@ -384,28 +384,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
 
     if (warp == 0) {
         // ---------------- producer: bulk copies of the operand blocks ----------------
-        if (lane == 0) {
-            uint32_t it = 0;
-            for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
-                const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
-                for (int64_t q = s0; q < s1; ++q, ++it) {
-                    const int st = it % kStages;
-                    const uint32_t ph = (it / kStages) & 1;
-                    if (!mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag)) break;
-                    mbar_expect_tx(&ctl->full[st], kStageBytes);
+        // The whole warp works: the block indices of the next K-step are loaded
+        // (one per lane 0..7) while the current step's 16 copies are issued by
+        // lanes 0..15 in parallel (lane m < 8: hi plane of slot m, lane 8 + m:
+        // lo plane of slot m).  Slot m < 4 is A block row m, m >= 4 B row m-4.
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < A.ntile && ok; t += gridDim.x) {
+            const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
+            int nxt = (s0 < s1 && lane < 8) ? A.steps[s0 * 8 + lane] : -1;
+            for (int64_t q = s0; q < s1; ++q, ++it) {
+                const int cur = nxt;
+                if (q + 1 < s1 && lane < 8) nxt = A.steps[(q + 1) * 8 + lane];
+                const int st = it % kStages;
+                const uint32_t ph = (it / kStages) & 1;
+                int waited = 1;
+                if (lane == 0) {
+                    waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag) ? 1 : 0;
+                    if (waited) mbar_expect_tx(&ctl->full[st], kStageBytes);
+                }
+                waited = __shfl_sync(0xffffffffu, waited, 0);
+                if (!waited) { ok = false; break; }
+                const int slot = lane & 7;
+                const int b = __shfl_sync(0xffffffffu, cur, slot);
+                if (lane < 16) {
                     uint8_t *dst = stages + st * kStageBytes;
-                    const int *ix = A.steps + q * 8;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const int b = ix[m];
-                        const uint16_t *h = b >= 0 ? A.hi + (size_t)b * kPlaneElems : A.zero;
-                        const uint16_t *l = b >= 0 ? A.lo + (size_t)b * kPlaneElems : A.zero;
-                        // A planes: [0, 8K) hi, [8K, 16K) lo; B planes: [16K, 24K) hi, [24K, 32K) lo
-                        const int side = m >> 2, r = m & 3;
-                        bulk_g2s(dst + side * 2 * kTilePlaneBytes + r * kPlaneBytes, h, kPlaneBytes, &ctl->full[st]);
-                        bulk_g2s(dst + side * 2 * kTilePlaneBytes + kTilePlaneBytes + r * kPlaneBytes, l, kPlaneBytes,
-                                 &ctl->full[st]);
-                    }
+                    const int side = slot >> 2, r = slot & 3, plane = lane >> 3;   // plane 0 hi, 1 lo
+                    const uint16_t *src = b >= 0 ? (plane ? A.lo : A.hi) + (size_t)b * kPlaneElems : A.zero;
+                    // A: [0, 8K) hi, [8K, 16K) lo; B: [16K, 24K) hi, [24K, 32K) lo
+                    bulk_g2s(dst + side * 2 * kTilePlaneBytes + plane * kTilePlaneBytes + r * kPlaneBytes, src,
+                             kPlaneBytes, &ctl->full[st]);
                 }
             }
         }

@@ -108,6 +108,7 @@ struct MatSet {
     DevBuf<float> nrm;        // total
     DevBuf<uint16_t> ophi;    // operand copies for the tensor-core tiers
     DevBuf<uint16_t> oplo;
+    DevBuf<float> opf32;      // FP32 operand copy for the CUDA-core FP32 products
     std::vector<int64_t> nnzb;   // host copy, per matrix
     int64_t total = 0;
     void release() {
@@ -202,6 +203,7 @@ void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const 
 // k_numeric.cu: C(upper slot) = c_lin X + c_sq sum(pairs); lower slot = transpose
 struct NumArgs {
     const double *in_val;
+    const float *in_f32;       // FP32 copy of in_val (FP32 products), may be null
     const float *in_nrm;
     const uint16_t *in_hi, *in_lo;
     const int *pair_a, *pair_b;
@@ -219,6 +221,8 @@ struct NumArgs {
     int b;
 };
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
+// FP32 copy of the FP64 master values (for the FP32 products)
+void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st);
 
 // k_compact.cu
 // upper slots of the active systems' jobs in job_mask, plus (with_inactive)

@@ -69,7 +69,7 @@ class rdm_info(C.Structure):
                 ("idempotency", C.c_double), ("band_energy0", C.c_double),
                 ("nnzb_p0", C.c_int64), ("nnzb_p1", C.c_int64 * 3), ("time_ms", C.c_double),
                 ("useful_flops", C.c_double), ("issued_flops", C.c_double),
-                ("kernel_ms", C.c_double * 6), ("kernel_flops", C.c_double * 2),
+                ("kernel_ms", C.c_double * 6), ("kernel_flops", C.c_double * 3),
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double)]
 

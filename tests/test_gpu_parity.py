@@ -136,6 +136,30 @@ def _sym_bsr(rng, n, b, density, scale=1.0):
     return a, Bsr.from_dense(a, b, drop_zero_blocks=False, keep_diagonal=True)
 
 
+@pytest.mark.parametrize("b", [4, 16, 32, 64])
+@pytest.mark.parametrize("terms", [1, 2])
+def test_block_product_fp32(rdm, b, terms):
+    """FP32 CUDA-core products (the tuned 32 x 32 kernel for b = 32) against
+    the dense FP64 product: FP32 rounding only (<= 2e-6 relative)."""
+    rng = np.random.default_rng(300 + b + terms)
+    n = 6 * b + b // 2
+    a, A = _sym_bsr(rng, n, b, 0.4)
+    bd, B = _sym_bsr(rng, n, b, 0.4, 0.5)
+    x, X = _sym_bsr(rng, n, b, 0.5, 0.25)
+    h = rdm.rdm_create(0)
+    try:
+        for c_lin, c_sq in ((0.0, 1.0), (2.0, -1.0)):
+            prod = a @ a if terms == 1 else a @ bd + bd @ a
+            ref = c_lin * x + c_sq * prod
+            res = rdm.rdm_block_product(h, A, B if terms == 2 else None, X, c_lin, c_sq, terms, 0.0,
+                                        rdm.MODES["fp32"])
+            got = res.to_dense()
+            assert rel_frobenius(got, ref) <= 2e-6
+            assert np.array_equal(got, got.T)
+    finally:
+        rdm.rdm_destroy(h)
+
+
 @pytest.mark.parametrize("b", [1, 2, 4, 8, 16, 32, 64])
 @pytest.mark.parametrize("terms", [1, 2])
 def test_block_product_fp64(rdm, b, terms):
