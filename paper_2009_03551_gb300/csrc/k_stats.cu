@@ -27,46 +27,61 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// row_part layout: [q][NB], q = 0 trace, 1 sumsq, 2 E0, 3+m-1 E1 of matrix m
-__global__ void k_row_stats(const int *__restrict__ rp, const int *__restrict__ col,
-                            const double *__restrict__ val, int nmat, int NB, int b,
-                            const int *__restrict__ hrp, const int *__restrict__ hcol,
-                            const double *__restrict__ hval, double *__restrict__ row_part) {
-    int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (i >= NB) return;
+// row_part layout: [q][NB], q = 0 trace, 1 sumsq, 2 E0, 3+m-1 E1 of matrix m.
+// One CTA per block row, warps over blocks, lanes over elements; the warp
+// partials are added in a fixed order.  Tr X0 and ||X0||_F^2 run over the
+// blocks of X0; the band energies Tr(X H0) only over the blocks of H0 (where
+// H0 is zero they get no contribution), each looking up the matching block of
+// X by binary search.
+constexpr int kStatWarps = 8;
+constexpr int kStatQ = 3 + 7;    // up to 7 first-order matrices
+
+__global__ void __launch_bounds__(kStatWarps * 32) k_row_stats(
+    const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val, int nmat, int NB, int b,
+    const int *__restrict__ hrp, const int *__restrict__ hcol, const double *__restrict__ hval,
+    double *__restrict__ row_part) {
+    __shared__ double sh[kStatWarps][kStatQ];
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int bb = b * b;
-    for (int m = 0; m < nmat; ++m) {
-        const int *rpm = rp + (size_t)m * NB;
-        double tr = 0.0, ss = 0.0, eb = 0.0;
-        for (int p = rpm[i]; p < rpm[i + 1]; ++p) {
-            int j = col[p];
+    double q[kStatQ];
+#pragma unroll
+    for (int k = 0; k < kStatQ; ++k) q[k] = 0.0;
+    // trace and squared norm of X0
+    for (int p = rp[i] + wid; p < rp[i + 1]; p += kStatWarps) {
+        const double *x = val + (size_t)p * bb;
+        const bool dg = col[p] == i;
+        for (int e = lane; e < bb; e += 32) {
+            const double v = x[e];
+            q[1] = fma(v, v, q[1]);
+            if (dg && (e / b) == (e % b)) q[0] += v;
+        }
+    }
+    // band energies over the pattern of H0
+    for (int ph = hrp[i] + wid; ph < hrp[i + 1]; ph += kStatWarps) {
+        const int j = hcol[ph];
+        const double *h = hval + (size_t)ph * bb;
+        for (int m = 0; m < nmat; ++m) {
+            const int *rpm = rp + (size_t)m * NB;
+            const int p = find_col(col, rpm[i], rpm[i + 1], j);
+            if (p < 0) continue;
             const double *x = val + (size_t)p * bb;
-            int q = find_col(hcol, hrp[i], hrp[i + 1], j);
-            const double *h = q >= 0 ? hval + (size_t)q * bb : nullptr;
-            for (int e = lane; e < bb; e += 32) {
-                double v = x[e];
-                if (m == 0) {
-                    ss += v * v;
-                    if (j == i && (e / b) == (e % b)) tr += v;
-                }
-                if (h) eb += v * h[e];
-            }
+            double eb = 0.0;
+            for (int e = lane; e < bb; e += 32) eb = fma(x[e], h[e], eb);
+            q[2 + m] += eb;
         }
-        if (m == 0) {
-            tr = warp_sum(tr);
-            ss = warp_sum(ss);
-        }
-        eb = warp_sum(eb);
-        if (lane == 0) {
-            if (m == 0) {
-                row_part[0 * (size_t)NB + i] = tr;
-                row_part[1 * (size_t)NB + i] = ss;
-                row_part[2 * (size_t)NB + i] = eb;
-            } else {
-                row_part[(size_t)(2 + m) * NB + i] = eb;
-            }
-        }
+    }
+#pragma unroll
+    for (int k = 0; k < kStatQ; ++k) {
+        const double v = warp_sum(q[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 + nmat) {
+        const int k = threadIdx.x;
+        double t = 0.0;
+        for (int w = 0; w < kStatWarps; ++w) t += sh[w][k];
+        row_part[(size_t)k * NB + i] = t;
     }
 }
 
@@ -125,9 +140,9 @@ void launch_row_stats(const int *row_ptr, const int *col, const double *val, int
                       int b, const int *h_row_ptr, const int *h_col, const double *h_val,
                       double *row_part, cudaStream_t st) {
     if (NB == 0) return;
-    int wpb = 8;
-    k_row_stats<<<(NB + wpb - 1) / wpb, wpb * 32, 0, st>>>(row_ptr, col, val, nmat, NB, b,
-                                                           h_row_ptr, h_col, h_val, row_part);
+    if (nmat > kStatQ - 2) throw Error{-1, "at most 7 first-order matrices"};
+    k_row_stats<<<NB, kStatWarps * 32, 0, st>>>(row_ptr, col, val, nmat, NB, b, h_row_ptr, h_col, h_val,
+                                                row_part);
     RDM_LAUNCH_CHECK();
 }
 
