@@ -1,7 +1,9 @@
 // Tensor-core numeric phase (tcgen05 + TMEM, sm_103a) for 32 x 32 blocks.
 //
-// Work decomposition.  Output blocks are grouped in 128 x 128 super-tiles
-// (block rows 4I..4I+3 x block columns 4J..4J+3, J >= I).  A super-tile is
+// Work decomposition.  Output blocks are grouped in 128 x 128 super-tiles:
+// block rows 4I..4I+3 times 4 block columns taken, in increasing order, from
+// the columns that these rows need (upper triangle of the mask), so that every
+// tile column is needed by at least one tile row.  A super-tile is
 // one MMA accumulator: D[128 x 128] = sum over K-steps of A[128 x 32] B[128 x 32]^T
 // where a K-step is one block index k at which some row of the tile's A rows
 // and some row of its B rows have a stored block (Gustavson's row merge,
@@ -38,13 +40,13 @@ namespace {
 
 constexpr int TB = 32;                       // block size handled here
 constexpr int TBL = 4;                       // blocks per tile edge
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
 constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
 constexpr int kTilePlaneBytes = TBL * kPlaneBytes;      // 8 KB: 4 blocks stacked
 constexpr int kStageBytes = 4 * kTilePlaneBytes;        // A_hi, A_lo, B_hi, B_lo
 constexpr int kThreads = 192;
-constexpr int kTileInts = 20;                // p, I, J, nsteps, slot[16]
+constexpr int kTileInts = 24;                // p, I, -, nsteps, slot[16], column j of each tile column[4]
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------------------
@@ -241,27 +243,33 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
         // neither produces tiles
         if (!T.active[T.sys_of_row[i]] || !((T.job_mask >> p) & 1u)) cur[m] = end[m];
     }
-    int n = 0;
-    int base = fill ? T.tile_off[t] : 0;
+    // the distinct columns needed by the 4 rows, in increasing order, are packed
+    // 4 at a time into tiles: every tile column is needed by at least one row
+    int ncol = 0, n = 0;
+    const int base = fill ? T.tile_off[t] : 0;
+    int *d = nullptr;
     while (true) {
         int jmin = 0x7fffffff;
         for (int m = 0; m < TBL; ++m)
-            if (cur[m] < end[m]) jmin = min(jmin, T.mcol[cur[m]] >> 2);
+            if (cur[m] < end[m]) jmin = min(jmin, T.mcol[cur[m]]);
         if (jmin == 0x7fffffff) break;
-        if (fill) {
-            int *d = T.tiles + (size_t)(base + n) * kTileInts;
-            d[0] = p; d[1] = I; d[2] = jmin; d[3] = 0;
-            for (int q = 0; q < 16; ++q) d[4 + q] = -1;
-            for (int m = 0; m < TBL; ++m)
-                while (cur[m] < end[m] && (T.mcol[cur[m]] >> 2) == jmin) {
-                    d[4 + m * 4 + (T.mcol[cur[m]] & 3)] = cur[m];
-                    ++cur[m];
-                }
-        } else {
-            for (int m = 0; m < TBL; ++m)
-                while (cur[m] < end[m] && (T.mcol[cur[m]] >> 2) == jmin) ++cur[m];
+        const int c = ncol & 3;
+        if (c == 0) {
+            if (fill) {
+                d = T.tiles + (size_t)(base + n) * kTileInts;
+                d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
+                for (int q = 0; q < 16; ++q) d[4 + q] = -1;
+                for (int q = 0; q < TBL; ++q) d[20 + q] = -1;
+            }
+            ++n;
         }
-        ++n;
+        if (fill) d[20 + c] = jmin;
+        for (int m = 0; m < TBL; ++m)
+            if (cur[m] < end[m] && T.mcol[cur[m]] == jmin) {
+                if (fill) d[4 + m * 4 + c] = cur[m];
+                ++cur[m];
+            }
+        ++ncol;
     }
     if (!fill) T.tile_cnt[t] = n;
 }
@@ -272,7 +280,7 @@ __global__ void k_tile_steps(TileBuild T, int fill) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T.ntile) return;
     const int *d = T.tiles + (size_t)t * kTileInts;
-    const int p = d[0], I = d[1], J = d[2];
+    const int p = d[0], I = d[1];
     const Job &job = T.jt.job[p];
     int64_t w = fill ? T.step_off[t] : 0;
     int n = 0;
@@ -280,11 +288,11 @@ __global__ void k_tile_steps(TileBuild T, int fill) {
         const int am = job.a[term], bm = job.b[term];
         int cur[2 * TBL], end[2 * TBL];
         for (int q = 0; q < TBL; ++q) {
-            int i = 4 * I + q, j = 4 * J + q;
+            const int i = 4 * I + q, j = d[20 + q];
             cur[q] = end[q] = 0;
             cur[TBL + q] = end[TBL + q] = 0;
             if (i < T.NB) { cur[q] = T.rp[am * T.NB + i]; end[q] = T.rp[am * T.NB + i + 1]; }
-            if (j < T.NB) { cur[TBL + q] = T.rp[bm * T.NB + j]; end[TBL + q] = T.rp[bm * T.NB + j + 1]; }
+            if (j >= 0) { cur[TBL + q] = T.rp[bm * T.NB + j]; end[TBL + q] = T.rp[bm * T.NB + j + 1]; }
         }
         while (true) {
             int kmin = 0x7fffffff;
@@ -356,8 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = smem_raw;                                       // kStages * 32 KB
     float *stage_ep = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes);   // 4 warps x 32 x 33
-    double *stage_x = reinterpret_cast<double *>(stage_ep + 4 * 32 * 33);           // 4 warps x 32 x 33
-    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_x + 4 * 32 * 33);
+    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_ep + 4 * 32 * 33);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &ctl->abort_flag;
@@ -385,11 +392,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     if (warp == 0) {
         // ---------------- producer: bulk copies of the operand blocks ----------------
         // The whole warp works: the block indices of the next K-step are loaded
-        // (one per lane 0..7) while the current step's 16 copies are issued by
+        // (one per lane 0..7) while the current step's copies are issued by
         // lanes 0..15 in parallel (lane m < 8: hi plane of slot m, lane 8 + m:
         // lo plane of slot m).  Slot m < 4 is A block row m, m >= 4 B row m-4.
+        // A slot whose block is missing needs zeros; a stage slot that already
+        // holds zeros from its previous use is not copied again (zmask).
         uint32_t it = 0;
         bool ok = true;
+        uint32_t zmask[kStages];
+#pragma unroll
+        for (int k = 0; k < kStages; ++k) zmask[k] = 0u;
         for (int t = blockIdx.x; t < A.ntile && ok; t += gridDim.x) {
             const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
             int nxt = (s0 < s1 && lane < 8) ? A.steps[s0 * 8 + lane] : -1;
@@ -398,19 +410,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 if (q + 1 < s1 && lane < 8) nxt = A.steps[(q + 1) * 8 + lane];
                 const int st = it % kStages;
                 const uint32_t ph = (it / kStages) & 1;
+                const int slot = lane & 7;
+                const int b = __shfl_sync(0xffffffffu, cur, slot);
+                const uint32_t zbits = __ballot_sync(0xffffffffu, lane < 8 && cur < 0) & 0xffu;
+                uint32_t zprev = 0u;
+#pragma unroll
+                for (int k = 0; k < kStages; ++k)
+                    if (k == st) zprev = zmask[k];
+                const bool skip = (b < 0) && ((zprev >> slot) & 1u);
+                const uint32_t need = __ballot_sync(0xffffffffu, lane < 16 && !skip);
                 int waited = 1;
                 if (lane == 0) {
                     waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag) ? 1 : 0;
-                    if (waited) mbar_expect_tx(&ctl->full[st], kStageBytes);
+                    if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * kPlaneBytes);
                 }
                 waited = __shfl_sync(0xffffffffu, waited, 0);
                 if (!waited) { ok = false; break; }
-                const int slot = lane & 7;
-                const int b = __shfl_sync(0xffffffffu, cur, slot);
-                if (lane < 16) {
+#pragma unroll
+                for (int k = 0; k < kStages; ++k)
+                    if (k == st) zmask[k] = zbits;
+                if (lane < 16 && !skip) {
                     uint8_t *dst = stages + st * kStageBytes;
                     const int side = slot >> 2, r = slot & 3, plane = lane >> 3;   // plane 0 hi, 1 lo
-                    const uint16_t *src = b >= 0 ? (plane ? A.lo : A.hi) + (size_t)b * kPlaneElems : A.zero;
+                    // zero planes: one per CTA and slot, so that the CTAs do not all
+                    // read the same few L2 sectors
+                    const uint16_t *src = b >= 0 ? (plane ? A.lo : A.hi) + (size_t)b * kPlaneElems
+                                                 : A.zero + ((size_t)blockIdx.x * 16 + lane) * kPlaneElems;
                     // A: [0, 8K) hi, [8K, 16K) lo; B: [16K, 24K) hi, [24K, 32K) lo
                     bulk_g2s(dst + side * 2 * kTilePlaneBytes + plane * kTilePlaneBytes + r * kPlaneBytes, src,
                              kPlaneBytes, &ctl->full[st]);
@@ -465,7 +490,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
         // ---------------- epilogue: warps 2..5, TMEM lane quarter = block row ----------------
         const int eq = warp & 3;                       // lanes 32*eq .. 32*eq+31
         float *S = stage_ep + (warp - 2) * 32 * 33;
-        double *SX = stage_x + (warp - 2) * 32 * 33;
         uint32_t lt = 0;
         for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
@@ -494,14 +518,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 const double tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
                 const int sx = A.slot_x[s], stt = A.slot_t[s];
                 const bool diag = (stt == s);
-                // linear term: stage X_old coalesced, each lane then owns its row
+                // linear term: each lane reads its own row (256 contiguous bytes)
                 if (sx >= 0 && cl != 0.f) {
-                    const double *gx = A.in_val + (size_t)sx * kPlaneElems;
-                    for (int r = 0; r < 32; ++r) SX[r * 33 + lane] = gx[r * 32 + lane];
-                    __syncwarp();
+                    const double2 *gx = reinterpret_cast<const double2 *>(A.in_val + (size_t)sx * kPlaneElems + lane * 32);
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[c] = fmaf(cl, (float)SX[lane * 33 + c], cq * acc[c]);
-                    __syncwarp();
+                    for (int c = 0; c < 16; ++c) {
+                        const double2 x2 = gx[c];
+                        acc[2 * c] = fmaf(cl, (float)x2.x, cq * acc[2 * c]);
+                        acc[2 * c + 1] = fmaf(cl, (float)x2.y, cq * acc[2 * c + 1]);
+                    }
                 } else {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) acc[c] = cq * acc[c];
@@ -553,8 +578,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 4 * 32 * 33 * sizeof(float) +
-                              4 * 32 * 33 * sizeof(double) + sizeof(SmemCtl) + 1024;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 4 * 32 * 33 * sizeof(float) + sizeof(SmemCtl) + 1024;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel exceeds 227 KB");
 
 }  // namespace
 
@@ -587,9 +612,13 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
                          int NB, const TcPlan &plan, cudaStream_t st) {
     if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
     if (plan.ntile == 0) return 0.0;
-    if (!w.zero.p) {
-        w.zero.ensure(kPlaneElems);
-        RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, kPlaneElems * sizeof(uint16_t), st));
+    int dev = 0, nsm = 0;
+    RDM_CUDA_TRY(cudaGetDevice(&dev));
+    RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t zero_elems = (size_t)nsm * 16 * kPlaneElems;   // 16 zero planes per CTA
+    if (!w.zero.p || w.zero.cap < zero_elems) {
+        w.zero.ensure(zero_elems);
+        RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, w.zero.cap * sizeof(uint16_t), st));
     }
     TcArgs A{};
     A.hi = in.ophi.p; A.lo = in.oplo.p; A.zero = w.zero.p;
@@ -612,9 +641,6 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
         RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
         attr = true;
     }
-    int dev = 0, nsm = 0;
-    RDM_CUDA_TRY(cudaGetDevice(&dev));
-    RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = plan.ntile < nsm ? plan.ntile : nsm;
     k_tc_bf16x3<<<grid, kThreads, kSmemBytes, st>>>(A);
     RDM_LAUNCH_CHECK();
