@@ -49,7 +49,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default=os.environ.get("RDM_BENCH_MODE", "mixed_fp16"),
                     choices=["fp64", "fp32", "mixed_bf16", "mixed_fp16"])
-    ap.add_argument("--atoms", type=int, default=2000)
+    ap.add_argument("--atoms", type=int, default=2000, help="atoms of the cluster workload")
+    ap.add_argument("--workload", default="cluster",
+                    help="cluster (default: the 2,000-atom cluster, or --atoms), batch24 (24 uneven "
+                         "chains/clusters, 300-8,000 atoms), slab<N> (30-bohr slab of N atoms)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -207,13 +210,19 @@ def to_device(sys_, torch, dev):
     return s
 
 
-def run_ours(args, sys_, rank, world, torch, dist):
+def alphas(sol, nsys):
+    return np.stack([sol.alpha(k) for k in range(nsys)])
+
+
+def run_ours(args, systems, wname, rank, world, torch, dist):
     from paper_2009_03551_gb300 import rdm
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    dsys = to_device(sys_, torch, dev)
+    nsys = len(systems)
+    sys_ = systems[0]
+    dsys = [to_device(s, torch, dev) for s in systems]
     torch.cuda.synchronize()
 
     sol = rdm.Solver(dev.index, stream.cuda_stream)
@@ -252,7 +261,7 @@ def run_ours(args, sys_, rank, world, torch, dist):
     else:
         t_max = t_local
     s_per_solve = t_max / (args.steps * world)
-    alpha_m = sol.alpha()
+    alpha_m = alphas(sol, nsys)
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
     kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(6)]
@@ -273,8 +282,10 @@ def run_ours(args, sys_, rank, world, torch, dist):
         a1.record(stream)
         torch.cuda.synchronize()
         t64 = a0.elapsed_time(a1) / 1e3
-        alpha64 = s64.alpha()
-        rel = float(np.max(np.abs(alpha_m - alpha64)) / np.max(np.abs(alpha64)))
+        alpha64 = alphas(s64, nsys)
+        # largest relative alpha error over the systems (each normalised by its own max |alpha|)
+        rel = float(max(np.max(np.abs(alpha_m[k] - alpha64[k])) / np.max(np.abs(alpha64[k]))
+                        for k in range(nsys)))
         fp64 = {"s_per_solve": t64, "steps": 1, "warmup": 0, "iterations": i64.iterations,
                 "tflops": i64.useful_flops / t64 / 1e12, "alpha_rel_diff_mixed_vs_fp64": rel,
                 "speedup_mixed_vs_fp64": t64 / s_per_solve}
@@ -283,22 +294,24 @@ def run_ours(args, sys_, rank, world, torch, dist):
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for m in [sys_.h0, *sys_.h1])
+        h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for s in systems for m in [s.h0, *s.h1])
         se = rdm.Solver(dev.index, stream.cuda_stream)
         se.set_params(**params)
-        se.load(sys_)
+        se.load(systems)
         se.solve()   # warm-up of the host path
         torch.cuda.synchronize()
         d2h = 0
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
-            se.load(sys_)
+            se.load(systems)
             se.solve()
-            d2h = 72
-            for d in range(len(sys_.h1)):
-                p = se.p1(0, d)
-                d2h += p.row_ptr.nbytes + p.col_idx.nbytes + p.vals.nbytes
-            _ = se.alpha()
+            d2h = 0
+            for k in range(nsys):
+                d2h += 72
+                for d in range(len(systems[k].h1)):
+                    p = se.p1(k, d)
+                    d2h += p.row_ptr.nbytes + p.col_idx.nbytes + p.vals.nbytes
+                _ = se.alpha(k)
         torch.cuda.synchronize()
         te = (time.perf_counter() - t) / args.e2e_steps
         e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
@@ -336,13 +349,18 @@ def run_ours(args, sys_, rank, world, torch, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed_bf16": "bf16x3+f64",
                                                                 "mixed_fp16": "fp16x3+f64"}[mode],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": mode, "atoms": args.atoms, "N": sys_.n, "b": sys_.b,
-                       "tau": 1e-6, "tol": 1e-9, "directions": 3, "iterations": last.iterations,
-                       "nnzb_p0": last.nnzb_p0, "nnzb_p1": list(last.nnzb_p1),
+            "config": {"workload": wname, "mode": mode, "systems": nsys,
+                       "atoms": int(sum(s.n_atoms for s in systems)), "N": int(sum(s.n for s in systems)),
+                       "b": sys_.b, "tau": 1e-6, "tol": 1e-9, "directions": 3,
+                       "iterations": int(max(sol.info(k).iterations for k in range(nsys))),
+                       "nnzb_p0": int(sum(sol.info(k).nnzb_p0 for k in range(nsys))),
+                       "nnzb_p1": [int(sum(sol.info(k).nnzb_p1[d] for k in range(nsys))) for d in range(3)],
+                       "nnzb_per_block_row_p0": float(sum(sol.info(k).nnzb_p0 for k in range(nsys)) /
+                                                      sum(s.h0.nb for s in systems)),
                        "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
             "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
             "block_spgemm_tflops": achieved_all / 1e12,
-            "alpha_diag": [float(alpha_m[k, k]) for k in range(3)],
+            "alpha_diag": [float(alpha_m[0][k, k]) for k in range(3)],
             "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
@@ -353,12 +371,29 @@ def run_ours(args, sys_, rank, world, torch, dist):
     return line
 
 
+def make_workload(args):
+    """(name, list of systems) of the requested workload."""
+    from synth import make_batch_config, make_config
+    w = args.workload
+    if w == "cluster":
+        cfg = 2 if args.atoms <= 2000 else 3
+        s = make_config(cfg, n_atoms=args.atoms)
+        name = WORKLOAD if args.atoms == 2000 else f"cluster-{args.atoms}-atoms-N{s.n}-b32-tau1e-6-xyz"
+        return name, [s]
+    if w == "batch24":
+        return "batch-24-systems-300-8000-atoms-b32-tau1e-6-xyz", make_batch_config(24, b=32)
+    if w.startswith("slab"):
+        n = int(w[4:])
+        return f"slab-{n}-atoms-30bohr-b32-tau1e-6-xyz", [make_config(5, n_atoms=n)]
+    raise SystemExit(f"unknown workload {w}")
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    from synth import make_config
-    sys_ = make_config(2, n_atoms=args.atoms)
+    wname, systems = make_workload(args)
+    sys_ = systems[0]
 
     if args.impl == "reference":
         run_reference(args, sys_, rank)
@@ -376,8 +411,8 @@ def main():
         b.build()
     if dist is not None:
         dist.barrier()
-    line = run_ours(args, sys_, rank, world, torch, dist)
-    if rank == 0 and world == 1 and not args.no_cpu:
+    line = run_ours(args, systems, wname, rank, world, torch, dist)
+    if rank == 0 and world == 1 and not args.no_cpu and len(systems) == 1 and sys_.n <= 16000:
         per_prod, per_solve, iters, n_prod = oracle_sample(sys_)
         line["cpu_baseline"] = {"value": per_solve, "unit": "s", "cores": cores(), "kind": "oracle",
                                 "sample": f"one dense FP64 {sys_.n}x{sys_.n} product of the oracle's TC2 "

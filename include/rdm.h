@@ -114,7 +114,9 @@ typedef struct {
     int32_t verbose;        /* 1: per-iteration log to stderr */
     int32_t refine_x1;      /* mixed modes, final tier, arithmetic of the first-order products
                                (RDM_REFINE_*); X0^2 is always FP64 there */
-    int32_t reserved[4];
+    int32_t symbolic_hash;  /* 1: use the hash-table symbolic phase (otherwise chosen only for
+                               systems above 8,192 block rows); results are identical */
+    int32_t reserved[3];
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */

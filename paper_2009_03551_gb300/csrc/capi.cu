@@ -84,6 +84,7 @@ struct rdm_handle {
     DevBuf<double> out_val, row_part, sys_q;
     DevBuf<float> out_nrm;
     DevBuf<uint8_t> keep;
+    DevBuf<unsigned long long> class_pairs;
     DevBuf<double> row_lo, row_hi;
     TcWork tcw;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -247,8 +248,6 @@ void assemble(rdm_handle *h) {
         h->row0[s] = NB;
         h->nbs[s] = h->hs[s].nb;
         h->norb[s] = h->hs[s].n;
-        if (h->hs[s].nb > kSymMaxNs)
-            throw Error{RDM_EINVAL, "systems above " + std::to_string(kSymMaxNs) + " block rows are not supported"};
         NB += h->hs[s].nb;
     }
     h->NB = NB;
@@ -403,36 +402,49 @@ void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0) {
     }
 }
 
-StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, const Arith *ar_job) {
+// tab[t][p]: arithmetic of job p for the systems in tier t; tiers_present:
+// bit t set when some active system is in tier t (the per-system tiers are in
+// h->sd.tier on the device)
+StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
+                   const Arith (*tab)[kMaxJobs], unsigned tiers_present) {
     cudaStream_t st = h->stream;
     const int NB = in.NB, b = in.b, njob = jt.njob;
     const size_t bb = (size_t)b * b;
     const int nrows = njob * NB;
     int max_ns = *std::max_element(h->nbs.begin(), h->nbs.end());
     StepStats ss;
-    unsigned tc_mask = 0, m64 = 0, m32 = 0;
+    JobMask tcm{}, m64{}, m32{}, simt{};
     Arith tc_ar = AR_FP16X3;
-    for (int p = 0; p < njob; ++p) {
-        if (is_tc(ar_job[p])) {
-            tc_mask |= 1u << p;
-            tc_ar = ar_job[p];
-        } else if (ar_job[p] == AR_FP64) {
-            m64 |= 1u << p;
-        } else {
-            m32 |= 1u << p;
+    bool any_tc = false, any64 = false, any32 = false;
+    for (int t = 0; t < kMaxTiers; ++t) {
+        if (!((tiers_present >> t) & 1u)) continue;
+        for (int p = 0; p < njob; ++p) {
+            const Arith a = tab[t][p];
+            if (is_tc(a)) {
+                tcm.m[t] |= 1u << p;
+                tc_ar = a;
+                any_tc = true;
+            } else if (a == AR_FP64) {
+                m64.m[t] |= 1u << p;
+                any64 = true;
+            } else {
+                m32.m[t] |= 1u << p;
+                any32 = true;
+            }
         }
+        simt.m[t] = m64.m[t] | m32.m[t];
     }
-    const unsigned simt_mask = m64 | m32;
     // first CUDA-core launch: the FP64 jobs (else the FP32 ones) plus the copies
     // of converged systems; second launch: the FP32 jobs when both kinds exist
-    const Arith simt_ar = m64 ? AR_FP64 : AR_FP32;
-    const unsigned first_mask = m64 ? m64 : m32;
-    const unsigned second_mask = (m64 && m32) ? m32 : 0u;
-    const bool tc = tc_mask != 0;
+    const Arith simt_ar = any64 ? AR_FP64 : AR_FP32;
+    const JobMask first_mask = any64 ? m64 : m32;
+    const bool second = any64 && any32;
+    const bool tc = any_tc;
+    const bool m32_any = any32;
     h->ensure_events();
     RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
-    if (m32) {
+    if (m32_any) {
         in.opf32.ensure(std::max<int64_t>(in.total, 1) * bb);
         launch_to_f32(in.val.p, in.opf32.p, in.total * (int64_t)bb, st);
     }
@@ -449,12 +461,14 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
         RDM_CUDA_TRY(cudaMemsetAsync(h->counters.p, 0, 8 * sizeof(int), st));
         SymOut so{h->row_cnt.p, h->row_off.p, h->pool_col.p, h->pool_npair.p, h->counters.p,
                   (int)h->pool_col.cap, h->counters.p + 1};
-        launch_symbolic(in, jt, h->sd, h->S, so, st, max_ns);
+        launch_symbolic(in, jt, h->sd, h->S, so, st, h->prm.symbolic_hash ? kSymMaxNs + 1 : max_ns);
         int hc[2];
         d2h(hc, h->counters.p, 2, st);
         sync(h);
         top = hc[0];
         if (!hc[1]) break;
+        if (hc[1] == 2)
+            throw Error{RDM_ECAPACITY, "a block row of a product reaches more than 6144 distinct block columns"};
         cap = (int64_t)top + top / 4 + 1024;
         if (attempt == 3) throw Error{RDM_ECAPACITY, "symbolic pool overflow after retries"};
     }
@@ -482,21 +496,19 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     scan_exclusive_i64(h->slot_npair.p, h->pair_off.p, (int)nslot, h->scan_tmp64.p, st);
     int64_t npairs = 0;
     d2h(&npairs, h->pair_off.p + nslot, 1, st);
-    // block triples per job: slots of job p are [out_rp[p NB], out_rp[(p+1) NB])
-    std::vector<int> job_slot(njob + 1);
-    for (int p = 0; p <= njob; ++p) d2h(&job_slot[p], h->out_rp.p + (size_t)p * NB, 1, st);
-    sync(h);
-    std::vector<int64_t> job_pair(njob + 1);
-    for (int p = 0; p <= njob; ++p) d2h(&job_pair[p], h->pair_off.p + job_slot[p], 1, st);
+    // block triples per kernel class (tensor cores, FP64, FP32) for the accounting
+    h->class_pairs.ensure(4);
+    RDM_CUDA_TRY(cudaMemsetAsync(h->class_pairs.p, 0, 4 * sizeof(unsigned long long), st));
+    launch_class_pairs(h->slot_row.p, mcol, h->slot_npair.p, h->slot_job.p, nslot, h->sd.sys_of_row.p,
+                       h->sd.active.p, h->sd.tier.p, tcm, m64, m32, h->class_pairs.p, st);
+    unsigned long long cls[3] = {0, 0, 0};
+    d2h(cls, h->class_pairs.p, 3, st);
     sync(h);
     ss.npairs = npairs;
-    for (int p = 0; p < njob; ++p) {
-        const int64_t np = job_pair[p + 1] - job_pair[p];
-        if (is_tc(ar_job[p])) ss.pairs_tc += np;
-        else if (ar_job[p] == AR_FP64) ss.pairs_64 += np;
-        else ss.pairs_32 += np;
-    }
-    if (simt_mask) {
+    ss.pairs_tc = (int64_t)cls[0];
+    ss.pairs_64 = (int64_t)cls[1];
+    ss.pairs_32 = (int64_t)cls[2];
+    if (any64 || any32) {
         h->pair_a.ensure(std::max<int64_t>(npairs, 1));
         h->pair_b.ensure(std::max<int64_t>(npairs, 1));
     }
@@ -506,24 +518,24 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     // builds its own K-steps); slot_x / slot_t for every job
     launch_pairs(in, jt, h->sd, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p, h->pair_off.p,
                  nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st,
-                 simt_mask);
+                 simt);
     h->work.ensure(std::max<int64_t>(nslot, 1));
-    // CUDA-core work: the jobs in simt_mask and the copies of converged systems
+    // CUDA-core work: the selected jobs and the copies of converged systems
     launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
-                      h->sd.active.p, h->slot_job.p, first_mask, 1);
-    if (second_mask) {
+                      h->sd.active.p, h->slot_job.p, h->sd.tier.p, first_mask, 1);
+    if (second) {
         h->work2.ensure(std::max<int64_t>(nslot, 1));
         launch_build_work(h->slot_row.p, mcol, nslot, h->work2.p, h->counters.p + 4, st, h->sd.sys_of_row.p,
-                          h->sd.active.p, h->slot_job.p, second_mask, 0);
+                          h->sd.active.p, h->slot_job.p, h->sd.tier.p, m32, 0);
     }
     TcPlan plan{};
-    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tc_mask, st);
+    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tcm, st);
     int hc[3];
     d2h(hc, h->counters.p + 2, 3, st);
     sync(h);
     if (hc[0]) throw Error{RDM_ECUDA, "internal error: pair lists inconsistent with the mask (code " + std::to_string(hc[0]) + ")"};
     const int nwork = hc[1];
-    const int nwork2 = second_mask ? hc[2] : 0;
+    const int nwork2 = second ? hc[2] : 0;
 
     // numeric + fused truncation
     h->out_val.ensure(std::max<int64_t>(nslot, 1) * bb);
@@ -531,7 +543,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt, c
     h->keep.ensure(std::max<int64_t>(nslot, 1));
     NumArgs a{};
     a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
-    a.in_f32 = m32 ? in.opf32.p : nullptr;
+    a.in_f32 = m32_any ? in.opf32.p : nullptr;
     a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
     a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
     a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
@@ -767,15 +779,24 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             h->log.push_back(L);
         }
         if (!any_active) break;
-        // all active systems of this step share one arithmetic per launch; a
-        // batch whose systems sit in different tiers runs the higher precision
-        int tier = final_tier;
-        for (int s = 0; s < S; ++s)
-            if (act[s]) tier = std::min(tier, ss[s].tier);
-        for (int s = 0; s < S; ++s)
-            if (act[s] && ss[s].tier != tier && mixed) tier = final_tier;
-        Arith ar[kMaxJobs];
-        tier_arith(P.mode, tier, jt.njob, ar, P.refine_x1);
+        // every system computes in its own tier; the kernels select the rows of
+        // each tier through per-tier job masks
+        Arith tab[kMaxTiers][kMaxJobs];
+        unsigned tiers_present = 0;
+        std::vector<int> tier_of(S, 0);
+        for (int t = 0; t <= final_tier; ++t) tier_arith(P.mode, t, jt.njob, tab[t], P.refine_x1);
+        for (int s = 0; s < S; ++s) {
+            tier_of[s] = ss[s].tier;
+            if (act[s]) tiers_present |= 1u << ss[s].tier;
+        }
+        Arith ar[kMaxJobs];   // arithmetic of the lowest tier present (log only)
+        for (int p = 0; p < jt.njob; ++p) ar[p] = tab[0][p];
+        for (int t = 0; t <= final_tier; ++t)
+            if ((tiers_present >> t) & 1u) {
+                for (int p = 0; p < jt.njob; ++p) ar[p] = tab[t][p];
+                break;
+            }
+        h2d(h->sd.tier.p, tier_of.data(), S, st);
         h2d(h->sd.c_lin.p, c_lin.data(), S, st);
         h2d(h->sd.c_sq.p, c_sq.data(), S, st);
         h2d(h->sd.tau0.p, t0.data(), S, st);
@@ -783,7 +804,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         h2d(h->sd.active.p, act.data(), S, st);
         RDM_CUDA_TRY(cudaEventRecord(ev0, st));
         MatSet &Xn = h->X[1 - h->cur];
-        StepStats sst = multiply(h, Xc, Xn, jt, ar);
+        StepStats sst = multiply(h, Xc, Xn, jt, tab, tiers_present);
         RDM_CUDA_TRY(cudaEventRecord(ev1, st));
         RDM_CUDA_TRY(cudaEventSynchronize(ev1));
         float ms = 0;
@@ -1145,7 +1166,6 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         if (!A || (terms == 2 && !B)) return fail(h, RDM_EINVAL, "null operand");
         if (terms != 1 && terms != 2) return fail(h, RDM_EINVAL, "terms must be 1 or 2");
         if (!(tau >= 0) || mode < 0 || mode > 3) return fail(h, RDM_EINVAL, "bad tau or mode");
-        if (A->nb > kSymMaxNs) return fail(h, RDM_EINVAL, "matrix too large for the product primitive");
         // a private single-system context so that the solve state is untouched
         rdm_handle t;
         t.device = h->device;
@@ -1206,6 +1226,8 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         SysDev &sd = t.sd;
         sd.row0.ensure(1); sd.nbs.ensure(1); sd.n_orb.ensure(1); sd.sys_of_row.ensure(NB);
         sd.c_lin.ensure(1); sd.c_sq.ensure(1); sd.tau0.ensure(1); sd.tau1.ensure(1); sd.active.ensure(1);
+        sd.tier.ensure(1);
+        RDM_CUDA_TRY(cudaMemsetAsync(sd.tier.p, 0, sizeof(int), t.stream));
         RDM_CUDA_TRY(cudaMemsetAsync(sd.row0.p, 0, sizeof(int), t.stream));
         RDM_CUDA_TRY(cudaMemsetAsync(sd.sys_of_row.p, 0, NB * sizeof(int), t.stream));
         int one = 1;
@@ -1222,10 +1244,10 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         int ix = X ? idx[2] : -1;
         if (terms == 1) jt.job[0] = Job{0, ix, 1, {ia, ia}, {ia, ia}, 0};
         else jt.job[0] = Job{0, ix, 2, {ia, ib}, {ib, ia}, 0};
-        Arith ar[kMaxJobs];
-        tier_arith(mode, 0, jt.njob, ar);
+        Arith tab[kMaxTiers][kMaxJobs];
+        tier_arith(mode, 0, jt.njob, tab[0]);
         MatSet res;
-        multiply(&t, in, res, jt, ar);
+        multiply(&t, in, res, jt, tab, 1u);
         int64_t n = res.nnzb[0];
         if (needed) *needed = n;
         if (!out || !out->row_ptr || out->nnzb < n || (n && (!out->col_idx || !out->vals))) {

@@ -15,19 +15,46 @@ namespace {
 __global__ void k_build_work(const int *__restrict__ slot_row, const int *__restrict__ out_col,
                              int64_t nslot, int *work, int *nwork, const int *__restrict__ sys_of_row,
                              const int *__restrict__ active, const int *__restrict__ slot_job,
-                             unsigned job_mask, int with_inactive) {
+                             const int *__restrict__ sys_tier, JobMask job_mask, int with_inactive) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lane = threadIdx.x & 31;
     bool up = s < nslot && out_col[s] >= slot_row[s];
     if (up) {
-        const bool act = active[sys_of_row[slot_row[s]]] != 0;
-        up = act ? ((job_mask >> slot_job[s]) & 1u) != 0 : with_inactive != 0;
+        const int sys = sys_of_row[slot_row[s]];
+        const bool act = active[sys] != 0;
+        up = act ? ((job_mask.m[sys_tier[sys] & (kMaxTiers - 1)] >> slot_job[s]) & 1u) != 0 : with_inactive != 0;
     }
     unsigned m = __ballot_sync(0xffffffffu, up);
     int base = 0;
     if (lane == 0 && m) base = atomicAdd(nwork, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (up) work[base + __popc(m & ((1u << lane) - 1u))] = (int)s;
+}
+
+__global__ void k_class_pairs(const int *__restrict__ slot_row, const int *__restrict__ out_col,
+                              const int *__restrict__ slot_npair, const int *__restrict__ slot_job, int64_t nslot,
+                              const int *__restrict__ sys_of_row, const int *__restrict__ active,
+                              const int *__restrict__ sys_tier, JobMask tc, JobMask m64, JobMask m32,
+                              unsigned long long *out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c[3] = {0, 0, 0};
+    if (s < nslot && out_col[s] >= slot_row[s]) {
+        const int sys = sys_of_row[slot_row[s]];
+        if (active[sys]) {
+            const int t = sys_tier[sys] & (kMaxTiers - 1);
+            const unsigned bit = 1u << slot_job[s];
+            const unsigned long long np = (unsigned long long)slot_npair[s];
+            if (tc.m[t] & bit) c[0] = np;
+            else if (m64.m[t] & bit) c[1] = np;
+            else if (m32.m[t] & bit) c[2] = np;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long v = c[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&out[k], v);
+    }
 }
 
 __global__ void k_compact_count(const int *__restrict__ rp, const uint8_t *__restrict__ keep,
@@ -79,11 +106,21 @@ __global__ void k_compact_copy(const int *__restrict__ rp, const int *__restrict
 
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot, int *work,
                        int *nwork, cudaStream_t st, const int *sys_of_row, const int *active,
-                       const int *slot_job, unsigned job_mask, int with_inactive) {
+                       const int *slot_job, const int *sys_tier, JobMask job_mask, int with_inactive) {
     if (nslot == 0) return;
     int64_t grid = (nslot + 255) / 256;
     k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, nslot, work, nwork, sys_of_row,
-                                                 active, slot_job, job_mask, with_inactive);
+                                                 active, slot_job, sys_tier, job_mask, with_inactive);
+    RDM_LAUNCH_CHECK();
+}
+
+void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot_npair, const int *slot_job,
+                        int64_t nslot, const int *sys_of_row, const int *active, const int *sys_tier,
+                        JobMask tc, JobMask m64, JobMask m32, unsigned long long *out, cudaStream_t st) {
+    if (nslot == 0) return;
+    const int64_t grid = (nslot + 255) / 256;
+    k_class_pairs<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, slot_npair, slot_job, nslot, sys_of_row,
+                                                  active, sys_tier, tc, m64, m32, out);
     RDM_LAUNCH_CHECK();
 }
 

@@ -200,6 +200,161 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic(SymParams P) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same symbolic step for systems wider than the dense accumulator: the
+// columns a row reaches (a few hundred, independent of the system size) go to
+// an open-addressing hash table in shared memory; the kept columns are then
+// sorted (bitonic) so that the row's list comes out in increasing order.  The
+// fixed-point bound and the keep rule are those of k_symbolic.
+// ---------------------------------------------------------------------------
+constexpr int kHashSlots = 8192;                 // 128 KB: key + acc + cnt
+constexpr int kHashMaxFill = kHashSlots * 3 / 4;
+
+__device__ __forceinline__ int hash_slot(int j) { return (int)(((unsigned)j * 2654435761u) >> (32 - 13)); }
+
+// returns the slot of key j (inserting it), or -1 when the table is full
+__device__ __forceinline__ int hash_find(int *keys, int j, int *fill) {
+    int h = hash_slot(j);
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const int k = keys[h];
+        if (k == j) return h;
+        if (k < 0) {
+            const int prev = atomicCAS(&keys[h], -1, j);
+            if (prev == -1) {
+                if (atomicAdd(fill, 1) >= kHashMaxFill) return -1;
+                return h;
+            }
+            if (prev == j) return h;
+        }
+        h = (h + 1) & (kHashSlots - 1);
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(kSymThreads) k_symbolic_hash(SymParams P) {
+    extern __shared__ unsigned long long sm_acc[];                 // kHashSlots
+    unsigned int *cnt = reinterpret_cast<unsigned int *>(sm_acc + kHashSlots);
+    int *keys = reinterpret_cast<int *>(cnt + kHashSlots);
+    __shared__ int sh_scan[32];
+    __shared__ int sh_off, sh_fill, sh_bad;
+    const int i = blockIdx.x, p = blockIdx.y;
+    const int NB = P.NB;
+    const Job &job = P.jt.job[p];
+    const int s = P.sys_of_row[i];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int out_r = p * NB + i;
+
+    if (!P.active[s]) {
+        const int xm = job.xmat;
+        int lo = P.rp[xm * NB + i], hi = P.rp[xm * NB + i + 1];
+        int n = hi - lo;
+        if (tid == 0) {
+            int off = atomicAdd(P.so.pool_top, n);
+            if (off + n > P.so.pool_cap) { atomicExch(P.so.overflow, 1); off = -1; }
+            sh_off = off;
+            P.so.row_cnt[out_r] = n;
+            P.so.row_off[out_r] = off;
+        }
+        __syncthreads();
+        if (sh_off >= 0)
+            for (int t = tid; t < n; t += blockDim.x) {
+                P.so.pool_col[sh_off + t] = P.col[lo + t];
+                P.so.pool_npair[sh_off + t] = 0;
+            }
+        return;
+    }
+    for (int t = tid; t < kHashSlots; t += blockDim.x) { sm_acc[t] = 0ull; cnt[t] = 0u; keys[t] = -1; }
+    if (tid == 0) { sh_fill = 0; sh_bad = 0; }
+    __syncthreads();
+
+    const double tau = job.tau_sel ? P.tau1[s] : P.tau0[s];
+    const bool exact = !(tau > 0.0);
+    const float inv_unit = exact ? 0.f : __fdiv_ru(1.0f, __double2float_rd(tau * (1.0 - 1.0 / 1024.0))) * kFixOne;
+    const float csq = (float)fabs(P.c_sq[s]);
+    const double cl = P.c_lin[s];
+    const int nw = blockDim.x >> 5;
+    for (int t = 0; t < job.nterm; ++t) {
+        const int am = job.a[t], bm = job.b[t];
+        const int alo = P.rp[am * NB + i], ahi = P.rp[am * NB + i + 1];
+        for (int pa = alo + wid; pa < ahi; pa += nw) {
+            const int k = P.col[pa];
+            const float na = __fmul_ru(P.nrm[pa], csq);
+            const int blo = P.rp[bm * NB + k], bhi = P.rp[bm * NB + k + 1];
+            for (int pb = blo + lane; pb < bhi; pb += 32) {
+                const int h = hash_find(keys, P.col[pb], &sh_fill);
+                if (h < 0) { sh_bad = 1; continue; }
+                if (!exact) atomicAdd(&sm_acc[h], fix_units(__fmul_ru(na, P.nrm[pb]), inv_unit));
+                atomicAdd(&cnt[h], 1u);
+            }
+        }
+    }
+    if (cl != 0.0 && job.xmat >= 0) {
+        const float fcl = (float)fabs(cl);
+        const int xlo = P.rp[job.xmat * NB + i], xhi = P.rp[job.xmat * NB + i + 1];
+        for (int px = xlo + tid; px < xhi; px += blockDim.x) {
+            const int h = hash_find(keys, P.col[px], &sh_fill);
+            if (h < 0) { sh_bad = 1; continue; }
+            if (!exact) atomicAdd(&sm_acc[h], fix_units(__fmul_ru(P.nrm[px], fcl), inv_unit));
+            atomicOr(&cnt[h], 0x80000000u);
+        }
+    }
+    __syncthreads();
+    if (sh_bad) {   // row reaches more columns than the table holds
+        if (tid == 0) {
+            atomicExch(P.so.overflow, 2);
+            P.so.row_cnt[out_r] = 0;
+            P.so.row_off[out_r] = -1;
+        }
+        return;
+    }
+    // keep decision, packed as (column << 32 | pair count); dropped slots sort last
+    const unsigned long long thr = (unsigned long long)kFixOne;
+    int my = 0;
+    for (int t = tid; t < kHashSlots; t += blockDim.x) {
+        unsigned long long packed = ~0ull;
+        if (keys[t] >= 0) {
+            const bool keep = exact ? (cnt[t] != 0u) : (sm_acc[t] >= thr);
+            if (keep) {
+                const int j = keys[t];
+                const unsigned np = (j >= i) ? (cnt[t] & 0x7fffffffu) : 0u;
+                packed = ((unsigned long long)(unsigned)j << 32) | np;
+                ++my;
+            }
+        }
+        sm_acc[t] = packed;
+    }
+    int total;
+    block_excl_scan<int>(my, sh_scan, &total);
+    // bitonic sort of the packed keys (ascending)
+    for (int k = 2; k <= kHashSlots; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = tid; t < kHashSlots; t += blockDim.x) {
+                const int partner = t ^ jj;
+                if (partner > t) {
+                    const unsigned long long a = sm_acc[t], b = sm_acc[partner];
+                    const bool up = (t & k) == 0;
+                    if ((a > b) == up) { sm_acc[t] = b; sm_acc[partner] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        int off = atomicAdd(P.so.pool_top, total);
+        if (off + total > P.so.pool_cap) { atomicExch(P.so.overflow, 1); off = -1; }
+        sh_off = off;
+        P.so.row_cnt[out_r] = total;
+        P.so.row_off[out_r] = off;
+    }
+    __syncthreads();
+    if (sh_off < 0) return;
+    for (int t = tid; t < total; t += blockDim.x) {
+        const unsigned long long v = sm_acc[t];
+        P.so.pool_col[sh_off + t] = (int)(v >> 32);
+        P.so.pool_npair[sh_off + t] = (int)(v & 0xffffffffu);
+    }
+}
+
 // one warp per (job,row): copy the pool lists into the output pattern
 __global__ void k_gather(SymOut so, int nrows, const int *__restrict__ out_rp, int *out_col,
                          int *slot_row, int *slot_job, int *slot_npair, int NB) {
@@ -224,8 +379,8 @@ struct PairParams {
     const int64_t *pair_off;
     int64_t nslot;
     int *pair_a, *pair_b, *slot_x, *slot_t, *err;
-    const int *sys_of_row, *active;
-    unsigned fill;   // jobs whose pair lists are filled (others: only slot_x / slot_t)
+    const int *sys_of_row, *active, *sys_tier;
+    JobMask fill;    // jobs whose pair lists are filled, per tier (others: only slot_x / slot_t)
 };
 
 // one warp per output slot; only upper-triangle slots (j >= i) do work
@@ -249,7 +404,8 @@ __global__ void k_pairs(PairParams P) {
         P.slot_x[s] = x;
     }
     // a converged system's blocks are copied: the symbolic phase gave them no pairs
-    if (!((P.fill >> p) & 1u) || !P.active[P.sys_of_row[i]]) return;
+    const int sys = P.sys_of_row[i];
+    if (!P.active[sys] || !((P.fill.m[P.sys_tier[sys] & (kMaxTiers - 1)] >> p) & 1u)) return;
     int64_t w = P.pair_off[s];
     const int64_t wend = P.pair_off[s + 1];
     for (int t = 0; t < job.nterm; ++t) {
@@ -290,14 +446,20 @@ void launch_symbolic(const MatSet &in, const JobTable &jt, const SysDev &sd, int
     P.sys_of_row = sd.sys_of_row.p; P.row0 = sd.row0.p; P.nbs = sd.nbs.p;
     P.c_lin = sd.c_lin.p; P.c_sq = sd.c_sq.p; P.tau0 = sd.tau0.p; P.tau1 = sd.tau1.p;
     P.active = sd.active.p; P.so = so;
-    size_t smem = (size_t)max_ns * (sizeof(unsigned long long) + sizeof(unsigned int));
     static bool attr_set = false;
     if (!attr_set) {
         RDM_CUDA_TRY(cudaFuncSetAttribute(k_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kSymMaxNs * 12));
+        RDM_CUDA_TRY(cudaFuncSetAttribute(k_symbolic_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kHashSlots * 16));
         attr_set = true;
     }
-    k_symbolic<<<dim3(in.NB, jt.njob), kSymThreads, smem, st>>>(P);
+    if (max_ns <= kSymMaxNs) {
+        size_t smem = (size_t)max_ns * (sizeof(unsigned long long) + sizeof(unsigned int));
+        k_symbolic<<<dim3(in.NB, jt.njob), kSymThreads, smem, st>>>(P);
+    } else {
+        k_symbolic_hash<<<dim3(in.NB, jt.njob), kSymThreads, kHashSlots * 16, st>>>(P);
+    }
     RDM_LAUNCH_CHECK();
 }
 
@@ -314,10 +476,11 @@ void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, i
 void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
                   const int *out_col, const int *slot_row, const int *slot_job,
                   const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
-                  int *slot_x, int *slot_t, int *err, cudaStream_t st, unsigned fill) {
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st, JobMask fill) {
     if (nslot == 0) return;
     PairParams P;
     P.fill = fill;
+    P.sys_tier = sd.tier.p;
     P.rp = in.row_ptr.p; P.col = in.col.p; P.NB = NB; P.jt = jt;
     P.out_rp = out_row_ptr; P.out_col = out_col; P.slot_row = slot_row; P.slot_job = slot_job;
     P.pair_off = pair_off; P.nslot = nslot; P.pair_a = pair_a; P.pair_b = pair_b;

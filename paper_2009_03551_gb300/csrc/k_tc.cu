@@ -207,8 +207,8 @@ struct TileBuild {
     JobTable jt;
     const int *out_rp;   // mask row_ptr (flat, njob*NB+1)
     const int *mcol;     // mask columns
-    const int *sys_of_row, *active;
-    unsigned job_mask;   // jobs computed on the tensor cores
+    const int *sys_of_row, *active, *sys_tier;
+    JobMask job_mask;    // jobs computed on the tensor cores, per tier
     int *tile_cnt;       // [njob*NB4]
     const int *tile_off; // scanned
     int *tiles;          // [ntile * kTileInts]
@@ -241,7 +241,8 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
         // converged systems keep their blocks through the copy path of the
         // numeric phase, and jobs on the CUDA cores have their own launch:
         // neither produces tiles
-        if (!T.active[T.sys_of_row[i]] || !((T.job_mask >> p) & 1u)) cur[m] = end[m];
+        const int sys = T.sys_of_row[i];
+        if (!T.active[sys] || !((T.job_mask.m[T.sys_tier[sys] & (kMaxTiers - 1)] >> p) & 1u)) cur[m] = end[m];
     }
     // the distinct columns needed by the 4 rows, in increasing order, are packed
     // 4 at a time into tiles: every tile column is needed by at least one row
@@ -649,7 +650,7 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
 }
 
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, unsigned job_mask, cudaStream_t st) {
+                     const int *mcol, TcWork &w, JobMask job_mask, cudaStream_t st) {
     TcPlan plan{};
     const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL, njob = jt.njob;
     const int nrow4 = njob * NB4;
@@ -662,6 +663,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NB4 = NB4; T.jt = jt;
     T.out_rp = out_rp; T.mcol = mcol; T.sys_of_row = sd.sys_of_row.p; T.active = sd.active.p;
     T.job_mask = job_mask;
+    T.sys_tier = sd.tier.p;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
     k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();

@@ -137,6 +137,14 @@ struct JobTable {
 // Operand arithmetic of a numeric launch
 enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_TF32 = 4 };
 
+// Jobs selected per precision tier: bit p of m[t] selects job p for the rows
+// of systems currently in tier t (systems of a batch move through the tiers
+// independently)
+constexpr int kMaxTiers = 4;
+struct JobMask {
+    unsigned m[kMaxTiers];
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (implemented in the k_*.cu files)
 // ---------------------------------------------------------------------------
@@ -198,7 +206,7 @@ void launch_gather(const SymOut &so, int njob, int NB, const int *out_row_ptr, i
 void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_row_ptr,
                   const int *out_col, const int *slot_row, const int *slot_job,
                   const int64_t *pair_off, int64_t nslot, int NB, int *pair_a, int *pair_b,
-                  int *slot_x, int *slot_t, int *err, cudaStream_t st, unsigned fill = ~0u);
+                  int *slot_x, int *slot_t, int *err, cudaStream_t st, JobMask fill);
 
 // k_numeric.cu: C(upper slot) = c_lin X + c_sq sum(pairs); lower slot = transpose
 struct NumArgs {
@@ -225,11 +233,17 @@ void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
 void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st);
 
 // k_compact.cu
-// upper slots of the active systems' jobs in job_mask, plus (with_inactive)
-// all upper slots of converged systems
+// block triples of the upper slots of active systems per kernel class:
+// out[0] tensor cores (tc), out[1] FP64 (m64), out[2] FP32 (m32)
+void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot_npair, const int *slot_job,
+                        int64_t nslot, const int *sys_of_row, const int *active, const int *sys_tier,
+                        JobMask tc, JobMask m64, JobMask m32, unsigned long long *out, cudaStream_t st);
+// upper slots of the active systems' jobs selected by job_mask (per system
+// tier), plus (with_inactive) all upper slots of converged systems
 void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot,
                        int *work, int *nwork, cudaStream_t st, const int *sys_of_row,
-                       const int *active, const int *slot_job, unsigned job_mask, int with_inactive);
+                       const int *active, const int *slot_job, const int *sys_tier, JobMask job_mask,
+                       int with_inactive);
 void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total,
                           int *cnt, cudaStream_t st);
 void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,

@@ -33,9 +33,9 @@ struct TcPlan {
 void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st);
 
 // Tile lists of one multiplication step from the output mask, for the jobs
-// whose bit is set in job_mask.
+// selected by job_mask (per system tier).
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, unsigned job_mask, cudaStream_t st);
+                     const int *mcol, TcWork &w, JobMask job_mask, cudaStream_t st);
 
 // Numeric phase on the tensor cores; same output contract as
 // launch_numeric_simt for the slots of active systems.  Returns the flops

@@ -111,6 +111,19 @@ def test_cluster_fp64_free_run_matches_oracle_limit(rdm, cluster150, oracle150):
         assert rel_frobenius(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-8
 
 
+def test_hash_symbolic_phase_is_identical(rdm, cluster150):
+    """The hash-table symbolic phase (used above 8,192 block rows) gives the same
+    masks, pair counts and therefore bit-identical results as the dense one."""
+    s = cluster150
+    ref, _, _ = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode="fp64")
+    hsh, code, info = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode="fp64", symbolic_hash=1)
+    assert code == rdm.RDM_OK
+    assert np.array_equal(hsh.p0().col_idx, ref.p0().col_idx)
+    assert np.array_equal(hsh.p0().vals, ref.p0().vals)
+    for d in range(3):
+        assert np.array_equal(hsh.p1(0, d).vals, ref.p1(0, d).vals)
+
+
 def test_cluster_fp32_vs_oracle(rdm, cluster150, oracle150):
     s = cluster150
     sol, code, info = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode="fp32")
