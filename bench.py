@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--tau", type=float, default=1e-6, help="block truncation threshold")
+    ap.add_argument("--tau-refine", type=float, default=-1.0,
+                    help="threshold of the final (FP64/FP32) tier of the mixed modes (< 0: --tau); the "
+                         "FP64 comparison solve runs at this threshold throughout")
     return ap.parse_args()
 
 
@@ -210,6 +214,18 @@ def to_device(sys_, torch, dev):
     return s
 
 
+def job_seconds_per_solve(t_local, steps, world, dist, torch, device):
+    """Whole-job time per solve: the slowest rank's timed region (every rank
+    solves its own replica of the workload, `steps` times) divided by the
+    solves all ranks completed."""
+    t = t_local
+    if dist is not None:
+        x = torch.tensor([t_local], device=device, dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t / (steps * world)
+
+
 def alphas(sol, nsys):
     return np.stack([sol.alpha(k) for k in range(nsys)])
 
@@ -226,7 +242,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     torch.cuda.synchronize()
 
     sol = rdm.Solver(dev.index, stream.cuda_stream)
-    params = dict(tau=1e-6, tol=1e-9, mode=args.mode, max_iter=100)
+    params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100)
+    tau64 = args.tau_refine if args.tau_refine > 0 else args.tau
     sol.set_params(**params)
     sol.load(dsys)
     for _ in range(args.warmup):
@@ -253,26 +270,21 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    t_local = ms / 1e3
-    if dist is not None:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    s_per_solve = t_max / (args.steps * world)
+    s_per_solve = job_seconds_per_solve(ms / 1e3, args.steps, world, dist, torch, dev)
     alpha_m = alphas(sol, nsys)
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
     kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(6)]
     kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(3)]
     launches = int(sum(i.kernel_launches for i in infos))
+    sinfo = [sol.info(k) for k in range(nsys)]
+    sol.close()   # frees the device buffers before the comparison solves
 
     # FP64 comparison solve (context for the metric's "FP64 vs mixed")
     fp64 = None
     if not args.no_fp64 and args.mode != "fp64":
         s64 = rdm.Solver(dev.index, stream.cuda_stream)
-        s64.set_params(tau=1e-6, tol=1e-9, mode="fp64", max_iter=100)
+        s64.set_params(tau=tau64, tol=1e-9, mode="fp64", max_iter=100)
         s64.load(dsys)
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
@@ -351,11 +363,11 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "data": "synthetic",
             "config": {"workload": wname, "mode": mode, "systems": nsys,
                        "atoms": int(sum(s.n_atoms for s in systems)), "N": int(sum(s.n for s in systems)),
-                       "b": sys_.b, "tau": 1e-6, "tol": 1e-9, "directions": 3,
-                       "iterations": int(max(sol.info(k).iterations for k in range(nsys))),
-                       "nnzb_p0": int(sum(sol.info(k).nnzb_p0 for k in range(nsys))),
-                       "nnzb_p1": [int(sum(sol.info(k).nnzb_p1[d] for k in range(nsys))) for d in range(3)],
-                       "nnzb_per_block_row_p0": float(sum(sol.info(k).nnzb_p0 for k in range(nsys)) /
+                       "b": sys_.b, "tau": args.tau, "tau_refine": tau64, "tol": 1e-9, "directions": 3,
+                       "iterations": int(max(i.iterations for i in sinfo)),
+                       "nnzb_p0": int(sum(i.nnzb_p0 for i in sinfo)),
+                       "nnzb_p1": [int(sum(i.nnzb_p1[d] for i in sinfo)) for d in range(3)],
+                       "nnzb_per_block_row_p0": float(sum(i.nnzb_p0 for i in sinfo) /
                                                       sum(s.h0.nb for s in systems)),
                        "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
             "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
@@ -366,8 +378,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
                                     "reductions_setup_host": kms[5]},
             "tier_iterations": list(last.tier_iters)[:2],
+            "device_gb_peak": last.device_bytes_peak / 1e9, "product_groups": int(last.product_groups),
             "clocks": clocks}
-    sol.close()
     return line
 
 
@@ -375,16 +387,20 @@ def make_workload(args):
     """(name, list of systems) of the requested workload."""
     from synth import make_batch_config, make_config
     w = args.workload
+    def e(x):
+        m, ex = f"{x:.0e}".split("e")
+        return f"{m}e{int(ex)}"
+    ts = f"tau{e(args.tau)}" + (f"-refine{e(args.tau_refine)}" if args.tau_refine > 0 else "")
     if w == "cluster":
         cfg = 2 if args.atoms <= 2000 else 3
         s = make_config(cfg, n_atoms=args.atoms)
-        name = WORKLOAD if args.atoms == 2000 else f"cluster-{args.atoms}-atoms-N{s.n}-b32-tau1e-6-xyz"
+        name = f"cluster-{args.atoms}-atoms-N{s.n}-b32-{ts}-xyz"
         return name, [s]
     if w == "batch24":
-        return "batch-24-systems-300-8000-atoms-b32-tau1e-6-xyz", make_batch_config(24, b=32)
+        return f"batch-24-systems-300-8000-atoms-b32-{ts}-xyz", make_batch_config(24, b=32)
     if w.startswith("slab"):
         n = int(w[4:])
-        return f"slab-{n}-atoms-30bohr-b32-tau1e-6-xyz", [make_config(5, n_atoms=n)]
+        return f"slab-{n}-atoms-30bohr-b32-{ts}-xyz", [make_config(5, n_atoms=n)]
     raise SystemExit(f"unknown workload {w}")
 
 

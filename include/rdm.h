@@ -116,7 +116,12 @@ typedef struct {
                                (RDM_REFINE_*); X0^2 is always FP64 there */
     int32_t symbolic_hash;  /* 1: use the hash-table symbolic phase (otherwise chosen only for
                                systems above 8,192 block rows); results are identical */
-    int32_t reserved[3];
+    int32_t chunk_mb;       /* cap in MiB on the buffer of untruncated product blocks (8 b^2 + 5
+                               bytes per block); the jobs of a step (X0^2, each X1 product) are
+                               then multiplied in groups of consecutive jobs that fit it (at
+                               least one job per group).  0: automatic, from the free device
+                               memory.  Results do not depend on the grouping. */
+    int32_t reserved[2];
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -146,6 +151,10 @@ typedef struct {
     double  numeric_bytes;  /* algorithmic bytes of the product launches: operand blocks read
                                once (8 bytes/element FP64, 4 bytes hi+lo planes) + output
                                blocks written (8 bytes/element) */
+    int64_t device_bytes_peak; /* largest device memory held by the library's buffers during
+                                  the solve (all handles of the process) */
+    int32_t product_groups;    /* most job groups a step of the solve was split into (chunk_mb) */
+    int32_t pad0;
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */

@@ -81,6 +81,7 @@ struct rdm_handle {
     DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work, work2;
     DevBuf<int64_t> pair_off, scan_tmp64;
     DevBuf<int> scan_tmp32, pair_a, pair_b, cnt_rows;
+    DevBuf<int> uidx, scan_tmp_s, urp, dest, cpsrc;   // upper-slot ranks, compaction maps
     DevBuf<double> out_val, row_part, sys_q;
     DevBuf<float> out_nrm;
     DevBuf<uint8_t> keep;
@@ -370,7 +371,8 @@ struct StepStats {
     double issued_tc = 0;
     double bytes = 0;
     double ms[5] = {0, 0, 0, 0, 0};         // symbolic, tc, fp64, fp32, compaction
-    int numeric_launches = 0, simt_launches = 0;
+    int tc_launches = 0, simt_launches = 0;
+    int groups = 1;                         // job groups of the numeric phase
 };
 
 bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
@@ -443,6 +445,20 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     const bool m32_any = any32;
     h->ensure_events();
     RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
+    // operand copies are made afresh from the input set at every step: one
+    // set of buffers, moved to whichever set is the input, serves both
+    auto take = [](auto &mine, auto &other) {
+        if (other.cap > mine.cap) mine.swap(other);
+        other.release();
+    };
+    take(in.ophi, out.ophi);
+    take(in.oplo, out.oplo);
+    take(in.opf32, out.opf32);
+    // copies the step does not use are kept for the next solve, unless they
+    // are large (above 4 GiB the solve's time dwarfs a re-allocation)
+    const size_t big = size_t(4) << 30;
+    if (!tc && in.ophi.cap * sizeof(uint16_t) > big) { in.ophi.release(); in.oplo.release(); }
+    if (!m32_any && in.opf32.cap * sizeof(float) > big) in.opf32.release();
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
     if (m32_any) {
         in.opf32.ensure(std::max<int64_t>(in.total, 1) * bb);
@@ -520,88 +536,185 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
                  nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st,
                  simt);
     h->work.ensure(std::max<int64_t>(nslot, 1));
-    // CUDA-core work: the selected jobs and the copies of converged systems
-    launch_build_work(h->slot_row.p, mcol, nslot, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
-                      h->sd.active.p, h->slot_job.p, h->sd.tier.p, first_mask, 1);
-    if (second) {
-        h->work2.ensure(std::max<int64_t>(nslot, 1));
-        launch_build_work(h->slot_row.p, mcol, nslot, h->work2.p, h->counters.p + 4, st, h->sd.sys_of_row.p,
-                          h->sd.active.p, h->slot_job.p, h->sd.tier.p, m32, 0);
-    }
-    TcPlan plan{};
-    if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tcm, st);
-    int hc[3];
-    d2h(hc, h->counters.p + 2, 3, st);
+    if (second) h->work2.ensure(std::max<int64_t>(nslot, 1));
+    // rank of every upper slot among the upper slots (the products store
+    // only those; compaction writes the lower blocks as transposes)
+    h->uidx.ensure(nslot + 1);
+    h->scan_tmp_s.ensure(scan_tmp_elems((int)nslot + 1));
+    launch_upper_flags(h->slot_row.p, mcol, nslot, h->uidx.p, st);
+    scan_exclusive_i32(h->uidx.p, h->uidx.p, (int)nslot, h->scan_tmp_s.p, st);
+    int hq[2] = {0, 0};
+    d2h(&hq[0], h->counters.p + 2, 1, st);
+    d2h(&hq[1], h->uidx.p + nslot, 1, st);
     sync(h);
-    if (hc[0]) throw Error{RDM_ECUDA, "internal error: pair lists inconsistent with the mask (code " + std::to_string(hc[0]) + ")"};
-    const int nwork = hc[1];
-    const int nwork2 = second ? hc[2] : 0;
+    if (hq[0]) throw Error{RDM_ECUDA, "internal error: pair lists inconsistent with the mask (code " + std::to_string(hq[0]) + ")"};
+    const int64_t nupper = hq[1];
 
-    // numeric + fused truncation
-    h->out_val.ensure(std::max<int64_t>(nslot, 1) * bb);
+    // Numeric phase, fused truncation and compaction, one group of
+    // consecutive super-rows (4 block rows of a job) at a time: the buffer of
+    // untruncated blocks holds one group's upper slots.  A lower block's
+    // upper partner lies in an earlier row, so it is in the same group or
+    // already compacted; the result does not depend on the grouping.
+    const size_t slot_bytes = bb * sizeof(double);
+    int64_t budget = nupper;
+    if (h->prm.chunk_mb > 0) {
+        budget = std::max<int64_t>(1, (int64_t)(((size_t)h->prm.chunk_mb << 20) / slot_bytes));
+    } else if ((size_t)nupper > h->out_val.cap / bb) {
+        size_t fr = 0, totm = 0;
+        RDM_CUDA_TRY(cudaMemGetInfo(&fr, &totm));
+        // at most 1/16 of the device (at least 4 GiB) and what is free: the
+        // current buffer is released before the new one is made; room is kept
+        // for the output set (about the size of the input set) and a margin
+        // for the plans, pair and work lists
+        const size_t held = h->out_val.cap * sizeof(double);
+        const size_t out_have = out.val.cap * sizeof(double);
+        const size_t out_need = (size_t)in.total * bb * sizeof(double) * 9 / 8;
+        const size_t reserve = (out_need > out_have ? out_need - out_have : 0) + (size_t(4) << 30);
+        const size_t avail = fr + held > reserve ? fr + held - reserve : 0;
+        const size_t cap = std::min(avail, std::max(totm / 16, size_t(4) << 30));
+        budget = std::max<int64_t>(1, (int64_t)(cap / slot_bytes));
+    }
+    const int NB4 = (NB + 3) / 4, nunit = njob * NB4;
+    auto unit_row = [&](int u) {   // first flat row of super-row unit u (u = nunit: nrows)
+        if (u >= nunit) return nrows;
+        return (u / NB4) * NB + 4 * (u % NB4);
+    };
+    std::vector<int> gunit{0};          // first unit of every group
+    std::vector<int> hrp, hurp;         // host out_rp and upper ranks at row starts (several groups)
+    if (nupper <= budget) {
+        gunit.push_back(nunit);
+    } else {
+        h->urp.ensure(nrows + 1);
+        launch_gather_i32(h->out_rp.p, h->uidx.p, nrows, h->urp.p, st);
+        hrp.resize(nrows + 1);
+        hurp.resize(nrows + 1);
+        d2h(hrp.data(), h->out_rp.p, nrows + 1, st);
+        d2h(hurp.data(), h->urp.p, nrows + 1, st);
+        sync(h);
+        int u = 0;
+        while (u < nunit) {
+            int v = u + 1;
+            while (v < nunit && hurp[unit_row(v + 1)] - hurp[unit_row(u)] <= budget) ++v;
+            gunit.push_back(v);
+            u = v;
+        }
+    }
+    const int ngroup = (int)gunit.size() - 1;
+    ss.groups = ngroup;
+    auto gslot = [&](int u) -> int64_t { return ngroup == 1 ? (u == 0 ? 0 : nslot) : hrp[unit_row(u)]; };
+    auto gupper = [&](int u) -> int64_t { return ngroup == 1 ? (u == 0 ? 0 : nupper) : hurp[unit_row(u)]; };
+    int64_t gmax = 1;
+    for (int g = 0; g < ngroup; ++g) gmax = std::max<int64_t>(gmax, gupper(gunit[g + 1]) - gupper(gunit[g]));
+    h->out_val.ensure((size_t)gmax * bb);
     h->out_nrm.ensure(std::max<int64_t>(nslot, 1));
     h->keep.ensure(std::max<int64_t>(nslot, 1));
-    NumArgs a{};
-    a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
-    a.in_f32 = m32_any ? in.opf32.p : nullptr;
-    a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
-    a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
-    a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
-    a.c_lin = h->sd.c_lin.p; a.c_sq = h->sd.c_sq.p; a.tau0 = h->sd.tau0.p; a.tau1 = h->sd.tau1.p;
-    a.active = h->sd.active.p;
-    for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
-    a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p; a.b = b;
-    RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
-    const long long l0 = g_kernel_launches;
-    if (nwork) launch_numeric_simt(a, simt_ar, st);
-    RDM_CUDA_TRY(cudaEventRecord(h->ev[5], st));
-    if (nwork2) {
-        NumArgs a2 = a;
-        a2.work = h->work2.p;
-        a2.nwork = nwork2;
-        launch_numeric_simt(a2, AR_FP32, st);
-    }
-    RDM_CUDA_TRY(cudaEventRecord(h->ev[4], st));
-    ss.simt_launches = (int)(g_kernel_launches - l0);
-    if (tc) ss.issued_tc = launch_numeric_tc(a, in, jt, tc_ar, h->tcw, NB, plan, st);
-    ss.numeric_launches = (int)(g_kernel_launches - l0);
-    ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (double)nslot * 8.0) * (double)bb;
-    RDM_CUDA_TRY(cudaEventRecord(h->ev[2], st));
-
-    // compaction
+    h->dest.ensure(std::max<int64_t>(nslot, 1));
     h->cnt_rows.ensure(nrows + 1);
-    launch_compact_count(h->out_rp.p, h->keep.p, nrows, h->cnt_rows.p, st);
     out.row_ptr.ensure(nrows + 1);
-    scan_exclusive_i32(h->cnt_rows.p, out.row_ptr.p, nrows, h->scan_tmp32.p, st);
     int kept = 0;
-    d2h(&kept, out.row_ptr.p + nrows, 1, st);
-    int tc_err = 0;
-    if (tc) d2h(&tc_err, h->tcw.counters.p, 1, st);
-    sync(h);
-    if (tc_err)
-        throw Error{tc_err & 1 ? RDM_ETIMEOUT : RDM_ECUDA,
-                    "tensor-core product kernel failed (code " + std::to_string(tc_err) + ")"};
-    out.col.ensure(std::max(kept, 1));
-    out.val.ensure((size_t)std::max(kept, 1) * bb);
-    out.nrm.ensure(std::max(kept, 1));
-    launch_compact_copy(h->out_rp.p, mcol, h->out_val.p, h->out_nrm.p, h->keep.p,
-                        out.row_ptr.p, nrows, b, out.col.p, out.val.p, out.nrm.p, st);
+    float t_simt1 = 0, t_simt2 = 0, t_tc = 0, t_cmp = 0;
+    for (int g = 0; g < ngroup; ++g) {
+        const int ua = gunit[g], ub = gunit[g + 1];
+        const int64_t s0 = gslot(ua), s1 = gslot(ub), u0 = gupper(ua);
+        const int r0 = unit_row(ua), nr = unit_row(ub) - r0;
+        RDM_CUDA_TRY(cudaMemsetAsync(h->counters.p + 3, 0, 2 * sizeof(int), st));
+        // CUDA-core work: the selected jobs and the copies of converged systems
+        launch_build_work(h->slot_row.p, mcol, s0, s1, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
+                          h->sd.active.p, h->slot_job.p, h->sd.tier.p, first_mask, 1);
+        if (second)
+            launch_build_work(h->slot_row.p, mcol, s0, s1, h->work2.p, h->counters.p + 4, st,
+                              h->sd.sys_of_row.p, h->sd.active.p, h->slot_job.p, h->sd.tier.p, m32, 0);
+        TcPlan plan{};
+        if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tcm, ua, ub, st);
+        const bool tc_g = tc && plan.ntile > 0;
+        int hc[2];
+        d2h(hc, h->counters.p + 3, 2, st);
+        sync(h);
+        const int nwork = hc[0];
+        const int nwork2 = second ? hc[1] : 0;
+
+        NumArgs a{};
+        a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
+        a.in_f32 = m32_any ? in.opf32.p : nullptr;
+        a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
+        a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
+        a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
+        a.c_lin = h->sd.c_lin.p; a.c_sq = h->sd.c_sq.p; a.tau0 = h->sd.tau0.p; a.tau1 = h->sd.tau1.p;
+        a.active = h->sd.active.p;
+        for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
+        a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p;
+        a.uidx = h->uidx.p; a.u0 = u0; a.b = b;
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
+        const long long lg = g_kernel_launches;
+        if (nwork) launch_numeric_simt(a, simt_ar, st);
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[5], st));
+        if (nwork2) {
+            NumArgs a2 = a;
+            a2.work = h->work2.p;
+            a2.nwork = nwork2;
+            launch_numeric_simt(a2, AR_FP32, st);
+        }
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[4], st));
+        ss.simt_launches += (int)(g_kernel_launches - lg);
+        if (tc_g) {
+            const long long lt = g_kernel_launches;
+            ss.issued_tc += launch_numeric_tc(a, in, jt, tc_ar, h->tcw, NB, plan, st);
+            ss.tc_launches += (int)(g_kernel_launches - lt);
+        }
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[2], st));
+
+        // compaction of the group's rows, appended after the previous groups
+        CompactArgs ca{};
+        ca.out_rp = h->out_rp.p; ca.out_col = mcol; ca.slot_row = h->slot_row.p; ca.slot_t = h->slot_t.p;
+        ca.uidx = h->uidx.p; ca.out_val = h->out_val.p; ca.out_nrm = h->out_nrm.p; ca.keep = h->keep.p;
+        ca.u0 = u0; ca.dest = h->dest.p; ca.new_rp = out.row_ptr.p; ca.r0 = r0; ca.nrows = nr; ca.b = b;
+        launch_compact_count(ca, h->cnt_rows.p, st);
+        scan_exclusive_i32(h->cnt_rows.p, out.row_ptr.p + r0, nr, h->scan_tmp32.p, st, kept);
+        int kept_end = 0;
+        d2h(&kept_end, out.row_ptr.p + r0 + nr, 1, st);
+        int tc_err = 0;
+        if (tc_g) d2h(&tc_err, h->tcw.counters.p, 1, st);
+        sync(h);
+        if (tc_err)
+            throw Error{tc_err & 1 ? RDM_ETIMEOUT : RDM_ECUDA,
+                        "tensor-core product kernel failed (code " + std::to_string(tc_err) + ")"};
+        if (g == 0) {
+            // the output set's old contents are dead; reserve about the input's size
+            const int64_t want = ngroup > 1 ? std::max<int64_t>(kept_end, in.total) : kept_end;
+            out.col.ensure(std::max<int64_t>(want, 1));
+            out.val.ensure((size_t)std::max<int64_t>(want, 1) * bb);
+            out.nrm.ensure(std::max<int64_t>(want, 1));
+        } else {
+            out.col.grow_keep(std::max(kept_end, 1), kept, st);
+            out.val.grow_keep((size_t)std::max(kept_end, 1) * bb, (size_t)kept * bb, st);
+            out.nrm.grow_keep(std::max(kept_end, 1), kept, st);
+        }
+        ca.new_col = out.col.p; ca.new_val = out.val.p; ca.new_nrm = out.nrm.p;
+        ca.src = h->cpsrc.ensure(std::max(kept_end - kept, 1));
+        ca.d0 = kept;
+        launch_compact_copy(ca, kept_end, st);
+        kept = kept_end;
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[3], st));
+        RDM_CUDA_TRY(cudaEventSynchronize(h->ev[3]));
+        float m15 = 0, m54 = 0, m42 = 0, m23 = 0;
+        cudaEventElapsedTime(&m15, h->ev[1], h->ev[5]);   // first CUDA-core launch
+        cudaEventElapsedTime(&m54, h->ev[5], h->ev[4]);   // second (FP32) CUDA-core launch
+        cudaEventElapsedTime(&m42, h->ev[4], h->ev[2]);   // tensor-core launch
+        cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);   // compaction
+        t_simt1 += m15; t_simt2 += m54; t_tc += m42; t_cmp += m23;
+    }
+    ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (double)nupper * 8.0) * (double)bb;
     out.total = kept;
-    RDM_CUDA_TRY(cudaEventRecord(h->ev[3], st));
     std::vector<int> rp(nrows + 1);
     d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
     sync(h);
-    float m01 = 0, m15 = 0, m54 = 0, m42 = 0, m23 = 0;
-    cudaEventElapsedTime(&m01, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&m15, h->ev[1], h->ev[5]);   // first CUDA-core launch
-    cudaEventElapsedTime(&m54, h->ev[5], h->ev[4]);   // second (FP32) CUDA-core launch
-    cudaEventElapsedTime(&m42, h->ev[4], h->ev[2]);
-    cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);
-    ss.ms[0] = m01;
-    ss.ms[1] = m42;                                   // tensor-core products
-    ss.ms[2] = simt_ar == AR_FP64 ? m15 : 0.f;        // FP64 products
-    ss.ms[3] = (simt_ar == AR_FP64 ? 0.f : m15) + m54;  // FP32 products (and copies)
-    ss.ms[4] = m23;
+    float mall = 0;
+    cudaEventElapsedTime(&mall, h->ev[0], h->ev[3]);
+    ss.ms[1] = t_tc;                                         // tensor-core products
+    ss.ms[2] = simt_ar == AR_FP64 ? t_simt1 : 0.f;           // FP64 products
+    ss.ms[3] = (simt_ar == AR_FP64 ? 0.f : t_simt1) + t_simt2;  // FP32 products (and copies)
+    ss.ms[4] = t_cmp;
+    ss.ms[0] = std::max(0.f, mall - (t_simt1 + t_simt2 + t_tc + t_cmp));  // mask, lists, plans
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -678,7 +791,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     std::vector<int> act(S);
     double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0;
     double kms[5] = {0, 0, 0, 0, 0};
-    int tc_launches = 0, simt_launches = 0;
+    int tc_launches = 0, simt_launches = 0, max_groups = 1;
+    g_dev_bytes_peak = g_dev_bytes.load();
     cudaEvent_t ev0, ev1;
     RDM_CUDA_TRY(cudaEventCreate(&ev0));
     RDM_CUDA_TRY(cudaEventCreate(&ev1));
@@ -816,8 +930,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         flops_32 += (double)sst.pairs_32 * fpb;
         issued += sst.issued_tc + (double)(sst.pairs_64 + sst.pairs_32) * fpb;
         nbytes += sst.bytes;
-        tc_launches += sst.numeric_launches - sst.simt_launches;
+        tc_launches += sst.tc_launches;
         simt_launches += sst.simt_launches;
+        max_groups = std::max(max_groups, sst.groups);
         for (int k = 0; k < 5; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
@@ -898,6 +1013,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.tc_launches = tc_launches;
         I.simt_launches = simt_launches;
         I.numeric_bytes = nbytes;
+        I.device_bytes_peak = (int64_t)g_dev_bytes_peak.load();
+        I.product_groups = max_groups;
     }
     // band energy of the result: recompute the stats of the final X
     q = stats(h, Xf);

@@ -1,8 +1,12 @@
 // Stream compaction after truncation: per-row counts of the kept blocks, a
 // scan (k_scan.cu) into the new row pointers, and an order-preserving copy of
-// the kept blocks (columns, values, norm bounds).  Also builds the work list
-// of upper-triangle output blocks for the numeric phase.
+// the kept blocks (columns, values, norm bounds); the products compute only
+// the upper triangle and the copy writes each lower block as the transpose
+// of its upper partner.  Also builds the work list of upper-triangle output
+// blocks for the numeric phase.
 #include "rdm_internal.cuh"
+
+#include <algorithm>
 
 namespace rdm {
 namespace {
@@ -13,12 +17,12 @@ namespace {
 // keeps the upper slots of the active systems' jobs in job_mask and, with
 // with_inactive, every upper slot of a converged system (those are copied)
 __global__ void k_build_work(const int *__restrict__ slot_row, const int *__restrict__ out_col,
-                             int64_t nslot, int *work, int *nwork, const int *__restrict__ sys_of_row,
+                             int64_t s0, int64_t s1, int *work, int *nwork, const int *__restrict__ sys_of_row,
                              const int *__restrict__ active, const int *__restrict__ slot_job,
                              const int *__restrict__ sys_tier, JobMask job_mask, int with_inactive) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int lane = threadIdx.x & 31;
-    bool up = s < nslot && out_col[s] >= slot_row[s];
+    bool up = s < s1 && out_col[s] >= slot_row[s];
     if (up) {
         const int sys = sys_of_row[slot_row[s]];
         const bool act = active[sys] != 0;
@@ -57,59 +61,104 @@ __global__ void k_class_pairs(const int *__restrict__ slot_row, const int *__res
     }
 }
 
-__global__ void k_compact_count(const int *__restrict__ rp, const uint8_t *__restrict__ keep,
-                                int nrows, int *cnt) {
-    int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (r >= nrows) return;
-    int c = 0;
-    for (int p = rp[r] + lane; p < rp[r + 1]; p += 32) c += keep[p] ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) cnt[r] = c;
+__global__ void k_upper_flags(const int *__restrict__ slot_row, const int *__restrict__ out_col,
+                              int64_t nslot, int *__restrict__ uidx) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nslot) uidx[s] = out_col[s] >= slot_row[s] ? 1 : 0;
 }
 
-__global__ void k_compact_copy(const int *__restrict__ rp, const int *__restrict__ col,
-                               const double *__restrict__ val, const float *__restrict__ nrm,
-                               const uint8_t *__restrict__ keep, const int *__restrict__ nrp,
-                               int nrows, int b, int *ncol, double *nval, float *nnrm) {
-    int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (r >= nrows) return;
-    const int bb = b * b;
-    int dst = nrp[r];
-    for (int base = rp[r]; base < rp[r + 1]; base += 32) {
-        int p = base + lane;
-        bool k = p < rp[r + 1] && keep[p];
-        unsigned m = __ballot_sync(0xffffffffu, k);
-        if (k) {
-            int d = dst + __popc(m & ((1u << lane) - 1u));
-            ncol[d] = col[p];
-            nnrm[d] = nrm[p];
+__global__ void k_gather_i32(const int *__restrict__ idx, const int *__restrict__ src, int n,
+                             int *__restrict__ dst) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r <= n) dst[r] = src[idx[r]];
+}
+
+// one warp per row of the group: kept blocks (an upper slot on its own flag,
+// a lower one on its upper partner's)
+__global__ void k_compact_count(CompactArgs c, int *cnt) {
+    const int rr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (rr >= c.nrows) return;
+    const int r = c.r0 + rr;
+    int n = 0;
+    for (int p = c.out_rp[r] + lane; p < c.out_rp[r + 1]; p += 32) {
+        const bool up = c.out_col[p] >= c.slot_row[p];
+        n += c.keep[up ? p : c.slot_t[p]] ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) cnt[rr] = n;
+}
+
+// one warp per row: columns, norm bounds and destinations of the kept blocks
+// (order-preserving); src[d - d0] receives the slot of output block d
+__global__ void k_compact_index(CompactArgs c) {
+    const int rr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (rr >= c.nrows) return;
+    const int r = c.r0 + rr;
+    const int rend = c.out_rp[r + 1];
+    int dst = c.new_rp[r];
+    for (int base = c.out_rp[r]; base < rend; base += 32) {
+        const int p = base + lane;
+        bool k = false, up = false;
+        int src = p;
+        if (p < rend) {
+            up = c.out_col[p] >= c.slot_row[p];
+            src = up ? p : c.slot_t[p];
+            k = c.keep[src] != 0;
         }
-        // copy the kept blocks' values, one block at a time, lanes over elements
-        unsigned mm = m;
-        int d = dst;
-        while (mm) {
-            int l = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const double *src = val + (size_t)(base + l) * bb;
-            double *out = nval + (size_t)d * bb;
-            for (int e = lane; e < bb; e += 32) out[e] = src[e];
-            ++d;
+        const unsigned m = __ballot_sync(0xffffffffu, k);
+        if (k) {
+            const int d = dst + __popc(m & ((1u << lane) - 1u));
+            c.new_col[d] = c.out_col[p];
+            c.new_nrm[d] = c.out_nrm[src];
+            c.src[d - c.d0] = p;
+            if (up) c.dest[p] = d;
         }
         dst += __popc(m);
     }
 }
 
+// one CTA per kept block (grid-stride): upper blocks are copied, lower ones
+// transposed through shared memory (b x (b+1) doubles) from their upper
+// partner, which is in this group's buffer or already compacted
+__global__ void __launch_bounds__(128) k_compact_vals(CompactArgs c, int d1) {
+    extern __shared__ double tile[];
+    const int b = c.b, bb = b * b, ld = b + 1;
+    for (int d = c.d0 + blockIdx.x; d < d1; d += gridDim.x) {
+        const int p = c.src[d - c.d0];
+        double *out = c.new_val + (size_t)d * bb;
+        if (c.out_col[p] >= c.slot_row[p]) {
+            const double *s = c.out_val + (size_t)(c.uidx[p] - c.u0) * bb;
+            if ((bb & 1) == 0) {
+                const double2 *s2 = reinterpret_cast<const double2 *>(s);
+                double2 *o2 = reinterpret_cast<double2 *>(out);
+                for (int e = threadIdx.x; e < bb / 2; e += blockDim.x) o2[e] = s2[e];
+            } else {
+                for (int e = threadIdx.x; e < bb; e += blockDim.x) out[e] = s[e];
+            }
+        } else {
+            const int t = c.slot_t[p];
+            const int ut = c.uidx[t];
+            const double *s = ut >= c.u0 ? c.out_val + (size_t)(ut - c.u0) * bb
+                                         : c.new_val + (size_t)c.dest[t] * bb;
+            for (int e = threadIdx.x; e < bb; e += blockDim.x) tile[(e / b) * ld + (e % b)] = s[e];
+            __syncthreads();
+            for (int e = threadIdx.x; e < bb; e += blockDim.x) out[e] = tile[(e % b) * ld + (e / b)];
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
-void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot, int *work,
+void launch_build_work(const int *slot_row, const int *out_col, int64_t s0, int64_t s1, int *work,
                        int *nwork, cudaStream_t st, const int *sys_of_row, const int *active,
                        const int *slot_job, const int *sys_tier, JobMask job_mask, int with_inactive) {
-    if (nslot == 0) return;
-    int64_t grid = (nslot + 255) / 256;
-    k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, nslot, work, nwork, sys_of_row,
+    if (s1 <= s0) return;
+    int64_t grid = (s1 - s0 + 255) / 256;
+    k_build_work<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, s0, s1, work, nwork, sys_of_row,
                                                  active, slot_job, sys_tier, job_mask, with_inactive);
     RDM_LAUNCH_CHECK();
 }
@@ -124,24 +173,40 @@ void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot
     RDM_LAUNCH_CHECK();
 }
 
-void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total, int *cnt,
-                          cudaStream_t st) {
-    if (nrows_total == 0) return;
-    int wpb = 8;
-    k_compact_count<<<(nrows_total + wpb - 1) / wpb, wpb * 32, 0, st>>>(out_row_ptr, keep,
-                                                                        nrows_total, cnt);
+void launch_upper_flags(const int *slot_row, const int *out_col, int64_t nslot, int *uidx,
+                        cudaStream_t st) {
+    if (nslot == 0) return;
+    k_upper_flags<<<(unsigned)((nslot + 255) / 256), 256, 0, st>>>(slot_row, out_col, nslot, uidx);
     RDM_LAUNCH_CHECK();
 }
 
-void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,
-                         const float *out_nrm, const uint8_t *keep, const int *new_row_ptr,
-                         int nrows_total, int b, int *new_col, double *new_val, float *new_nrm,
-                         cudaStream_t st) {
-    if (nrows_total == 0) return;
-    int wpb = 8;
-    k_compact_copy<<<(nrows_total + wpb - 1) / wpb, wpb * 32, 0, st>>>(
-        out_row_ptr, out_col, out_val, out_nrm, keep, new_row_ptr, nrows_total, b, new_col,
-        new_val, new_nrm);
+void launch_gather_i32(const int *idx, const int *src, int n, int *dst, cudaStream_t st) {
+    k_gather_i32<<<(n + 256) / 256, 256, 0, st>>>(idx, src, n, dst);
+    RDM_LAUNCH_CHECK();
+}
+
+void launch_compact_count(const CompactArgs &c, int *cnt, cudaStream_t st) {
+    if (c.nrows == 0) return;
+    const int wpb = 8;
+    k_compact_count<<<(c.nrows + wpb - 1) / wpb, wpb * 32, 0, st>>>(c, cnt);
+    RDM_LAUNCH_CHECK();
+}
+
+void launch_compact_copy(const CompactArgs &c, int d1, cudaStream_t st) {
+    if (c.nrows == 0) return;
+    const int wpb = 8;
+    k_compact_index<<<(c.nrows + wpb - 1) / wpb, wpb * 32, 0, st>>>(c);
+    RDM_LAUNCH_CHECK();
+    if (d1 <= c.d0) return;
+    const size_t smem = (size_t)c.b * (c.b + 1) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        RDM_CUDA_TRY(cudaFuncSetAttribute(k_compact_vals, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          64 * 65 * (int)sizeof(double)));
+        attr = true;
+    }
+    const int grid = (int)std::min<int64_t>((int64_t)d1 - c.d0, 152 * 16);
+    k_compact_vals<<<grid, 128, smem, st>>>(c, d1);
     RDM_LAUNCH_CHECK();
 }
 

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
             }
         }
 
-        // epilogue: linear term, symmetrisation, norm, truncation, both triangles
+        // epilogue: linear term, symmetrisation, norm, truncation (the lower
+        // triangle is written by the compaction, as the transpose)
         double out[PER];
         const double *gx = sx >= 0 ? a.in_val + (size_t)sx * BB : nullptr;
         __syncthreads();
@@ -116,21 +117,15 @@ __global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
         }
         const double nrm = sqrt(block_sum(ss, red));
         const bool keep = (nrm >= tau) && (nrm > 0.0);
-        double *o = a.out_val + (size_t)s * BB;
+        double *o = a.out_val + (size_t)(a.uidx[s] - a.u0) * BB;
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
             const int e = tid + r * NT;
             if (e < BB) o[e] = out[r];
         }
-        if (!diag) {
-            double *ot = a.out_val + (size_t)st * BB;
-            for (int e = tid; e < BB; e += NT) ot[e] = Cs[(e % B) * LD + (e / B)];
-        }
         if (tid == 0) {
-            const float fn = __double2float_ru(nrm);
-            a.out_nrm[s] = fn;
+            a.out_nrm[s] = __double2float_ru(nrm);
             a.keep[s] = keep;
-            if (!diag) { a.out_nrm[st] = fn; a.keep[st] = keep; }
         }
     }
 }
@@ -266,16 +261,11 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
         __syncthreads();
         const float nrm = sqrtf(red[0] + red[1]) * (1.0f + 1e-6f);
         const bool keep = ((double)nrm >= tau) && (nrm > 0.f);
-        double *o = a.out_val + (size_t)s * 1024;
+        double *o = a.out_val + (size_t)(a.uidx[s] - a.u0) * 1024;
         for (int e = tid; e < 1024; e += 64) o[e] = (double)sC[(e >> 5) * 33 + (e & 31)];
-        if (!diag) {
-            double *ot = a.out_val + (size_t)st * 1024;
-            for (int e = tid; e < 1024; e += 64) ot[e] = (double)sC[(e & 31) * 33 + (e >> 5)];
-        }
         if (tid == 0) {
             a.out_nrm[s] = nrm;
             a.keep[s] = keep;
-            if (!diag) { a.out_nrm[st] = nrm; a.keep[st] = keep; }
         }
     }
 }

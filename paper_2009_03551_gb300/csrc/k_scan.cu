@@ -1,6 +1,7 @@
 // Exclusive prefix sums used to turn per-row / per-slot counts into offsets.
 // Three launches: per-tile sums, a single-CTA scan of the tile sums, and the
-// per-tile scan with the tile offset added.  out[n] receives the total.
+// per-tile scan with the tile offset added.  out[n] receives the total; an
+// initial value `init` is added to every output.
 // The scan is deterministic (integer addition).
 #include "rdm_internal.cuh"
 
@@ -53,9 +54,9 @@ __global__ void tile_sums(const In *__restrict__ in, int n, Out *__restrict__ ti
 }
 
 template <class Out>
-__global__ void scan_tiles(Out *tile_sum, int ntiles, Out *total_out) {
+__global__ void scan_tiles(Out *tile_sum, int ntiles, Out *total_out, Out init) {
     __shared__ Out sh[32];
-    Out carry = 0;
+    Out carry = init;
     for (int base = 0; base < ntiles; base += kThreads) {
         int i = base + threadIdx.x;
         Out v = i < ntiles ? tile_sum[i] : Out(0);
@@ -88,12 +89,12 @@ __global__ void scan_apply(const In *in, int n, const Out *__restrict__ tile_sum
 }
 
 template <class In, class Out>
-void scan_impl(const In *in, Out *out, int n, Out *tmp, cudaStream_t st) {
+void scan_impl(const In *in, Out *out, int n, Out *tmp, cudaStream_t st, Out init) {
     int ntiles = (n + kTile - 1) / kTile;
     if (ntiles < 1) ntiles = 1;
     tile_sums<In, Out><<<ntiles, kThreads, 0, st>>>(in, n, tmp);
     RDM_LAUNCH_CHECK();
-    scan_tiles<Out><<<1, kThreads, 0, st>>>(tmp, ntiles, out + n);
+    scan_tiles<Out><<<1, kThreads, 0, st>>>(tmp, ntiles, out + n, init);
     RDM_LAUNCH_CHECK();
     if (n > 0) {
         scan_apply<In, Out><<<ntiles, kThreads, 0, st>>>(in, n, tmp, out);
@@ -105,11 +106,11 @@ void scan_impl(const In *in, Out *out, int n, Out *tmp, cudaStream_t st) {
 
 size_t scan_tmp_elems(int n) { return (size_t)((n + kTile - 1) / kTile + 1); }
 
-void scan_exclusive_i32(const int *in, int *out, int n, int *tmp, cudaStream_t st) {
-    scan_impl<int, int>(in, out, n, tmp, st);
+void scan_exclusive_i32(const int *in, int *out, int n, int *tmp, cudaStream_t st, int init) {
+    scan_impl<int, int>(in, out, n, tmp, st, init);
 }
 void scan_exclusive_i64(const int *in, int64_t *out, int n, int64_t *tmp, cudaStream_t st) {
-    scan_impl<int, int64_t>(in, out, n, tmp, st);
+    scan_impl<int, int64_t>(in, out, n, tmp, st, int64_t(0));
 }
 
 }  // namespace rdm

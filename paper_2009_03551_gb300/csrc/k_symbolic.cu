@@ -383,7 +383,9 @@ struct PairParams {
     JobMask fill;    // jobs whose pair lists are filled, per tier (others: only slot_x / slot_t)
 };
 
-// one warp per output slot; only upper-triangle slots (j >= i) do work
+// one warp per output slot; only upper-triangle slots (j >= i) do work.
+// slot_t pairs every off-diagonal upper slot with its lower mirror (both
+// ways); a diagonal slot maps to itself
 __global__ void k_pairs(PairParams P) {
     int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
@@ -399,6 +401,7 @@ __global__ void k_pairs(PairParams P) {
             if (t < 0) atomicOr(P.err, 1);
         }
         P.slot_t[s] = t;
+        if (t >= 0 && t != s) P.slot_t[t] = (int)s;   // the lower partner points back
         int x = -1;
         if (job.xmat >= 0) x = find_col(P.col, P.rp[job.xmat * NB + i], P.rp[job.xmat * NB + i + 1], j);
         P.slot_x[s] = x;

@@ -209,7 +209,8 @@ struct TileBuild {
     const int *mcol;     // mask columns
     const int *sys_of_row, *active, *sys_tier;
     JobMask job_mask;    // jobs computed on the tensor cores, per tier
-    int *tile_cnt;       // [njob*NB4]
+    int u0, u1;          // super-row units (job * NB4 + I) of this plan
+    int *tile_cnt;       // [u1 - u0]
     const int *tile_off; // scanned
     int *tiles;          // [ntile * kTileInts]
     int *step_cnt;       // [ntile]
@@ -221,10 +222,9 @@ struct TileBuild {
 // one thread per (job, super-row): the union of super-columns J of the upper
 // mask blocks in block rows 4I..4I+3 (count or fill)
 __global__ void k_tile_rows(TileBuild T, int fill) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int njob = T.jt.njob;
-    if (t >= njob * T.NB4) return;
-    int p = t / T.NB4, I = t % T.NB4;
+    const int t = T.u0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T.u1) return;
+    const int p = t / T.NB4, I = t % T.NB4;
     int cur[TBL], end[TBL];
     for (int m = 0; m < TBL; ++m) {
         int i = 4 * I + m;
@@ -247,7 +247,7 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
     // the distinct columns needed by the 4 rows, in increasing order, are packed
     // 4 at a time into tiles: every tile column is needed by at least one row
     int ncol = 0, n = 0;
-    const int base = fill ? T.tile_off[t] : 0;
+    const int base = fill ? T.tile_off[t - T.u0] : 0;
     int *d = nullptr;
     while (true) {
         int jmin = 0x7fffffff;
@@ -272,7 +272,7 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
             }
         ++ncol;
     }
-    if (!fill) T.tile_cnt[t] = n;
+    if (!fill) T.tile_cnt[t - T.u0] = n;
 }
 
 // one thread per tile: K-steps = union over the tile's A rows intersected with
@@ -347,9 +347,11 @@ struct TcArgs {
     const int *sys_of_row;
     const double *c_lin, *c_sq, *tau0, *tau1;
     int job_tau_sel[kMaxJobs];
-    double *out_val;
+    double *out_val;        // upper slot s at index uidx[s] - u0
     float *out_nrm;
     uint8_t *keep;
+    const int *uidx;
+    int64_t u0;
     int *err;
 };
 
@@ -550,16 +552,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
                 const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
                 const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
-                double *o = A.out_val + (size_t)s * kPlaneElems;
+                double *o = A.out_val + (size_t)(A.uidx[s] - A.u0) * kPlaneElems;
                 for (int r = 0; r < 32; ++r) o[r * 32 + lane] = (double)S[r * 33 + lane];
-                if (!diag) {
-                    double *ot = A.out_val + (size_t)stt * kPlaneElems;
-                    for (int r = 0; r < 32; ++r) ot[r * 32 + lane] = (double)S[lane * 33 + r];
-                }
                 if (lane == 0) {
                     A.out_nrm[s] = nrm;
                     A.keep[s] = kp;
-                    if (!diag) { A.out_nrm[stt] = nrm; A.keep[stt] = kp; }
                 }
                 __syncwarp();
             }
@@ -636,7 +633,8 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     A.slot_t = a.slot_t; A.sys_of_row = a.sys_of_row; A.c_lin = a.c_lin; A.c_sq = a.c_sq;
     A.tau0 = a.tau0; A.tau1 = a.tau1;
     for (int p = 0; p < kMaxJobs; ++p) A.job_tau_sel[p] = a.job_tau_sel[p];
-    A.out_val = a.out_val; A.out_nrm = a.out_nrm; A.keep = a.keep; A.err = w.counters.p;
+    A.out_val = a.out_val; A.out_nrm = a.out_nrm; A.keep = a.keep; A.uidx = a.uidx; A.u0 = a.u0;
+    A.err = w.counters.p;
     static bool attr = false;
     if (!attr) {
         RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
@@ -650,10 +648,11 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
 }
 
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, JobMask job_mask, cudaStream_t st) {
+                     const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st) {
     TcPlan plan{};
-    const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL, njob = jt.njob;
-    const int nrow4 = njob * NB4;
+    const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL;
+    const int nrow4 = unit1 - unit0;
+    if (nrow4 <= 0) return plan;
     w.counters.ensure(8);
     RDM_CUDA_TRY(cudaMemsetAsync(w.counters.p, 0, 8 * sizeof(int), st));
     w.tile_cnt.ensure(nrow4 + 1);
@@ -663,6 +662,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NB4 = NB4; T.jt = jt;
     T.out_rp = out_rp; T.mcol = mcol; T.sys_of_row = sd.sys_of_row.p; T.active = sd.active.p;
     T.job_mask = job_mask;
+    T.u0 = unit0; T.u1 = unit1;
     T.sys_tier = sd.tier.p;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
     k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 0);

@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -50,6 +51,25 @@ extern long long g_kernel_launches;
         RDM_CUDA_TRY(cudaGetLastError());       \
     } while (0)
 
+// device bytes held by all DevBufs of the process (current and high-water mark)
+inline std::atomic<size_t> g_dev_bytes{0};
+inline std::atomic<size_t> g_dev_bytes_peak{0};
+
+inline void *dev_alloc(size_t bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{-3, "cudaMalloc of " + std::to_string(bytes) + " bytes failed (" +
+                            std::to_string(g_dev_bytes.load()) + " bytes held by the library)"};
+    }
+    const size_t now = g_dev_bytes += bytes;
+    size_t pk = g_dev_bytes_peak.load();
+    while (now > pk && !g_dev_bytes_peak.compare_exchange_weak(pk, now)) {
+    }
+    return p;
+}
+
 // grow-only device buffer (capacity is kept across iterations and solves)
 template <class T>
 struct DevBuf {
@@ -65,23 +85,45 @@ struct DevBuf {
     }
     ~DevBuf() { release(); }
     void swap(DevBuf &o) noexcept { std::swap(p, o.p); std::swap(cap, o.cap); }
+    // headroom for regrowth: a quarter, a sixteenth above 1 GiB
+    static size_t with_headroom(size_t n) {
+        if (n < 16) return 16;
+        return n * sizeof(T) > (size_t(1) << 30) ? n + n / 16 : n + n / 4;
+    }
+    // contents are not kept
     T *ensure(size_t n) {
         if (n <= cap && p) return p;
-        size_t want = n < 16 ? 16 : n + n / 4;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        cudaError_t e = cudaMalloc((void **)&p, want * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            throw Error{-3, "cudaMalloc of " + std::to_string(want * sizeof(T)) + " bytes failed"};
+        const size_t want = with_headroom(n);
+        release();
+        p = (T *)dev_alloc(want * sizeof(T));
+        cap = want;
+        return p;
+    }
+    // keeps the first `used` elements (copied on stream st); the old and the
+    // new allocation coexist during the copy
+    T *grow_keep(size_t n, size_t used, cudaStream_t st) {
+        if (n <= cap && p) return p;
+        const size_t want = with_headroom(n);
+        T *q = (T *)dev_alloc(want * sizeof(T));
+        if (p && used) {
+            cudaError_t e = cudaMemcpyAsync(q, p, used * sizeof(T), cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                g_dev_bytes -= want * sizeof(T);
+                throw Error{-4, std::string("buffer regrowth copy: ") + cudaGetErrorString(e)};
+            }
         }
+        release();
+        p = q;
         cap = want;
         return p;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            g_dev_bytes -= cap * sizeof(T);
+        }
         p = nullptr;
         cap = 0;
     }
@@ -113,7 +155,7 @@ struct MatSet {
     int64_t total = 0;
     void release() {
         row_ptr.release(); col.release(); val.release(); nrm.release();
-        ophi.release(); oplo.release();
+        ophi.release(); oplo.release(); opf32.release();
         nnzb.clear(); total = 0;
     }
 };
@@ -150,7 +192,7 @@ struct JobMask {
 // ---------------------------------------------------------------------------
 
 // k_scan.cu: exclusive scan (out may alias in); returns nothing, total at out[n]
-void scan_exclusive_i32(const int *in, int *out, int n, int *tmp, cudaStream_t st);
+void scan_exclusive_i32(const int *in, int *out, int n, int *tmp, cudaStream_t st, int init = 0);
 void scan_exclusive_i64(const int *in, int64_t *out, int n, int64_t *tmp, cudaStream_t st);
 size_t scan_tmp_elems(int n);
 
@@ -223,9 +265,15 @@ struct NumArgs {
     const double *c_lin, *c_sq, *tau0, *tau1;
     const int *active;
     int job_tau_sel[kMaxJobs];
+    // outputs: only upper-triangle slots (col >= row) are computed; the
+    // values of upper slot s go to out_val at index uidx[s] - u0 (uidx: rank
+    // of s among the upper slots, u0: that of the group's first one);
+    // norm bound and keep flag to out_nrm[s], keep[s]
     double *out_val;
     float *out_nrm;
     uint8_t *keep;
+    const int *uidx;
+    int64_t u0;
     int b;
 };
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
@@ -240,15 +288,40 @@ void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot
                         JobMask tc, JobMask m64, JobMask m32, unsigned long long *out, cudaStream_t st);
 // upper slots of the active systems' jobs selected by job_mask (per system
 // tier), plus (with_inactive) all upper slots of converged systems
-void launch_build_work(const int *slot_row, const int *out_col, int64_t nslot,
+// (slots [s0, s1) only)
+void launch_build_work(const int *slot_row, const int *out_col, int64_t s0, int64_t s1,
                        int *work, int *nwork, cudaStream_t st, const int *sys_of_row,
                        const int *active, const int *slot_job, const int *sys_tier, JobMask job_mask,
                        int with_inactive);
-void launch_compact_count(const int *out_row_ptr, const uint8_t *keep, int nrows_total,
-                          int *cnt, cudaStream_t st);
-void launch_compact_copy(const int *out_row_ptr, const int *out_col, const double *out_val,
-                         const float *out_nrm, const uint8_t *keep, const int *new_row_ptr,
-                         int nrows_total, int b, int *new_col, double *new_val,
-                         float *new_nrm, cudaStream_t st);
+// uidx[s] = 1 for upper slots (col >= row), else 0 (scanned afterwards)
+void launch_upper_flags(const int *slot_row, const int *out_col, int64_t nslot, int *uidx,
+                        cudaStream_t st);
+// urp[r] = uidx[out_row_ptr[r]] for r in [0, n]
+void launch_gather_i32(const int *idx, const int *src, int n, int *dst, cudaStream_t st);
+
+// Compaction of the rows [r0, r0 + nrows) of the mask.  An upper slot is kept
+// on its own flag; a lower slot t on that of its upper partner slot_t[t],
+// and receives that block's transpose, read from out_val when the partner
+// belongs to the current group (uidx >= u0) and otherwise from the already
+// compacted output (dest[partner]).  dest[s] receives the output position of
+// every kept upper slot s.
+struct CompactArgs {
+    const int *out_rp, *out_col, *slot_row, *slot_t, *uidx;
+    const double *out_val;
+    const float *out_nrm;
+    const uint8_t *keep;
+    int64_t u0;
+    int *dest;
+    int *src;               // [kept blocks of the group]: slot of output block d0 + k
+    const int *new_rp;
+    int *new_col;
+    double *new_val;
+    float *new_nrm;
+    int r0, nrows, b;
+    int d0;                 // first output block of the group
+};
+void launch_compact_count(const CompactArgs &c, int *cnt, cudaStream_t st);
+// output blocks [d0, d1) of the group
+void launch_compact_copy(const CompactArgs &c, int d1, cudaStream_t st);
 
 }  // namespace rdm

@@ -33,9 +33,11 @@ struct TcPlan {
 void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st);
 
 // Tile lists of one multiplication step from the output mask, for the jobs
-// selected by job_mask (per system tier).
+// selected by job_mask (per system tier) and the super-row units
+// [unit0, unit1) (unit = job * ceil(NB/4) + I covers block rows 4I..4I+3 of
+// the job).
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, JobMask job_mask, cudaStream_t st);
+                     const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st);
 
 // Numeric phase on the tensor cores; same output contract as
 // launch_numeric_simt for the slots of active systems.  Returns the flops

@@ -60,7 +60,7 @@ class rdm_params(C.Structure):
                 ("tol", C.c_double), ("stall_tol", C.c_double), ("spin_factor", C.c_double),
                 ("max_iter", C.c_int32), ("mode", C.c_int32), ("min_iter", C.c_int32),
                 ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
-                ("symbolic_hash", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class rdm_info(C.Structure):
@@ -71,7 +71,8 @@ class rdm_info(C.Structure):
                 ("useful_flops", C.c_double), ("issued_flops", C.c_double),
                 ("kernel_ms", C.c_double * 6), ("kernel_flops", C.c_double * 3),
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
-                ("numeric_bytes", C.c_double)]
+                ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
+                ("product_groups", C.c_int32), ("pad0", C.c_int32)]
 
 
 class rdm_iter_log(C.Structure):

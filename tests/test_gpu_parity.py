@@ -11,7 +11,7 @@ import pytest
 from oracle import exact_response, polarizability, tc2_response
 from oracle.dense import rel_frobenius
 from oracle.tc2 import block_truncate
-from synth import Bsr, make_chain, make_cluster, make_config
+from synth import Bsr, make_batch_config, make_chain, make_cluster, make_config
 
 pytestmark = pytest.mark.gpu
 
@@ -122,6 +122,40 @@ def test_hash_symbolic_phase_is_identical(rdm, cluster150):
     assert np.array_equal(hsh.p0().vals, ref.p0().vals)
     for d in range(3):
         assert np.array_equal(hsh.p1(0, d).vals, ref.p1(0, d).vals)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed_fp16"])
+def test_job_groups_are_identical(rdm, cluster150, mode):
+    """A cap on the untruncated-product buffer (1 MiB: 128 blocks) splits every
+    step into many groups of super-rows, so most lower blocks take their
+    transpose from an earlier group's compacted output; masks, values and
+    alpha stay bit-identical to the single-group run."""
+    s = cluster150
+    ref, _, rinfo = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode=mode)
+    grp, code, info = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode=mode, chunk_mb=1)
+    assert code == rdm.RDM_OK
+    assert rinfo.product_groups == 1 and info.product_groups >= 8
+    assert info.iterations == rinfo.iterations
+    assert info.device_bytes_peak > 0
+    assert np.array_equal(grp.p0().col_idx, ref.p0().col_idx)
+    assert np.array_equal(grp.p0().vals, ref.p0().vals)
+    for d in range(3):
+        assert np.array_equal(grp.p1(0, d).col_idx, ref.p1(0, d).col_idx)
+        assert np.array_equal(grp.p1(0, d).vals, ref.p1(0, d).vals)
+    assert np.array_equal(grp.alpha(), ref.alpha())
+
+
+def test_job_groups_batch_identical(rdm):
+    """Job groups over a batch of uneven systems (chains and clusters)."""
+    systems = make_batch_config(n_systems=4, lo=40, hi=160)
+    ref, _, _ = gpu_solve(rdm, systems, tau=1e-6, tol=1e-9, mode="mixed_fp16")
+    grp, code, info = gpu_solve(rdm, systems, tau=1e-6, tol=1e-9, mode="mixed_fp16", chunk_mb=1)
+    assert code == rdm.RDM_OK and info.product_groups > 1
+    for k in range(len(systems)):
+        assert np.array_equal(grp.p0(k).vals, ref.p0(k).vals)
+        for d in range(3):
+            assert np.array_equal(grp.p1(k, d).vals, ref.p1(k, d).vals)
+        assert np.array_equal(grp.alpha(k), ref.alpha(k))
 
 
 def test_cluster_fp32_vs_oracle(rdm, cluster150, oracle150):
