@@ -113,7 +113,7 @@ typedef struct {
     int32_t use_graphs;     /* 1: capture the iteration in CUDA graphs when possible */
     int32_t verbose;        /* 1: per-iteration log to stderr */
     int32_t refine_x1;      /* mixed modes, final tier, arithmetic of the first-order products
-                               (RDM_REFINE_*); X0^2 is always FP64 there */
+                               (RDM_REFINE_*) */
     int32_t symbolic_hash;  /* 1: use the hash-table symbolic phase (otherwise chosen only for
                                systems above 8,192 block rows); results are identical */
     int32_t chunk_mb;       /* cap in MiB on the buffer of untruncated product blocks (8 b^2 + 5
@@ -121,7 +121,10 @@ typedef struct {
                                then multiplied in groups of consecutive jobs that fit it (at
                                least one job per group).  0: automatic, from the free device
                                memory.  Results do not depend on the grouping. */
-    int32_t reserved[2];
+    int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT or
+                               RDM_REFINE_FP64 (FP64), RDM_REFINE_FP32 (FP32 on the CUDA cores; the
+                               final tier then ends on the idempotency stall) */
+    int32_t reserved[1];
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */

@@ -380,12 +380,12 @@ bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
 // Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
 // Mixed modes: tier 0 runs every product as a split product on the tensor
 // cores.  In the final tier the purification X0^2 is refined in FP64 on the
-// CUDA cores; the first-order products use `refine_x1` (RDM_REFINE_*): the
-// default is FP32 on the CUDA cores for the fp16 mode and FP64 for the bf16
-// mode.  (Split products in the final tier leave ~1e-6 of the tensor cores'
-// accumulation error in alpha; FP32 with round-to-nearest accumulation does
-// not.)
-void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0) {
+// CUDA cores (`refine_x0` = RDM_REFINE_FP32 moves it to FP32); the
+// first-order products use `refine_x1` (RDM_REFINE_*): the default is FP32 on
+// the CUDA cores for the fp16 mode and FP64 for the bf16 mode.  (Split
+// products in the final tier leave ~1e-6 of the tensor cores' accumulation
+// error in alpha; FP32 with round-to-nearest accumulation does not.)
+void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0) {
     if (refine_x1 == RDM_REFINE_DEFAULT)
         refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32 : RDM_REFINE_FP64;
     for (int p = 0; p < njob; ++p) {
@@ -396,7 +396,8 @@ void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0) {
             case RDM_MODE_MIXED_BF16:
             case RDM_MODE_MIXED_FP16:
                 if (tier == 0) ar[p] = split;
-                else if (p == 0 || refine_x1 == RDM_REFINE_FP64) ar[p] = AR_FP64;
+                else if (p == 0) ar[p] = refine_x0 == RDM_REFINE_FP32 ? AR_FP32 : AR_FP64;
+                else if (refine_x1 == RDM_REFINE_FP64) ar[p] = AR_FP64;
                 else ar[p] = refine_x1 == RDM_REFINE_SPLIT ? split : AR_FP32;
                 break;
             default: ar[p] = AR_FP64;
@@ -898,7 +899,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         Arith tab[kMaxTiers][kMaxJobs];
         unsigned tiers_present = 0;
         std::vector<int> tier_of(S, 0);
-        for (int t = 0; t <= final_tier; ++t) tier_arith(P.mode, t, jt.njob, tab[t], P.refine_x1);
+        for (int t = 0; t <= final_tier; ++t) tier_arith(P.mode, t, jt.njob, tab[t], P.refine_x1, P.refine_x0);
         for (int s = 0; s < S; ++s) {
             tier_of[s] = ss[s].tier;
             if (act[s]) tiers_present |= 1u << ss[s].tier;

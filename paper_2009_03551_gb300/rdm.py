@@ -60,7 +60,8 @@ class rdm_params(C.Structure):
                 ("tol", C.c_double), ("stall_tol", C.c_double), ("spin_factor", C.c_double),
                 ("max_iter", C.c_int32), ("mode", C.c_int32), ("min_iter", C.c_int32),
                 ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
-                ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("refine_x0", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class rdm_info(C.Structure):

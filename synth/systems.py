@@ -78,6 +78,25 @@ class Bsr:
         a = a.reshape(self.nb * b, self.nb * b)
         return a if padded else a[: self.n, : self.n]
 
+    def submatrix_dense(self, idx: np.ndarray) -> np.ndarray:
+        """Dense A[idx][:, idx] for sorted row/column indices, read from the
+        blocks that intersect them (the full matrix is never formed)."""
+        b = self.b
+        idx = np.asarray(idx, dtype=np.int64)
+        loc = np.full(self.nb * b, -1, dtype=np.int64)
+        loc[idx] = np.arange(idx.size)
+        blk_has = np.zeros(self.nb, dtype=bool)
+        blk_has[idx // b] = True
+        rows = self.row_of_block()
+        sel = np.nonzero(blk_has[rows] & blk_has[self.col_idx])[0]
+        out = np.zeros((idx.size, idx.size), dtype=np.float64)
+        for k in sel:
+            lr = loc[rows[k] * b + np.arange(b)]
+            lc = loc[int(self.col_idx[k]) * b + np.arange(b)]
+            mr, mc = lr >= 0, lc >= 0
+            out[np.ix_(lr[mr], lc[mc])] = self.vals[k][np.ix_(mr, mc)]
+        return out
+
     @staticmethod
     def from_dense(a: np.ndarray, b: int, drop_zero_blocks: bool = True,
                    keep_diagonal: bool = True) -> "Bsr":
@@ -325,8 +344,8 @@ def carve_sphere(sys_: System, n_keep: int, b: int | None = None, name: str | No
     keep = np.sort(np.argsort(d, kind="stable")[:n_keep])
     opa = sys_.opa
     orb = (keep[:, None] * opa + np.arange(opa)[None, :]).reshape(-1)
-    h0 = Bsr.from_dense(sys_.h0.to_dense()[np.ix_(orb, orb)], b)
-    h1 = [Bsr.from_dense(m.to_dense()[np.ix_(orb, orb)], b) for m in sys_.h1]
+    h0 = Bsr.from_dense(sys_.h0.submatrix_dense(orb), b)
+    h1 = [Bsr.from_dense(m.submatrix_dense(orb), b) for m in sys_.h1]
     return System(name or f"{sys_.name}-carve{n_keep}", sys_.kind, sys_.coords[keep], opa,
                   n_keep * opa // 2, b, h0, h1, sys_.dirs, sys_.cutoff, sys_.seed,
                   {"parent": sys_.name, "n_keep": n_keep})

@@ -144,6 +144,24 @@ def test_final_tier_first_order_arithmetic(rdm, cluster150, oracle150, refine, t
     assert abs(info.idempotency) < 1e-8
 
 
+def test_final_tier_fp32_purification(rdm, cluster150, oracle150):
+    """refine_x0 = FP32: the whole final tier on the FP32 CUDA cores.  It ends
+    on the idempotency stall (FP32 floor) instead of the FP64 one; alpha stays
+    within 1e-6 of the oracle."""
+    s = cluster150
+    ob, h1s = oracle150
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x0=3)
+    sol.load(s)
+    code, info = sol.solve()
+    assert code == rdm.RDM_OK and info.converged
+    assert info.kernel_flops[1] == 0.0          # no FP64 products
+    a = sol.alpha()
+    ao = polarizability(ob.p1s, h1s)
+    assert np.max(np.abs(a - ao)) / np.max(np.abs(ao)) <= 1e-6
+    assert abs(info.idempotency) < 1e-3
+
+
 def test_mixed_batch_with_converged_copies(rdm):
     systems = [make_chain(40, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=21, dirs=("x", "y", "z")),
                make_cluster(90, opa=8, b=32, cutoff=10.0, seed=22, dirs=("x", "y", "z"))]
