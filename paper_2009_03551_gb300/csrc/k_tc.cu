@@ -18,16 +18,24 @@
 // matrix, core matrices adjacent along K 128 bytes apart, 8-row groups 512
 // bytes apart), so one 2 KB bulk copy per block lands ready for the MMA.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over a static tile
-// schedule): warp 0 issues the bulk copies into a 4-stage ring, warp 1 owns
-// the tensor-memory allocation and one thread issues the MMAs, warps 2-5
-// (one per TMEM lane quarter = one block row of the tile) run the epilogue:
-// C = c_lin X + c_sq D, diagonal blocks symmetrised, block Frobenius norm,
-// truncation flag, FP64 store of the block and of its transpose.  The
-// accumulator is double-buffered in TMEM (2 x 128 columns) so the epilogue of
-// one tile overlaps the MMAs of the next.  Every mbarrier wait is bounded: on
-// timeout the kernel raises an error flag, drains what it issued and frees its
-// tensor memory.
+// Warp roles (320 threads, one CTA per SM, persistent over a static tile
+// schedule): warp 0 issues the bulk copies into a 6-stage ring, warp 1 owns
+// the tensor-memory allocation and one thread issues the MMAs, warps 2-9 (two
+// per TMEM lane quarter = block row of the tile, two block columns each) run
+// the epilogue.
+//
+// Accumulation in segments.  The tensor cores' FP32 accumulation truncates
+// (it is not round-to-nearest), so a long accumulation chain drifts towards
+// zero: measured on positive data, -2e-7 relative per K-step, -2e-5 after 96
+// K-steps.  The K-steps of a tile are therefore accumulated in segments of
+// kSegSteps in fresh TMEM accumulators (4 rotating buffers of 128 columns);
+// the epilogue warps add every finished segment to registers with
+// round-to-nearest FP32 adds and release the buffer.  The drift is then that
+// of one segment (-7e-7 relative), independent of the tile's length.  After
+// the last segment: C = c_lin X + c_sq D, diagonal blocks symmetrised, block
+// Frobenius norm, truncation flag, FP64 store of the (upper-triangle) block.
+// Every mbarrier wait is bounded: on timeout the kernel raises an error flag,
+// drains what it issued and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -45,8 +53,11 @@ constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
 constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
 constexpr int kTilePlaneBytes = TBL * kPlaneBytes;      // 8 KB: 4 blocks stacked
 constexpr int kStageBytes = 4 * kTilePlaneBytes;        // A_hi, A_lo, B_hi, B_lo
-constexpr int kThreads = 192;
-constexpr int kTileInts = 24;                // p, I, -, nsteps, slot[16], column j of each tile column[4]
+constexpr int kEpiWarps = 8;                 // epilogue warps: 2 per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTileInts = 24;
+constexpr int kSegSteps = 4;                 // K-steps accumulated in tensor memory per segment
+constexpr int kSegBufs = 4;                  // segment accumulators in TMEM (4 x 128 columns)                // p, I, -, nsteps, slot[16], column j of each tile column[4]
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------------------
@@ -357,7 +368,7 @@ struct TcArgs {
 
 struct __align__(8) SmemCtl {
     uint64_t full[kStages], empty[kStages];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t seg_full[kSegBufs], seg_empty[kSegBufs];
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
@@ -366,15 +377,15 @@ struct __align__(8) SmemCtl {
 __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = smem_raw;                                       // kStages * 32 KB
-    float *stage_ep = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes);   // 4 warps x 32 x 33
-    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_ep + 4 * 32 * 33);
+    float *stage_ep = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes);   // kEpiWarps x 32 x 33
+    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_ep + kEpiWarps * 32 * 33);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->acc_full[b], 1); mbar_init(&ctl->acc_empty[b], 4); }
+        for (int b = 0; b < kSegBufs; ++b) { mbar_init(&ctl->seg_full[b], 1); mbar_init(&ctl->seg_empty[b], kEpiWarps); }
         mbar_init(&ctl->drain, 1);
         ctl->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -383,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&ctl->tmem_base)),
-                     "r"(256)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -448,38 +459,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            uint32_t it = 0, lt = 0;
+            uint32_t it = 0, seg = 0;
             bool issued = false;
-            for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x, ++lt) {
-                const int buf = lt & 1;
-                const uint32_t use = lt >> 1;
-                if (!mbar_wait(&ctl->acc_empty[buf], (use & 1) ^ 1, abort_flag)) break;
-                fence_after();
-                const uint32_t d_tmem = tmem + buf * 128;
+            for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
                 const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
                 bool ok = true;
-                for (int64_t q = s0; q < s1; ++q, ++it) {
-                    const int st = it % kStages;
-                    const uint32_t ph = (it / kStages) & 1;
-                    if (!mbar_wait(&ctl->full[st], ph, abort_flag)) { ok = false; break; }
+                for (int64_t q = s0; q < s1 && ok; ++seg) {
+                    // one segment: up to kSegSteps K-steps into a fresh accumulator
+                    const int buf = seg & (kSegBufs - 1);
+                    const uint32_t use = seg / kSegBufs;
+                    if (!mbar_wait(&ctl->seg_empty[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t base = smem_u32(stages + st * kStageBytes);
-                    const uint32_t a_hi = base, a_lo = base + kTilePlaneBytes;
-                    const uint32_t b_hi = base + 2 * kTilePlaneBytes, b_lo = base + 3 * kTilePlaneBytes;
+                    const uint32_t d_tmem = tmem + buf * 128;
+                    const int64_t qe = q + kSegSteps < s1 ? q + kSegSteps : s1;
+                    const int64_t qs = q;
+                    for (; q < qe; ++q, ++it) {
+                        const int st = it % kStages;
+                        const uint32_t ph = (it / kStages) & 1;
+                        if (!mbar_wait(&ctl->full[st], ph, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t base = smem_u32(stages + st * kStageBytes);
+                        const uint32_t a_hi = base, a_lo = base + kTilePlaneBytes;
+                        const uint32_t b_hi = base + 2 * kTilePlaneBytes, b_lo = base + 3 * kTilePlaneBytes;
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t ko = kk * 256;
-                        const uint32_t first = (q == s0 && kk == 0) ? 0u : 1u;
-                        mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, first);
-                        mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_lo + ko, 128, 512), A.idesc, 1u);
-                        mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, 1u);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t ko = kk * 256;
+                            const uint32_t first = (q == qs && kk == 0) ? 0u : 1u;
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, first);
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_lo + ko, 128, 512), A.idesc, 1u);
+                            mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, 1u);
+                        }
+                        issued = true;
+                        mma_commit(&ctl->empty[st]);
                     }
-                    issued = true;
-                    mma_commit(&ctl->empty[st]);
+                    if (ok) mma_commit(&ctl->seg_full[buf]);
                 }
                 if (!ok) break;
-                if (s1 > s0) mma_commit(&ctl->acc_full[buf]);
-                else mbar_arrive(&ctl->acc_full[buf]);
             }
             if (*abort_flag && issued) {
                 // drain: wait (bounded) until every MMA this thread issued has completed
@@ -490,37 +505,79 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lane quarter = block row ----------------
+        // ---------------- epilogue: warps 2..9, TMEM lane quarter = block row ----------------
         const int eq = warp & 3;                       // lanes 32*eq .. 32*eq+31
+        const int n0 = ((warp - 2) >> 2) * 2;           // this warp's two column blocks n0, n0+1
         float *S = stage_ep + (warp - 2) * 32 * 33;
-        uint32_t lt = 0;
-        for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x, ++lt) {
-            const int buf = lt & 1;
-            const uint32_t use = lt >> 1;
-            if (!mbar_wait(&ctl->acc_full[buf], use & 1, abort_flag)) break;
-            fence_after();
+        uint32_t seg = 0;
+        for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
+            // metadata of this warp's 2 output blocks, one lane each (lanes 0..1),
+            // gathered while the tile's MMAs run; the old X blocks of the
+            // linear term are prefetched into L2
             const int *d = A.tiles + (size_t)t * kTileInts;
+            int m_s = -1, m_sx = -1, m_diag = 0, m_keepidx = 0;
+            float m_cl = 0.f, m_cq = 0.f;
+            double m_tau = 0.0;
+            if (lane < 2) {
+                m_s = d[4 + eq * 4 + n0 + lane];
+                if (m_s >= 0) {
+                    const int i = A.slot_row[m_s];
+                    const int sys = A.sys_of_row[i];
+                    const int job = A.slot_job[m_s];
+                    m_cl = (float)A.c_lin[sys];
+                    // undo the operand scaling: every term of a job has the same scale product
+                    m_cq = (float)A.c_sq[sys] / (A.scale[A.job_a[job]] * A.scale[A.job_b[job]]);
+                    m_tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
+                    m_sx = A.slot_x[m_s];
+                    m_diag = A.slot_t[m_s] == m_s;
+                    m_keepidx = A.uidx[m_s] - (int)A.u0;
+                    if (m_sx >= 0 && m_cl != 0.f) {
+                        const double *px = A.in_val + (size_t)m_sx * kPlaneElems;
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8192) : "memory");
+                    }
+                }
+            }
             const int nst = d[3];
             if (nst < 0 && lane == 0) atomicOr(A.err, 4);
-            for (int n = 0; n < TBL; ++n) {
-                const int s = d[4 + eq * 4 + n];
+            // the tile's accumulator: sum of its segments, added with
+            // round-to-nearest in registers (row 32*eq + lane, this warp's 64 columns)
+            float racc[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) racc[c] = 0.f;
+            const int nseg = nst > 0 ? (nst + kSegSteps - 1) / kSegSteps : 0;
+            bool ok = true;
+            for (int g = 0; g < nseg; ++g, ++seg) {
+                const int buf = seg & (kSegBufs - 1);
+                const uint32_t use = seg / kSegBufs;
+                if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag)) { ok = false; break; }
+                fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * 128;
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    float part[32];
+                    tmem_ld32(ta + (n0 + n) * 32, part);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) racc[n * 32 + c] += part[c];
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->seg_empty[buf]);
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const int s = __shfl_sync(0xffffffffu, m_s, n);
                 if (s < 0) continue;
                 float acc[32];
-                __syncwarp();
-                if (nst > 0) tmem_ld32(tmem + ((uint32_t)(32 * eq) << 16) + buf * 128 + n * 32, acc);
-                else {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-                }
-                const int i = A.slot_row[s];
-                const int sys = A.sys_of_row[i];
-                const int job = A.slot_job[s];
-                const float cl = (float)A.c_lin[sys];
-                // undo the operand scaling: every term of a job has the same scale product
-                const float cq = (float)A.c_sq[sys] / (A.scale[A.job_a[job]] * A.scale[A.job_b[job]]);
-                const double tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
-                const int sx = A.slot_x[s], stt = A.slot_t[s];
-                const bool diag = (stt == s);
+                for (int c = 0; c < 32; ++c) acc[c] = racc[n * 32 + c];
+                __syncwarp();
+                const float cl = __shfl_sync(0xffffffffu, m_cl, n);
+                const float cq = __shfl_sync(0xffffffffu, m_cq, n);
+                const double tau = __shfl_sync(0xffffffffu, m_tau, n);
+                const int sx = __shfl_sync(0xffffffffu, m_sx, n);
+                const bool diag = __shfl_sync(0xffffffffu, m_diag, n) != 0;
+                const int oidx = __shfl_sync(0xffffffffu, m_keepidx, n);
                 // linear term: each lane reads its own row (256 contiguous bytes)
                 if (sx >= 0 && cl != 0.f) {
                     const double2 *gx = reinterpret_cast<const double2 *>(A.in_val + (size_t)sx * kPlaneElems + lane * 32);
@@ -552,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
                 const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
                 const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
-                double *o = A.out_val + (size_t)(A.uidx[s] - A.u0) * kPlaneElems;
+                double *o = A.out_val + (size_t)oidx * kPlaneElems;
                 for (int r = 0; r < 32; ++r) o[r * 32 + lane] = (double)S[r * 33 + lane];
                 if (lane == 0) {
                     A.out_nrm[s] = nrm;
@@ -560,9 +617,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 }
                 __syncwarp();
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->acc_empty[buf]);
         }
     }
 
@@ -572,11 +626,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     if (warp == 1) {
         __syncwarp();
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 4 * 32 * 33 * sizeof(float) + sizeof(SmemCtl) + 1024;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + kEpiWarps * 32 * 33 * sizeof(float) + sizeof(SmemCtl) + 1024;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel exceeds 227 KB");
 
 }  // namespace
