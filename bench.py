@@ -377,7 +377,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
                                     "reductions_setup_host": kms[5]},
-            "tier_iterations": list(last.tier_iters)[:2],
+            "tier_iterations": list(last.tier_iters)[:3],
             "device_gb_peak": last.device_bytes_peak / 1e9, "product_groups": int(last.product_groups),
             "clocks": clocks}
     return line

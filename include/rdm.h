@@ -63,17 +63,22 @@ extern "C" {
 #define RDM_MODE_FP32        1   /* every product in FP32 (CUDA cores), FP64 scalars */
 #define RDM_MODE_MIXED_BF16  2   /* bf16 hi+lo split products on the tensor cores
                                     (tcgen05, FP32 accumulate) until the idempotency
-                                    error stalls, then a final tier with X0^2 in FP64
-                                    (CUDA cores) and the first-order products split */
+                                    error stalls, then a final tier on the CUDA cores:
+                                    X0^2 in FP64, the first-order products in FP64
+                                    (refine_x0 / refine_x1 choose otherwise) */
 #define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
                                     by a power of two into fp16's normal range
-                                    (22-bit products instead of 16-bit) */
+                                    (22-bit products instead of 16-bit); final tier:
+                                    X0^2 in FP64, first-order products in FP32 */
 
 /* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
 #define RDM_REFINE_DEFAULT   0   /* FP32 for RDM_MODE_MIXED_FP16, FP64 for RDM_MODE_MIXED_BF16 */
 #define RDM_REFINE_FP64      1
 #define RDM_REFINE_SPLIT     2   /* keep the tensor-core split product */
 #define RDM_REFINE_FP32      3   /* FP32 on the CUDA cores (round-to-nearest accumulation) */
+#define RDM_REFINE_FP32X2    4   /* double-FP32 on the CUDA cores: each FP64 value as the sum of
+                                    two FP32 words, the products accumulated with error-free
+                                    transformations (about 46 bits; 32 x 32 blocks) */
 
 typedef struct rdm_handle rdm_handle;
 
@@ -141,13 +146,14 @@ typedef struct {
     double  time_ms;        /* wall time of the solve on the handle's stream */
     double  useful_flops;   /* 2 b^3 per (i,k,j) block triple, summed over the solve */
     double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
-    double  kernel_ms[6];   /* device time per kernel class (CUDA events on the handle's stream):
+    double  kernel_ms[7];   /* device time per kernel class (CUDA events on the handle's stream):
                                0 symbolic mask + pair / tile lists, 1 tensor-core products,
                                2 FP64 CUDA-core products, 3 FP32 CUDA-core products (and copies
                                of converged systems), 4 truncation compaction, 5 reductions,
-                               set-up and host decisions (the remainder of the solve) */
-    double  kernel_flops[3];   /* useful flops (2 b^3 per block triple) of the tensor-core (0),
-                                  FP64 (1) and FP32 (2) product launches */
+                               set-up and host decisions (the remainder of the solve),
+                               6 double-FP32 CUDA-core products */
+    double  kernel_flops[4];   /* useful flops (2 b^3 per block triple) of the tensor-core (0),
+                                  FP64 (1), FP32 (2) and double-FP32 (3) product launches */
     int64_t kernel_launches;   /* kernels launched by the solve */
     int32_t tc_launches;       /* launches of the tensor-core product kernel */
     int32_t simt_launches;     /* launches of the CUDA-core product kernel */

@@ -78,7 +78,7 @@ struct rdm_handle {
 
     // work buffers
     DevBuf<int> row_cnt, row_off, pool_col, pool_npair, counters, mask_col;
-    DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work, work2;
+    DevBuf<int> out_rp, slot_row, slot_job, slot_npair, slot_x, slot_t, work, work2, work3;
     DevBuf<int64_t> pair_off, scan_tmp64;
     DevBuf<int> scan_tmp32, pair_a, pair_b, cnt_rows;
     DevBuf<int> uidx, scan_tmp_s, urp, dest, cpsrc;   // upper-slot ranks, compaction maps
@@ -88,7 +88,7 @@ struct rdm_handle {
     DevBuf<unsigned long long> class_pairs;
     DevBuf<double> row_lo, row_hi;
     TcWork tcw;
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void ensure_events() {
         for (auto &e : ev)
             if (!e) RDM_CUDA_TRY(cudaEventCreate(&e));
@@ -367,10 +367,10 @@ void assemble(rdm_handle *h) {
 struct StepStats {
     int64_t npairs = 0;
     int64_t nslot = 0;
-    int64_t pairs_tc = 0, pairs_64 = 0, pairs_32 = 0;   // block triples per kernel class
+    int64_t pairs_tc = 0, pairs_64 = 0, pairs_32 = 0, pairs_ff = 0;   // block triples per kernel class
     double issued_tc = 0;
     double bytes = 0;
-    double ms[5] = {0, 0, 0, 0, 0};         // symbolic, tc, fp64, fp32, compaction
+    double ms[6] = {0, 0, 0, 0, 0, 0};      // symbolic, tc, fp64, fp32, compaction, double-fp32
     int tc_launches = 0, simt_launches = 0;
     int groups = 1;                         // job groups of the numeric phase
 };
@@ -396,8 +396,10 @@ void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int 
             case RDM_MODE_MIXED_BF16:
             case RDM_MODE_MIXED_FP16:
                 if (tier == 0) ar[p] = split;
-                else if (p == 0) ar[p] = refine_x0 == RDM_REFINE_FP32 ? AR_FP32 : AR_FP64;
+                else if (p == 0) ar[p] = refine_x0 == RDM_REFINE_FP32 ? AR_FP32
+                                        : refine_x0 == RDM_REFINE_FP32X2 ? AR_FF : AR_FP64;
                 else if (refine_x1 == RDM_REFINE_FP64) ar[p] = AR_FP64;
+                else if (refine_x1 == RDM_REFINE_FP32X2) ar[p] = AR_FF;
                 else ar[p] = refine_x1 == RDM_REFINE_SPLIT ? split : AR_FP32;
                 break;
             default: ar[p] = AR_FP64;
@@ -416,9 +418,12 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     const int nrows = njob * NB;
     int max_ns = *std::max_element(h->nbs.begin(), h->nbs.end());
     StepStats ss;
-    JobMask tcm{}, m64{}, m32{}, simt{};
+    // CUDA-core classes, launched in this order: FP64, double-FP32, FP32
+    constexpr int kSimt = 3;
+    const Arith simt_ar[kSimt] = {AR_FP64, AR_FF, AR_FP32};
+    JobMask tcm{}, cm[kSimt]{}, simt{};
     Arith tc_ar = AR_FP16X3;
-    bool any_tc = false, any64 = false, any32 = false;
+    bool any_tc = false, any_c[kSimt] = {false, false, false};
     for (int t = 0; t < kMaxTiers; ++t) {
         if (!((tiers_present >> t) & 1u)) continue;
         for (int p = 0; p < njob; ++p) {
@@ -427,23 +432,21 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
                 tcm.m[t] |= 1u << p;
                 tc_ar = a;
                 any_tc = true;
-            } else if (a == AR_FP64) {
-                m64.m[t] |= 1u << p;
-                any64 = true;
-            } else {
-                m32.m[t] |= 1u << p;
-                any32 = true;
+                continue;
             }
+            const int c = a == AR_FP64 ? 0 : a == AR_FF ? 1 : 2;
+            cm[c].m[t] |= 1u << p;
+            any_c[c] = true;
         }
-        simt.m[t] = m64.m[t] | m32.m[t];
+        simt.m[t] = cm[0].m[t] | cm[1].m[t] | cm[2].m[t];
     }
-    // first CUDA-core launch: the FP64 jobs (else the FP32 ones) plus the copies
-    // of converged systems; second launch: the FP32 jobs when both kinds exist
-    const Arith simt_ar = any64 ? AR_FP64 : AR_FP32;
-    const JobMask first_mask = any64 ? m64 : m32;
-    const bool second = any64 && any32;
+    // the first class present also copies the blocks of converged systems (the
+    // FP32 class when no CUDA-core product is left)
+    int first_c = kSimt - 1;
+    for (int c = kSimt - 1; c >= 0; --c)
+        if (any_c[c]) first_c = c;
     const bool tc = any_tc;
-    const bool m32_any = any32;
+    const bool f32_planes = any_c[1] || any_c[2];
     h->ensure_events();
     RDM_CUDA_TRY(cudaEventRecord(h->ev[0], st));
     // operand copies are made afresh from the input set at every step: one
@@ -455,15 +458,18 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     take(in.ophi, out.ophi);
     take(in.oplo, out.oplo);
     take(in.opf32, out.opf32);
+    take(in.opf32lo, out.opf32lo);
     // copies the step does not use are kept for the next solve, unless they
     // are large (above 4 GiB the solve's time dwarfs a re-allocation)
     const size_t big = size_t(4) << 30;
     if (!tc && in.ophi.cap * sizeof(uint16_t) > big) { in.ophi.release(); in.oplo.release(); }
-    if (!m32_any && in.opf32.cap * sizeof(float) > big) in.opf32.release();
+    if (!f32_planes && in.opf32.cap * sizeof(float) > big) in.opf32.release();
+    if (!any_c[1] && in.opf32lo.cap * sizeof(float) > big) in.opf32lo.release();
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
-    if (m32_any) {
+    if (f32_planes) {
         in.opf32.ensure(std::max<int64_t>(in.total, 1) * bb);
-        launch_to_f32(in.val.p, in.opf32.p, in.total * (int64_t)bb, st);
+        if (any_c[1]) in.opf32lo.ensure(std::max<int64_t>(in.total, 1) * bb);
+        launch_to_f32(in.val.p, in.opf32.p, in.total * (int64_t)bb, st, any_c[1] ? in.opf32lo.p : nullptr);
     }
 
     h->row_cnt.ensure(nrows);
@@ -513,19 +519,20 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     scan_exclusive_i64(h->slot_npair.p, h->pair_off.p, (int)nslot, h->scan_tmp64.p, st);
     int64_t npairs = 0;
     d2h(&npairs, h->pair_off.p + nslot, 1, st);
-    // block triples per kernel class (tensor cores, FP64, FP32) for the accounting
+    // block triples per kernel class (tensor cores, FP64, FP32, double-FP32) for the accounting
     h->class_pairs.ensure(4);
     RDM_CUDA_TRY(cudaMemsetAsync(h->class_pairs.p, 0, 4 * sizeof(unsigned long long), st));
     launch_class_pairs(h->slot_row.p, mcol, h->slot_npair.p, h->slot_job.p, nslot, h->sd.sys_of_row.p,
-                       h->sd.active.p, h->sd.tier.p, tcm, m64, m32, h->class_pairs.p, st);
-    unsigned long long cls[3] = {0, 0, 0};
-    d2h(cls, h->class_pairs.p, 3, st);
+                       h->sd.active.p, h->sd.tier.p, tcm, cm[0], cm[2], cm[1], h->class_pairs.p, st);
+    unsigned long long cls[4] = {0, 0, 0, 0};
+    d2h(cls, h->class_pairs.p, 4, st);
     sync(h);
     ss.npairs = npairs;
     ss.pairs_tc = (int64_t)cls[0];
     ss.pairs_64 = (int64_t)cls[1];
     ss.pairs_32 = (int64_t)cls[2];
-    if (any64 || any32) {
+    ss.pairs_ff = (int64_t)cls[3];
+    if (any_c[0] || any_c[1] || any_c[2]) {
         h->pair_a.ensure(std::max<int64_t>(npairs, 1));
         h->pair_b.ensure(std::max<int64_t>(npairs, 1));
     }
@@ -536,8 +543,9 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     launch_pairs(in, jt, h->sd, h->out_rp.p, mcol, h->slot_row.p, h->slot_job.p, h->pair_off.p,
                  nslot, NB, h->pair_a.p, h->pair_b.p, h->slot_x.p, h->slot_t.p, h->counters.p + 2, st,
                  simt);
-    h->work.ensure(std::max<int64_t>(nslot, 1));
-    if (second) h->work2.ensure(std::max<int64_t>(nslot, 1));
+    DevBuf<int> *worklist[kSimt] = {&h->work, &h->work2, &h->work3};
+    for (int c = 0; c < kSimt; ++c)
+        if (any_c[c] || c == first_c) worklist[c]->ensure(std::max<int64_t>(nslot, 1));
     // rank of every upper slot among the upper slots (the products store
     // only those; compaction writes the lower blocks as transposes)
     h->uidx.ensure(nslot + 1);
@@ -613,33 +621,34 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     h->cnt_rows.ensure(nrows + 1);
     out.row_ptr.ensure(nrows + 1);
     int kept = 0;
-    float t_simt1 = 0, t_simt2 = 0, t_tc = 0, t_cmp = 0;
+    float t_simt[kSimt] = {0, 0, 0}, t_tc = 0, t_cmp = 0;
+    const int ev_simt[kSimt] = {5, 6, 4};   // events after each CUDA-core class
     for (int g = 0; g < ngroup; ++g) {
         const int ua = gunit[g], ub = gunit[g + 1];
         const int64_t s0 = gslot(ua), s1 = gslot(ub), u0 = gupper(ua);
         const int r0 = unit_row(ua), nr = unit_row(ub) - r0;
-        RDM_CUDA_TRY(cudaMemsetAsync(h->counters.p + 3, 0, 2 * sizeof(int), st));
-        // CUDA-core work: the selected jobs and the copies of converged systems
-        launch_build_work(h->slot_row.p, mcol, s0, s1, h->work.p, h->counters.p + 3, st, h->sd.sys_of_row.p,
-                          h->sd.active.p, h->slot_job.p, h->sd.tier.p, first_mask, 1);
-        if (second)
-            launch_build_work(h->slot_row.p, mcol, s0, s1, h->work2.p, h->counters.p + 4, st,
-                              h->sd.sys_of_row.p, h->sd.active.p, h->slot_job.p, h->sd.tier.p, m32, 0);
+        RDM_CUDA_TRY(cudaMemsetAsync(h->counters.p + 3, 0, kSimt * sizeof(int), st));
+        // CUDA-core work per class: the selected jobs, and in the first class
+        // the copies of converged systems
+        for (int c = 0; c < kSimt; ++c)
+            if (any_c[c] || c == first_c)
+                launch_build_work(h->slot_row.p, mcol, s0, s1, worklist[c]->p, h->counters.p + 3 + c, st,
+                                  h->sd.sys_of_row.p, h->sd.active.p, h->slot_job.p, h->sd.tier.p, cm[c],
+                                  c == first_c ? 1 : 0);
         TcPlan plan{};
         if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tcm, ua, ub, st);
         const bool tc_g = tc && plan.ntile > 0;
-        int hc[2];
-        d2h(hc, h->counters.p + 3, 2, st);
+        int nwork[kSimt];
+        d2h(nwork, h->counters.p + 3, kSimt, st);
         sync(h);
-        const int nwork = hc[0];
-        const int nwork2 = second ? hc[1] : 0;
 
         NumArgs a{};
         a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
-        a.in_f32 = m32_any ? in.opf32.p : nullptr;
+        a.in_f32 = f32_planes ? in.opf32.p : nullptr;
+        a.in_f32lo = any_c[1] ? in.opf32lo.p : nullptr;
         a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;
         a.slot_row = h->slot_row.p; a.slot_job = h->slot_job.p; a.slot_x = h->slot_x.p; a.slot_t = h->slot_t.p;
-        a.work = h->work.p; a.nwork = nwork; a.sys_of_row = h->sd.sys_of_row.p;
+        a.sys_of_row = h->sd.sys_of_row.p;
         a.c_lin = h->sd.c_lin.p; a.c_sq = h->sd.c_sq.p; a.tau0 = h->sd.tau0.p; a.tau1 = h->sd.tau1.p;
         a.active = h->sd.active.p;
         for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
@@ -647,15 +656,15 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         a.uidx = h->uidx.p; a.u0 = u0; a.b = b;
         RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
         const long long lg = g_kernel_launches;
-        if (nwork) launch_numeric_simt(a, simt_ar, st);
-        RDM_CUDA_TRY(cudaEventRecord(h->ev[5], st));
-        if (nwork2) {
-            NumArgs a2 = a;
-            a2.work = h->work2.p;
-            a2.nwork = nwork2;
-            launch_numeric_simt(a2, AR_FP32, st);
+        for (int c = 0; c < kSimt; ++c) {
+            if (nwork[c]) {
+                NumArgs ac = a;
+                ac.work = worklist[c]->p;
+                ac.nwork = nwork[c];
+                launch_numeric_simt(ac, simt_ar[c], st);
+            }
+            RDM_CUDA_TRY(cudaEventRecord(h->ev[ev_simt[c]], st));
         }
-        RDM_CUDA_TRY(cudaEventRecord(h->ev[4], st));
         ss.simt_launches += (int)(g_kernel_launches - lg);
         if (tc_g) {
             const long long lt = g_kernel_launches;
@@ -697,12 +706,14 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         kept = kept_end;
         RDM_CUDA_TRY(cudaEventRecord(h->ev[3], st));
         RDM_CUDA_TRY(cudaEventSynchronize(h->ev[3]));
-        float m15 = 0, m54 = 0, m42 = 0, m23 = 0;
-        cudaEventElapsedTime(&m15, h->ev[1], h->ev[5]);   // first CUDA-core launch
-        cudaEventElapsedTime(&m54, h->ev[5], h->ev[4]);   // second (FP32) CUDA-core launch
-        cudaEventElapsedTime(&m42, h->ev[4], h->ev[2]);   // tensor-core launch
-        cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);   // compaction
-        t_simt1 += m15; t_simt2 += m54; t_tc += m42; t_cmp += m23;
+        float mc[kSimt] = {0, 0, 0}, m42 = 0, m23 = 0;
+        cudaEventElapsedTime(&mc[0], h->ev[1], h->ev[ev_simt[0]]);             // FP64 class
+        cudaEventElapsedTime(&mc[1], h->ev[ev_simt[0]], h->ev[ev_simt[1]]);    // double-FP32 class
+        cudaEventElapsedTime(&mc[2], h->ev[ev_simt[1]], h->ev[ev_simt[2]]);    // FP32 class (and copies)
+        cudaEventElapsedTime(&m42, h->ev[ev_simt[2]], h->ev[2]);               // tensor-core launch
+        cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);                        // compaction
+        for (int c = 0; c < kSimt; ++c) t_simt[c] += mc[c];
+        t_tc += m42; t_cmp += m23;
     }
     ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (double)nupper * 8.0) * (double)bb;
     out.total = kept;
@@ -711,11 +722,12 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     sync(h);
     float mall = 0;
     cudaEventElapsedTime(&mall, h->ev[0], h->ev[3]);
-    ss.ms[1] = t_tc;                                         // tensor-core products
-    ss.ms[2] = simt_ar == AR_FP64 ? t_simt1 : 0.f;           // FP64 products
-    ss.ms[3] = (simt_ar == AR_FP64 ? 0.f : t_simt1) + t_simt2;  // FP32 products (and copies)
+    ss.ms[1] = t_tc;          // tensor-core products
+    ss.ms[2] = t_simt[0];     // FP64 products
+    ss.ms[3] = t_simt[2];     // FP32 products (and copies of converged systems)
     ss.ms[4] = t_cmp;
-    ss.ms[0] = std::max(0.f, mall - (t_simt1 + t_simt2 + t_tc + t_cmp));  // mask, lists, plans
+    ss.ms[5] = t_simt[1];     // double-FP32 products
+    ss.ms[0] = std::max(0.f, mall - (t_simt[0] + t_simt[1] + t_simt[2] + t_tc + t_cmp));  // mask, lists, plans
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -790,8 +802,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     JobTable jt = solve_jobs(nd);
     std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
     std::vector<int> act(S);
-    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0;
-    double kms[5] = {0, 0, 0, 0, 0};
+    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0, flops_ff = 0;
+    double kms[6] = {0, 0, 0, 0, 0, 0};
     int tc_launches = 0, simt_launches = 0, max_groups = 1;
     g_dev_bytes_peak = g_dev_bytes.load();
     cudaEvent_t ev0, ev1;
@@ -929,12 +941,13 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         flops_tc += (double)sst.pairs_tc * fpb;
         flops_64 += (double)sst.pairs_64 * fpb;
         flops_32 += (double)sst.pairs_32 * fpb;
-        issued += sst.issued_tc + (double)(sst.pairs_64 + sst.pairs_32) * fpb;
+        flops_ff += (double)sst.pairs_ff * fpb;
+        issued += sst.issued_tc + (double)(sst.pairs_64 + sst.pairs_32 + sst.pairs_ff) * fpb;
         nbytes += sst.bytes;
         tc_launches += sst.tc_launches;
         simt_launches += sst.simt_launches;
         max_groups = std::max(max_groups, sst.groups);
-        for (int k = 0; k < 5; ++k) kms[k] += sst.ms[k];
+        for (int k = 0; k < 6; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
             if (act[s]) {
@@ -1006,10 +1019,12 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.useful_flops = useful;
         I.issued_flops = issued;
         for (int k = 0; k < 5; ++k) I.kernel_ms[k] = kms[k];
-        I.kernel_ms[5] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3] - kms[4]);
+        I.kernel_ms[6] = kms[5];
+        I.kernel_ms[5] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3] - kms[4] - kms[5]);
         I.kernel_flops[0] = flops_tc;
         I.kernel_flops[1] = flops_64;
         I.kernel_flops[2] = flops_32;
+        I.kernel_flops[3] = flops_ff;
         I.kernel_launches = g_kernel_launches - launches0;
         I.tc_launches = tc_launches;
         I.simt_launches = simt_launches;
@@ -1135,8 +1150,10 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
     if (!h) return RDM_EINVAL;
     if (!p) return fail(h, RDM_EINVAL, "null params");
     if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 3 ||
-        !(p->spin_factor > 0) || p->min_iter < 0)
-        return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3)");
+        !(p->spin_factor > 0) || p->min_iter < 0 || p->refine_x1 < 0 || p->refine_x1 > 4 ||
+        p->refine_x0 < 0 || p->refine_x0 > 4 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0)
+        return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
+                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0)");
     h->prm = *p;
     return RDM_OK;
 }

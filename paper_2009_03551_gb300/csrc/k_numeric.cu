@@ -15,6 +15,8 @@
 // kernel; the FP32 variant converts the FP64 master values on load.
 #include "rdm_internal.cuh"
 
+#include <type_traits>
+
 namespace rdm {
 namespace {
 
@@ -148,38 +150,52 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// FF = false: FP32 products.  FF = true: double-FP32 ("float-float")
+// products of the FP64 masters split as x = hi + lo (two FP32 planes): the
+// hi*hi products are accumulated without rounding loss by the error-free
+// transformations of Ogita, Rump and Oishi (2005) -- the exact product
+// p + e = hi_a hi_b from one multiply and one fused multiply-add, the exact
+// sum s + t = acc + p from six additions -- and the small cross terms hi*lo
+// and lo*hi are added in plain FP32 into the low word.  The result carries
+// about 46 bits, enough for FP64-class refinement of X0^2, on the FP32 pipe.
+template <bool FF>
 __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
-    __shared__ __align__(16) float sA[2][32 * kF32Ld];
-    __shared__ __align__(16) float sB[2][32 * kF32Ld];
-    __shared__ float sC[32 * 33];
+    constexpr int NP = FF ? 2 : 1;                 // operand planes (hi, lo)
+    __shared__ __align__(16) float sA[2][NP][32 * kF32Ld];
+    __shared__ __align__(16) float sB[2][NP][32 * kF32Ld];
+    using CT = typename std::conditional<FF, double, float>::type;
+    __shared__ CT sC[32 * 33];
     __shared__ float red[2];
     const int tid = threadIdx.x;
     const int r0 = tid >> 3, c0 = tid & 7;
+    const float *planes[2] = {a.in_f32, a.in_f32lo};
 
     for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
         const int s = a.work[w];
         const int i = a.slot_row[s];
         const int sys = a.sys_of_row[i];
         const int job = a.slot_job[s];
-        const float cl = (float)a.c_lin[sys], cq = (float)a.c_sq[sys];
         const double tau = a.job_tau_sel[job] ? a.tau1[sys] : a.tau0[sys];
         const int64_t p0 = a.pair_off[s], p1 = a.pair_off[s + 1];
         const int st = a.slot_t[s], sx = a.slot_x[s];
 
-        float acc[4][4];
+        float acc[4][4], accl[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+            for (int v = 0; v < 4; ++v) acc[u][v] = accl[u][v] = 0.f;
 
         auto issue = [&](int64_t q, int buf) {
-            const float *ga = a.in_f32 + (size_t)a.pair_a[q] * 1024;
-            const float *gb = a.in_f32 + (size_t)a.pair_b[q] * 1024;
 #pragma unroll
-            for (int c = tid; c < 256; c += 64) {
-                const int row = c >> 3, col4 = (c & 7) * 4;
-                cp_async16(&sA[buf][row * kF32Ld + col4], ga + row * 32 + col4);
-                cp_async16(&sB[buf][row * kF32Ld + col4], gb + row * 32 + col4);
+            for (int pl = 0; pl < NP; ++pl) {
+                const float *ga = planes[pl] + (size_t)a.pair_a[q] * 1024;
+                const float *gb = planes[pl] + (size_t)a.pair_b[q] * 1024;
+#pragma unroll
+                for (int c = tid; c < 256; c += 64) {
+                    const int row = c >> 3, col4 = (c & 7) * 4;
+                    cp_async16(&sA[buf][pl][row * kF32Ld + col4], ga + row * 32 + col4);
+                    cp_async16(&sB[buf][pl][row * kF32Ld + col4], gb + row * 32 + col4);
+                }
             }
             cp_async_commit();
         };
@@ -194,8 +210,8 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
                 cp_async_wait0();
             }
             __syncthreads();
-            const float *A_ = sA[buf];
-            const float *B_ = sB[buf];
+            const float *A_ = sA[buf][0];
+            const float *B_ = sB[buf][0];
 #pragma unroll
             for (int kk = 0; kk < 32; kk += 4) {
                 float4 av[4], bv[4];
@@ -203,43 +219,87 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
                 for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const float4 *>(&A_[(r0 + 8 * u) * kF32Ld + kk]);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) bv[v] = *reinterpret_cast<const float4 *>(&B_[(c0 + 8 * v) * kF32Ld + kk]);
+                if (!FF) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        float t = acc[u][v];
-                        t = fmaf(av[u].x, bv[v].x, t);
-                        t = fmaf(av[u].y, bv[v].y, t);
-                        t = fmaf(av[u].z, bv[v].z, t);
-                        t = fmaf(av[u].w, bv[v].w, t);
-                        acc[u][v] = t;
+                        for (int v = 0; v < 4; ++v) {
+                            float t = acc[u][v];
+                            t = fmaf(av[u].x, bv[v].x, t);
+                            t = fmaf(av[u].y, bv[v].y, t);
+                            t = fmaf(av[u].z, bv[v].z, t);
+                            t = fmaf(av[u].w, bv[v].w, t);
+                            acc[u][v] = t;
+                        }
+                } else {
+                    const float *Al = sA[buf][NP - 1];
+                    const float *Bl = sB[buf][NP - 1];
+                    float4 al[4], bl[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) al[u] = *reinterpret_cast<const float4 *>(&Al[(r0 + 8 * u) * kF32Ld + kk]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) bl[v] = *reinterpret_cast<const float4 *>(&Bl[(c0 + 8 * v) * kF32Ld + kk]);
+                    // k outermost: the 16 accumulator chains of the thread are
+                    // independent, so consecutive operations do not wait on each other
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float ah = k == 0 ? av[u].x : k == 1 ? av[u].y : k == 2 ? av[u].z : av[u].w;
+                            const float alo = k == 0 ? al[u].x : k == 1 ? al[u].y : k == 2 ? al[u].z : al[u].w;
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                const float bh = k == 0 ? bv[v].x : k == 1 ? bv[v].y : k == 2 ? bv[v].z : bv[v].w;
+                                const float blo = k == 0 ? bl[v].x : k == 1 ? bl[v].y : k == 2 ? bl[v].z : bl[v].w;
+                                const float sh = acc[u][v];
+                                const float p = __fmul_rn(ah, bh);
+                                const float e = fmaf(ah, bh, -p);                // p + e = ah bh exactly
+                                const float sn = __fadd_rn(sh, p);
+                                const float z = __fsub_rn(sn, sh);
+                                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(sn, z)), __fsub_rn(p, z));   // sn + t = sh + p
+                                acc[u][v] = sn;
+                                float sl = accl[u][v];
+                                sl = fmaf(ah, blo, sl);
+                                sl = fmaf(alo, bh, sl);
+                                accl[u][v] = __fadd_rn(sl, __fadd_rn(t, e));
+                            }
+                        }
                     }
+                }
             }
             __syncthreads();
         }
 
-        // epilogue: C = c_lin X + c_sq acc, symmetrised on the diagonal, norm, truncation
+        // epilogue: C = c_lin X + c_sq acc (FP64 for FF), symmetrised on the diagonal,
+        // norm, truncation
         const double *gx = sx >= 0 ? a.in_val + (size_t)sx * 1024 : nullptr;
         const bool diag = (st == s);
+        const double cl = a.c_lin[sys], cq = a.c_sq[sys];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int r = r0 + 8 * u, c = c0 + 8 * v;
-                float x = cq * acc[u][v];
-                if (gx) x = fmaf(cl, (float)gx[r * 32 + c], x);
-                sC[r * 33 + c] = x;
+                if (FF) {
+                    double x = cq * ((double)acc[u][v] + (double)accl[u][v]);
+                    if (gx) x = fma(cl, gx[r * 32 + c], x);
+                    sC[r * 33 + c] = (CT)x;
+                } else {
+                    float x = (float)cq * acc[u][v];
+                    if (gx) x = fmaf((float)cl, (float)gx[r * 32 + c], x);
+                    sC[r * 33 + c] = (CT)x;
+                }
             }
         __syncthreads();
         float ss = 0.f;
         if (diag) {
-            float sym[4][4];
+            CT sym[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const int r = r0 + 8 * u, c = c0 + 8 * v;
-                    sym[u][v] = 0.5f * (sC[r * 33 + c] + sC[c * 33 + r]);
+                    sym[u][v] = (CT)0.5 * (sC[r * 33 + c] + sC[c * 33 + r]);
                 }
             __syncthreads();
 #pragma unroll
@@ -252,7 +312,7 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float x = sC[(r0 + 8 * u) * 33 + c0 + 8 * v];
+                const float x = (float)sC[(r0 + 8 * u) * 33 + c0 + 8 * v];
                 ss = fmaf(x, x, ss);
             }
 #pragma unroll
@@ -270,10 +330,16 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
     }
 }
 
-__global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ f, int64_t n) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) f[e] = (float)v[e];
+// FP64 masters -> FP32 hi plane and (optionally) FP32 lo plane, x = hi + lo
+__global__ void k_split_f32(const double *__restrict__ v, float *__restrict__ hi, float *__restrict__ lo, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double x = v[e];
+    const float h = (float)x;
+    hi[e] = h;
+    if (lo) lo[e] = (float)(x - (double)h);
 }
+
 
 template <int B, class T>
 void launch_b(const NumArgs &a, cudaStream_t st) {
@@ -311,20 +377,24 @@ void dispatch(const NumArgs &a, cudaStream_t st) {
 
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st) {
     if (a.nwork == 0) return;
-    if (ar == AR_FP64) {
+    const int grid = a.nwork < 152 * 32 ? a.nwork : 152 * 32;
+    if (ar == AR_FF) {
+        if (a.b != 32 || !a.in_f32 || !a.in_f32lo) throw Error{-1, "double-FP32 products need 32 x 32 blocks"};
+        k_numeric_f32_b32<true><<<grid, 64, 0, st>>>(a);
+        RDM_LAUNCH_CHECK();
+    } else if (ar == AR_FP64) {
         dispatch<double>(a, st);
     } else if (a.b == 32 && a.in_f32) {
-        const int grid = a.nwork < 152 * 32 ? a.nwork : 152 * 32;
-        k_numeric_f32_b32<<<grid, 64, 0, st>>>(a);
+        k_numeric_f32_b32<false><<<grid, 64, 0, st>>>(a);
         RDM_LAUNCH_CHECK();
     } else {
         dispatch<float>(a, st);
     }
 }
 
-void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st) {
+void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st, float *f32lo) {
     if (n == 0) return;
-    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(val, f32, n);
+    k_split_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(val, f32, f32lo, n);
     RDM_LAUNCH_CHECK();
 }
 

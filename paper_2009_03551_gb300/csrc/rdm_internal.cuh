@@ -150,12 +150,13 @@ struct MatSet {
     DevBuf<float> nrm;        // total
     DevBuf<uint16_t> ophi;    // operand copies for the tensor-core tiers
     DevBuf<uint16_t> oplo;
-    DevBuf<float> opf32;      // FP32 operand copy for the CUDA-core FP32 products
+    DevBuf<float> opf32;      // FP32 operand copy for the CUDA-core FP32 products (hi word)
+    DevBuf<float> opf32lo;    // lo word (x - hi) for the double-FP32 products
     std::vector<int64_t> nnzb;   // host copy, per matrix
     int64_t total = 0;
     void release() {
         row_ptr.release(); col.release(); val.release(); nrm.release();
-        ophi.release(); oplo.release(); opf32.release();
+        ophi.release(); oplo.release(); opf32.release(); opf32lo.release();
         nnzb.clear(); total = 0;
     }
 };
@@ -177,7 +178,8 @@ struct JobTable {
 };
 
 // Operand arithmetic of a numeric launch
-enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_TF32 = 4 };
+// (AR_FF: double-FP32 products on the FP32 pipe, about 46 bits)
+enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_TF32 = 4, AR_FF = 5 };
 
 // Jobs selected per precision tier: bit p of m[t] selects job p for the rows
 // of systems currently in tier t (systems of a batch move through the tiers
@@ -254,6 +256,7 @@ void launch_pairs(const MatSet &in, const JobTable &jt, const SysDev &sd, const 
 struct NumArgs {
     const double *in_val;
     const float *in_f32;       // FP32 copy of in_val (FP32 products), may be null
+    const float *in_f32lo;     // in_val - in_f32 rounded to FP32 (double-FP32 products), may be null
     const float *in_nrm;
     const uint16_t *in_hi, *in_lo;
     const int *pair_a, *pair_b;
@@ -278,14 +281,16 @@ struct NumArgs {
 };
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st);
 // FP32 copy of the FP64 master values (for the FP32 products)
-void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st);
+// FP32 copy (and, with f32lo, the FP32 remainder) of FP64 values
+void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st, float *f32lo = nullptr);
 
 // k_compact.cu
 // block triples of the upper slots of active systems per kernel class:
-// out[0] tensor cores (tc), out[1] FP64 (m64), out[2] FP32 (m32)
+// out[0] tensor cores (tc), out[1] FP64 (m64), out[2] FP32 (m32), out[3] double-FP32 (mff)
 void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot_npair, const int *slot_job,
                         int64_t nslot, const int *sys_of_row, const int *active, const int *sys_tier,
-                        JobMask tc, JobMask m64, JobMask m32, unsigned long long *out, cudaStream_t st);
+                        JobMask tc, JobMask m64, JobMask m32, JobMask mff, unsigned long long *out,
+                        cudaStream_t st);
 // upper slots of the active systems' jobs selected by job_mask (per system
 // tier), plus (with_inactive) all upper slots of converged systems
 // (slots [s0, s1) only)

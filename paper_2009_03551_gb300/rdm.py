@@ -70,7 +70,7 @@ class rdm_info(C.Structure):
                 ("idempotency", C.c_double), ("band_energy0", C.c_double),
                 ("nnzb_p0", C.c_int64), ("nnzb_p1", C.c_int64 * 3), ("time_ms", C.c_double),
                 ("useful_flops", C.c_double), ("issued_flops", C.c_double),
-                ("kernel_ms", C.c_double * 6), ("kernel_flops", C.c_double * 3),
+                ("kernel_ms", C.c_double * 7), ("kernel_flops", C.c_double * 4),
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("pad0", C.c_int32)]

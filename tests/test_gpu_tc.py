@@ -164,6 +164,28 @@ def test_final_tier_first_order_arithmetic(rdm, cluster150, oracle150, refine, t
     assert abs(info.idempotency) < 1e-8
 
 
+def test_final_tier_double_fp32_purification(rdm, cluster150):
+    """refine_x0 = double-FP32 (error-free transformations on the FP32 pipe):
+    the refined X0 is FP64-class, so P0, P1 and alpha agree with the FP64
+    refinement far below the split tier's own error, and P0 is idempotent to
+    the same floor."""
+    s = cluster150
+    out = {}
+    for r0 in (1, 4):
+        sol = rdm.Solver(0)
+        sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x0=r0)
+        sol.load(s)
+        code, info = sol.solve()
+        assert code == rdm.RDM_OK and info.converged
+        out[r0] = (sol.alpha(), sol.p0().to_dense(), info)
+    (a64, p64, i64), (aff, pff, iff) = out[1], out[4]
+    assert iff.kernel_flops[3] > 0 and iff.kernel_flops[1] == 0.0
+    assert iff.iterations == i64.iterations
+    assert rel_frobenius(pff, p64) <= 1e-9
+    assert np.max(np.abs(aff - a64)) / np.max(np.abs(a64)) <= 1e-9
+    assert abs(iff.idempotency) < 1e-8
+
+
 def test_final_tier_fp32_purification(rdm, cluster150, oracle150):
     """refine_x0 = FP32: the whole final tier on the FP32 CUDA cores.  It ends
     on the idempotency stall (FP32 floor) instead of the FP64 one; alpha stays
