@@ -69,7 +69,8 @@ extern "C" {
 #define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
                                     by a power of two into fp16's normal range
                                     (22-bit products instead of 16-bit); final tier:
-                                    X0^2 in FP64, first-order products in FP32 */
+                                    X0^2 in double-FP32 (FP64-class), first-order
+                                    products in FP32 */
 
 /* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
 #define RDM_REFINE_DEFAULT   0   /* FP32 for RDM_MODE_MIXED_FP16, FP64 for RDM_MODE_MIXED_BF16 */
@@ -126,9 +127,11 @@ typedef struct {
                                then multiplied in groups of consecutive jobs that fit it (at
                                least one job per group).  0: automatic, from the free device
                                memory.  Results do not depend on the grouping. */
-    int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT or
-                               RDM_REFINE_FP64 (FP64), RDM_REFINE_FP32 (FP32 on the CUDA cores; the
-                               final tier then ends on the idempotency stall) */
+    int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT
+                               (RDM_REFINE_FP32X2 for RDM_MODE_MIXED_FP16, RDM_REFINE_FP64 for
+                               RDM_MODE_MIXED_BF16), RDM_REFINE_FP64, RDM_REFINE_FP32X2, or
+                               RDM_REFINE_FP32 (the final tier then ends on the FP32 idempotency
+                               stall) */
     int32_t reserved[1];
 } rdm_params;
 

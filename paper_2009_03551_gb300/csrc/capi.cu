@@ -379,15 +379,18 @@ bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
 
 // Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
 // Mixed modes: tier 0 runs every product as a split product on the tensor
-// cores.  In the final tier the purification X0^2 is refined in FP64 on the
-// CUDA cores (`refine_x0` = RDM_REFINE_FP32 moves it to FP32); the
-// first-order products use `refine_x1` (RDM_REFINE_*): the default is FP32 on
-// the CUDA cores for the fp16 mode and FP64 for the bf16 mode.  (Split
-// products in the final tier leave ~1e-6 of the tensor cores' accumulation
-// error in alpha; FP32 with round-to-nearest accumulation does not.)
+// cores.  In the final tier the purification X0^2 is refined on the CUDA
+// cores (`refine_x0`): by default in double-FP32 (FP64-class, ~46 bits, on
+// the FP32 pipe) for the fp16 mode and in FP64 for the bf16 mode; the
+// first-order products use `refine_x1`: by default FP32 on the CUDA cores for
+// the fp16 mode and FP64 for the bf16 mode.  (Split products in the final
+// tier leave ~1e-6 of the tensor cores' accumulation error in alpha; FP32
+// with round-to-nearest accumulation does not.)
 void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0) {
     if (refine_x1 == RDM_REFINE_DEFAULT)
         refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32 : RDM_REFINE_FP64;
+    if (refine_x0 == RDM_REFINE_DEFAULT)
+        refine_x0 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32X2 : RDM_REFINE_FP64;
     for (int p = 0; p < njob; ++p) {
         Arith split = mode == RDM_MODE_MIXED_BF16 ? AR_BF16X3 : AR_FP16X3;
         switch (mode) {

@@ -212,7 +212,10 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
             __syncthreads();
             const float *A_ = sA[buf][0];
             const float *B_ = sB[buf][0];
-#pragma unroll
+            // the double-FP32 body is large: not unrolled over kk, so that the
+            // loop stays in the instruction cache
+            constexpr int kUnrollKK = FF ? 1 : 8;
+#pragma unroll kUnrollKK
             for (int kk = 0; kk < 32; kk += 4) {
                 float4 av[4], bv[4];
 #pragma unroll

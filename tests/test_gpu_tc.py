@@ -148,7 +148,7 @@ def test_mixed_solve_vs_oracle(rdm, cluster150, oracle150, mode):
 
 @pytest.mark.parametrize("refine,tol", [(1, 1e-6), (3, 1e-6), (2, 5e-6)])
 def test_final_tier_first_order_arithmetic(rdm, cluster150, oracle150, refine, tol):
-    """Final tier of the fp16 ladder: X0^2 in FP64, X1 products in FP64 (1),
+    """Final tier of the fp16 ladder (X0^2 refined in double-FP32): X1 products in FP64 (1),
     FP32 on the CUDA cores (3), or kept on the tensor cores (2).  The last
     keeps the tensor cores' FP32 accumulation error (a few 1e-6 in alpha)."""
     s = cluster150
