@@ -82,6 +82,7 @@ struct rdm_handle {
     DevBuf<int64_t> pair_off, scan_tmp64;
     DevBuf<int> scan_tmp32, pair_a, pair_b, cnt_rows;
     DevBuf<int> uidx, scan_tmp_s, urp, dest, cpsrc;   // upper-slot ranks, compaction maps
+    DevBuf<int> work_ctr;                             // work-item counters of the CUDA-core launches
     DevBuf<double> out_val, row_part, sys_q;
     DevBuf<float> out_nrm;
     DevBuf<uint8_t> keep;
@@ -657,6 +658,8 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         for (int p = 0; p < njob; ++p) a.job_tau_sel[p] = jt.job[p].tau_sel;
         a.out_val = h->out_val.p; a.out_nrm = h->out_nrm.p; a.keep = h->keep.p;
         a.uidx = h->uidx.p; a.u0 = u0; a.b = b;
+        h->work_ctr.ensure(kSimt);
+        RDM_CUDA_TRY(cudaMemsetAsync(h->work_ctr.p, 0, kSimt * sizeof(int), st));
         RDM_CUDA_TRY(cudaEventRecord(h->ev[1], st));
         const long long lg = g_kernel_launches;
         for (int c = 0; c < kSimt; ++c) {
@@ -664,6 +667,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
                 NumArgs ac = a;
                 ac.work = worklist[c]->p;
                 ac.nwork = nwork[c];
+                ac.work_next = h->work_ctr.p + c;
                 launch_numeric_simt(ac, simt_ar[c], st);
             }
             RDM_CUDA_TRY(cudaEventRecord(h->ev[ev_simt[c]], st));

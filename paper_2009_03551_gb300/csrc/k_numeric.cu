@@ -15,6 +15,7 @@
 // kernel; the FP32 variant converts the FP64 master values on load.
 #include "rdm_internal.cuh"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace rdm {
@@ -50,7 +51,15 @@ __global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
     __shared__ double red[32];
     const int tid = threadIdx.x;
 
-    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+    __shared__ int s_w;
+    for (;;) {
+        // work items are handed out in list order by an atomic counter, so the
+        // blocks in flight stay close in the list and share operands in L2
+        if (threadIdx.x == 0) s_w = atomicAdd(a.work_next, 1);
+        __syncthreads();
+        const int w = s_w;
+        __syncthreads();
+        if (w >= a.nwork) break;
         const int s = a.work[w];
         const int i = a.slot_row[s];
         const int sys = a.sys_of_row[i];
@@ -170,7 +179,15 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
     const int r0 = tid >> 3, c0 = tid & 7;
     const float *planes[2] = {a.in_f32, a.in_f32lo};
 
-    for (int w = blockIdx.x; w < a.nwork; w += gridDim.x) {
+    __shared__ int s_w;
+    for (;;) {
+        // work items are handed out in list order by an atomic counter, so the
+        // blocks in flight stay close in the list and share operands in L2
+        if (threadIdx.x == 0) s_w = atomicAdd(a.work_next, 1);
+        __syncthreads();
+        const int w = s_w;
+        __syncthreads();
+        if (w >= a.nwork) break;
         const int s = a.work[w];
         const int i = a.slot_row[s];
         const int sys = a.sys_of_row[i];
@@ -356,7 +373,15 @@ void launch_b(const NumArgs &a, cudaStream_t st) {
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    int grid = a.nwork < 152 * 16 ? a.nwork : 152 * 16;
+    static int resident = 0;
+    if (!resident) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        RDM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_numeric_simt<B, T>, NT, smem));
+        RDM_CUDA_TRY(cudaGetDevice(&dev));
+        RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        resident = std::max(1, per_sm) * nsm;
+    }
+    const int grid = a.nwork < resident ? a.nwork : resident;
     if (grid <= 0) return;
     k_numeric_simt<B, T><<<grid, NT, smem, st>>>(a);
     RDM_LAUNCH_CHECK();
@@ -376,19 +401,30 @@ void dispatch(const NumArgs &a, cudaStream_t st) {
     }
 }
 
+// blocks of kernel k (threads per block nt, static shared memory) resident on the whole GPU
+template <class K>
+int resident_blocks(K k, int nt) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    RDM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0));
+    RDM_CUDA_TRY(cudaGetDevice(&dev));
+    RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(1, per_sm) * nsm;
+}
+
 }  // namespace
 
 void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st) {
     if (a.nwork == 0) return;
-    const int grid = a.nwork < 152 * 32 ? a.nwork : 152 * 32;
     if (ar == AR_FF) {
         if (a.b != 32 || !a.in_f32 || !a.in_f32lo) throw Error{-1, "double-FP32 products need 32 x 32 blocks"};
-        k_numeric_f32_b32<true><<<grid, 64, 0, st>>>(a);
+        static const int res = resident_blocks(k_numeric_f32_b32<true>, 64);
+        k_numeric_f32_b32<true><<<std::min(a.nwork, res), 64, 0, st>>>(a);
         RDM_LAUNCH_CHECK();
     } else if (ar == AR_FP64) {
         dispatch<double>(a, st);
     } else if (a.b == 32 && a.in_f32) {
-        k_numeric_f32_b32<false><<<grid, 64, 0, st>>>(a);
+        static const int res = resident_blocks(k_numeric_f32_b32<false>, 64);
+        k_numeric_f32_b32<false><<<std::min(a.nwork, res), 64, 0, st>>>(a);
         RDM_LAUNCH_CHECK();
     } else {
         dispatch<float>(a, st);

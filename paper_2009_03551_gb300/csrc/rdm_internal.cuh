@@ -263,6 +263,7 @@ struct NumArgs {
     const int64_t *pair_off;
     const int *slot_row, *slot_job, *slot_x, *slot_t;
     const int *work;        // upper slots to process
+    int *work_next;         // zeroed counter: next work item to hand out
     int nwork;
     const int *sys_of_row;
     const double *c_lin, *c_sq, *tau0, *tau1;
