@@ -460,13 +460,12 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         other.release();
     };
     take(in.ophi, out.ophi);
-    take(in.oplo, out.oplo);
     take(in.opf32, out.opf32);
     take(in.opf32lo, out.opf32lo);
     // copies the step does not use are kept for the next solve, unless they
     // are large (above 4 GiB the solve's time dwarfs a re-allocation)
     const size_t big = size_t(4) << 30;
-    if (!tc && in.ophi.cap * sizeof(uint16_t) > big) { in.ophi.release(); in.oplo.release(); }
+    if (!tc && in.ophi.cap * sizeof(uint16_t) > big) in.ophi.release();
     if (!f32_planes && in.opf32.cap * sizeof(float) > big) in.opf32.release();
     if (!any_c[1] && in.opf32lo.cap * sizeof(float) > big) in.opf32lo.release();
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
@@ -647,7 +646,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         sync(h);
 
         NumArgs a{};
-        a.in_val = in.val.p; a.in_nrm = in.nrm.p; a.in_hi = in.ophi.p; a.in_lo = in.oplo.p;
+        a.in_val = in.val.p; a.in_nrm = in.nrm.p;
         a.in_f32 = f32_planes ? in.opf32.p : nullptr;
         a.in_f32lo = any_c[1] ? in.opf32lo.p : nullptr;
         a.pair_a = h->pair_a.p; a.pair_b = h->pair_b.p; a.pair_off = h->pair_off.p;

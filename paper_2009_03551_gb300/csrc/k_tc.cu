@@ -15,8 +15,11 @@
 // hi*hi + hi*lo + lo*hi (2 MMAs of K = 16 each), all accumulated in FP32 in
 // tensor memory.  The operand planes are laid out in global memory in the
 // canonical K-major core-matrix order of the MMA (8 rows x 16 bytes per core
-// matrix, core matrices adjacent along K 128 bytes apart, 8-row groups 512
-// bytes apart), so one 2 KB bulk copy per block lands ready for the MMA.
+// matrix, core matrices adjacent along K 128 bytes apart), with the 8-row
+// groups of a block's hi and lo planes alternating (512 bytes each, 1 KB
+// between the groups of one plane): one 4 KB bulk copy per block lands both
+// planes ready for the MMA.  The producer warp issues about one bulk copy
+// per 60 cycles, which bounds the kernel; interleaving halved the copies.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over a static tile
 // schedule): warp 0 issues the bulk copies into a 6-stage ring, warp 1 owns
@@ -51,8 +54,9 @@ constexpr int TBL = 4;                       // blocks per tile edge
 constexpr int kStages = 6;
 constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
 constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
-constexpr int kTilePlaneBytes = TBL * kPlaneBytes;      // 8 KB: 4 blocks stacked
-constexpr int kStageBytes = 4 * kTilePlaneBytes;        // A_hi, A_lo, B_hi, B_lo
+constexpr int kPairBytes = 2 * kPlaneBytes;  // hi and lo planes of one block, interleaved: 4 KB
+constexpr int kSideBytes = TBL * kPairBytes; // 16 KB: 4 blocks stacked
+constexpr int kStageBytes = 2 * kSideBytes;  // A side, B side
 constexpr int kEpiWarps = 8;                 // epilogue warps: 2 per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileInts = 24;
@@ -147,10 +151,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ---------------------------------------------------------------------------
 // operand planes: hi/lo split in the K-major core-matrix layout
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int core_offset(int r, int c) {
-    // element (r, c) of a 32 x 32 block: core matrix (r/8, c/8) at 64-element
-    // granularity, 4 core matrices per 8-row group
-    return (((r >> 3) * 4 + (c >> 3)) << 6) + ((r & 7) << 3) + (c & 7);
+__device__ __forceinline__ int pair_offset(int r, int c, int plane) {
+    // element (r, c) of plane `plane` (0 hi, 1 lo) of a 32 x 32 block: the two
+    // planes' 8-row groups alternate (512 bytes each), so that one 4 KB copy
+    // brings both and both are K-major core-matrix operands with a 1 KB stride
+    // between 8-row groups; inside a group, core matrix (c/8) at 64 elements
+    return ((r >> 3) << 9) + (plane << 8) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7);
 }
 
 // per matrix m: scale[m] = 2^floor(log2(2^14 / max block norm)) for fp16 (the
@@ -181,7 +187,7 @@ __global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__rest
 
 template <bool BF16>
 __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
-                               uint16_t *__restrict__ lo, const float *__restrict__ scale,
+                               const float *__restrict__ scale,
                                const int *__restrict__ mat_first, int nmat) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n = nblk * kPlaneElems;
@@ -203,9 +209,9 @@ __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uin
         h = __half_as_ushort(hh);
         l = __half_as_ushort(hl);
     }
-    int64_t o = p * kPlaneElems + core_offset(rc >> 5, rc & 31);
-    hi[o] = h;
-    lo[o] = l;
+    const int64_t o = p * (2 * kPlaneElems);
+    hi[o + pair_offset(rc >> 5, rc & 31, 0)] = h;
+    hi[o + pair_offset(rc >> 5, rc & 31, 1)] = l;
 }
 
 // ---------------------------------------------------------------------------
@@ -343,8 +349,8 @@ __global__ void k_set_nsteps(int *tiles, const int *step_cnt, int ntile) {
 // the tensor-core product kernel
 // ---------------------------------------------------------------------------
 struct TcArgs {
-    const uint16_t *hi, *lo;      // operand planes of the input set
-    const uint16_t *zero;         // one zero plane
+    const uint16_t *planes;       // operand planes of the input set (hi and lo interleaved, 4 KB per block)
+    const uint16_t *zero;         // zero blocks (8 per CTA)
     const int *tiles;
     const int64_t *step_off;
     const int *steps;
@@ -432,27 +438,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 for (int k = 0; k < kStages; ++k)
                     if (k == st) zprev = zmask[k];
                 const bool skip = (b < 0) && ((zprev >> slot) & 1u);
-                const uint32_t need = __ballot_sync(0xffffffffu, lane < 16 && !skip);
+                const uint32_t need = __ballot_sync(0xffffffffu, lane < 8 && !skip);
                 int waited = 1;
                 if (lane == 0) {
                     waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag) ? 1 : 0;
-                    if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * kPlaneBytes);
+                    if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * kPairBytes);
                 }
                 waited = __shfl_sync(0xffffffffu, waited, 0);
                 if (!waited) { ok = false; break; }
 #pragma unroll
                 for (int k = 0; k < kStages; ++k)
                     if (k == st) zmask[k] = zbits;
-                if (lane < 16 && !skip) {
+                if (lane < 8 && !skip) {
                     uint8_t *dst = stages + st * kStageBytes;
-                    const int side = slot >> 2, r = slot & 3, plane = lane >> 3;   // plane 0 hi, 1 lo
-                    // zero planes: one per CTA and slot, so that the CTAs do not all
+                    const int side = slot >> 2, r = slot & 3;
+                    // zero blocks: one per CTA and slot, so that the CTAs do not all
                     // read the same few L2 sectors
-                    const uint16_t *src = b >= 0 ? (plane ? A.lo : A.hi) + (size_t)b * kPlaneElems
-                                                 : A.zero + ((size_t)blockIdx.x * 16 + lane) * kPlaneElems;
-                    // A: [0, 8K) hi, [8K, 16K) lo; B: [16K, 24K) hi, [24K, 32K) lo
-                    bulk_g2s(dst + side * 2 * kTilePlaneBytes + plane * kTilePlaneBytes + r * kPlaneBytes, src,
-                             kPlaneBytes, &ctl->full[st]);
+                    const uint16_t *src = b >= 0 ? A.planes + (size_t)b * (2 * kPlaneElems)
+                                                 : A.zero + ((size_t)blockIdx.x * 8 + lane) * (2 * kPlaneElems);
+                    // A side [0, 16K), B side [16K, 32K); block r of a side at r * 4K
+                    bulk_g2s(dst + side * kSideBytes + r * kPairBytes, src, kPairBytes, &ctl->full[st]);
                 }
             }
         }
@@ -479,15 +484,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                         if (!mbar_wait(&ctl->full[st], ph, abort_flag)) { ok = false; break; }
                         fence_after();
                         const uint32_t base = smem_u32(stages + st * kStageBytes);
-                        const uint32_t a_hi = base, a_lo = base + kTilePlaneBytes;
-                        const uint32_t b_hi = base + 2 * kTilePlaneBytes, b_lo = base + 3 * kTilePlaneBytes;
+                        const uint32_t a_hi = base, a_lo = base + 512;
+                        const uint32_t b_hi = base + kSideBytes, b_lo = base + kSideBytes + 512;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint32_t ko = kk * 256;
                             const uint32_t first = (q == qs && kk == 0) ? 0u : 1u;
-                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, first);
-                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 512), smem_desc(b_lo + ko, 128, 512), A.idesc, 1u);
-                            mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 512), smem_desc(b_hi + ko, 128, 512), A.idesc, 1u);
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 1024), smem_desc(b_hi + ko, 128, 1024), A.idesc, first);
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 1024), smem_desc(b_lo + ko, 128, 1024), A.idesc, 1u);
+                            mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 1024), smem_desc(b_hi + ko, 128, 1024), A.idesc, 1u);
                         }
                         issued = true;
                         mma_commit(&ctl->empty[st]);
@@ -647,15 +652,14 @@ void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
     k_matrix_scales<<<nmat, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
     RDM_LAUNCH_CHECK();
     const int64_t n = in.total * kPlaneElems;
-    in.ophi.ensure(std::max<int64_t>(n, 1));
-    in.oplo.ensure(std::max<int64_t>(n, 1));
+    in.ophi.ensure(std::max<int64_t>(2 * n, 1));   // hi and lo, interleaved per block
     if (n == 0) return;
     const int64_t grid = (n + 255) / 256;
     if (ar == AR_BF16X3)
-        k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p, w.scale.p,
+        k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
                                                              w.mat_first.p, nmat);
     else
-        k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, in.oplo.p, w.scale.p,
+        k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
                                                               w.mat_first.p, nmat);
     RDM_LAUNCH_CHECK();
 }
@@ -667,13 +671,13 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     int dev = 0, nsm = 0;
     RDM_CUDA_TRY(cudaGetDevice(&dev));
     RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t zero_elems = (size_t)nsm * 16 * kPlaneElems;   // 16 zero planes per CTA
+    const size_t zero_elems = (size_t)nsm * 8 * 2 * kPlaneElems;   // 8 zero blocks (hi and lo) per CTA
     if (!w.zero.p || w.zero.cap < zero_elems) {
         w.zero.ensure(zero_elems);
         RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, w.zero.cap * sizeof(uint16_t), st));
     }
     TcArgs A{};
-    A.hi = in.ophi.p; A.lo = in.oplo.p; A.zero = w.zero.p;
+    A.planes = in.ophi.p; A.zero = w.zero.p;
     A.tiles = w.tiles.p; A.step_off = w.step_off.p; A.steps = w.steps.p; A.ntile = plan.ntile;
     // kind::f16: D = F32 (bit 4), A/B = BF16 (1) or F16 (0), K-major, N = 128, M = 128
     const uint32_t ab = ar == AR_BF16X3 ? 1u : 0u;

@@ -148,15 +148,14 @@ struct MatSet {
     DevBuf<int> col;          // total blocks
     DevBuf<double> val;       // total*b*b
     DevBuf<float> nrm;        // total
-    DevBuf<uint16_t> ophi;    // operand copies for the tensor-core tiers
-    DevBuf<uint16_t> oplo;
+    DevBuf<uint16_t> ophi;    // tensor-core operand planes (hi and lo interleaved, 4 KB per block)
     DevBuf<float> opf32;      // FP32 operand copy for the CUDA-core FP32 products (hi word)
     DevBuf<float> opf32lo;    // lo word (x - hi) for the double-FP32 products
     std::vector<int64_t> nnzb;   // host copy, per matrix
     int64_t total = 0;
     void release() {
         row_ptr.release(); col.release(); val.release(); nrm.release();
-        ophi.release(); oplo.release(); opf32.release(); opf32lo.release();
+        ophi.release(); opf32.release(); opf32lo.release();
         nnzb.clear(); total = 0;
     }
 };
@@ -258,7 +257,6 @@ struct NumArgs {
     const float *in_f32;       // FP32 copy of in_val (FP32 products), may be null
     const float *in_f32lo;     // in_val - in_f32 rounded to FP32 (double-FP32 products), may be null
     const float *in_nrm;
-    const uint16_t *in_hi, *in_lo;
     const int *pair_a, *pair_b;
     const int64_t *pair_off;
     const int *slot_row, *slot_job, *slot_x, *slot_t;
