@@ -69,11 +69,12 @@ extern "C" {
 #define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
                                     by a power of two into fp16's normal range
                                     (22-bit products instead of 16-bit); final tier:
-                                    X0^2 in double-FP32 (FP64-class), first-order
-                                    products in FP32 */
+                                    X0^2 in double-FP32 (FP64-class) on the CUDA
+                                    cores, first-order products still split */
 
 /* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
-#define RDM_REFINE_DEFAULT   0   /* FP32 for RDM_MODE_MIXED_FP16, FP64 for RDM_MODE_MIXED_BF16 */
+#define RDM_REFINE_DEFAULT   0   /* refine_x1: the split product for RDM_MODE_MIXED_FP16, FP64 for
+                                    RDM_MODE_MIXED_BF16; refine_x0: see rdm_params */
 #define RDM_REFINE_FP64      1
 #define RDM_REFINE_SPLIT     2   /* keep the tensor-core split product */
 #define RDM_REFINE_FP32      3   /* FP32 on the CUDA cores (round-to-nearest accumulation) */

@@ -383,13 +383,13 @@ bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
 // cores.  In the final tier the purification X0^2 is refined on the CUDA
 // cores (`refine_x0`): by default in double-FP32 (FP64-class, ~46 bits, on
 // the FP32 pipe) for the fp16 mode and in FP64 for the bf16 mode; the
-// first-order products use `refine_x1`: by default FP32 on the CUDA cores for
-// the fp16 mode and FP64 for the bf16 mode.  (Split products in the final
-// tier leave ~1e-6 of the tensor cores' accumulation error in alpha; FP32
-// with round-to-nearest accumulation does not.)
+// first-order products use `refine_x1`: by default they stay split products
+// on the tensor cores for the fp16 mode (with the segmented accumulation of
+// the tensor-core kernel they are as accurate as FP32 CUDA-core products
+// there) and FP64 for the bf16 mode.
 void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0) {
     if (refine_x1 == RDM_REFINE_DEFAULT)
-        refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32 : RDM_REFINE_FP64;
+        refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_SPLIT : RDM_REFINE_FP64;
     if (refine_x0 == RDM_REFINE_DEFAULT)
         refine_x0 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32X2 : RDM_REFINE_FP64;
     for (int p = 0; p < njob; ++p) {
