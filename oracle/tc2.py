@@ -26,7 +26,12 @@ order:
 Readings of the paper used here: a tie Tr X0 = N_occ takes the square branch
 (the ">=" of Eq. TC2); X1_0 uses the Gershgorin bounds of X0_0 so that X1_n is
 exactly the derivative of X0_n; truncation follows each update and never
-touches H0, H1 or the initial matrices.
+touches H0, H1 or the initial matrices.  The paper does not say what TC2 does
+when the filter pushes eigenvalues out of [0, 1] (idempotency error below
+zero): with the trace test alone the iteration then diverges for large
+thresholds (1e-5 and 1e-4 on the synthetic clusters); here the branch
+alternates with the previous one whenever e < -1e-10 N_occ, a level that
+rounding at tau = 0 never reaches.
 """
 
 from __future__ import annotations
@@ -115,6 +120,12 @@ def tc2_response(h0: np.ndarray, h1s: Sequence[np.ndarray], n_occ: int, b: int,
             branch = int(force_branches[it])
         else:
             branch = 1 if t >= n_occ else 2
+            # an idempotency error clearly below zero means eigenvalues outside
+            # [0, 1] (the filter moves them); the trace test alone would then
+            # square an eigenvalue above 1 again and again, so the branch
+            # alternates with the previous one and both edges contract
+            if it > 0 and idem < -1e-10 * max(1.0, float(n_occ)):
+                branch = 2 if res.branches[-1] == 1 else 1
         x0sq = x0 @ x0
         if branch == 1:
             x0n = x0sq

@@ -891,7 +891,11 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             // in the reduced-precision modes a negative idempotency error (spectrum
             // outside [0,1]) alternates the branch so that both edges contract
             int branch = (tr >= nocc[s]) ? 1 : 2;
-            if (lowprec && e < 0 && n > 0) branch = y.prev_branch == 1 ? 2 : 1;
+            // (FP64: only a clearly negative error, e < -1e-10 N_occ, as in the
+            // oracle; that level is out of reach of rounding but the filter at
+            // large thresholds reaches it, and the trace test alone then diverges)
+            if (n > 0 && (lowprec ? e < 0 : e < -1e-10 * std::max(1.0, nocc[s])))
+                branch = y.prev_branch == 1 ? 2 : 1;
             if (n < (int)h->forced.size()) branch = h->forced[n];
             y.prev_branch = branch;
             c_lin[s] = branch == 1 ? 0.0 : 2.0;

@@ -111,6 +111,22 @@ def test_cluster_fp64_free_run_matches_oracle_limit(rdm, cluster150, oracle150):
         assert rel_frobenius(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-8
 
 
+def test_fp64_large_threshold_stays_bounded(rdm, cluster150):
+    """tau = 1e-4: the filter pushes eigenvalues out of [0, 1]; the FP64 path
+    alternates the branch like the oracle (e < -1e-10 N_occ) and stays bounded
+    with alpha at the accuracy the threshold allows (the trace test alone
+    diverges here)."""
+    s = cluster150
+    h0, h1s = dense_list(s)
+    _, p1s, _, _ = exact_response(h0, h1s, s.n_occ)
+    ae = polarizability(p1s, h1s)
+    sol, code, info = gpu_solve(rdm, s, tau=1e-4, tol=0.0, mode="fp64", max_iter=40)
+    a = sol.alpha()
+    assert np.isfinite(a).all()
+    assert np.max(np.abs(a - ae)) / np.max(np.abs(ae)) < 1e-5
+    assert abs(info.trace_error) < 1e-3
+
+
 def test_hash_symbolic_phase_is_identical(rdm, cluster150):
     """The hash-table symbolic phase (used above 8,192 block rows) gives the same
     masks, pair counts and therefore bit-identical results as the dense one."""

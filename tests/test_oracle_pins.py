@@ -286,6 +286,27 @@ def test_tc2_truncation_error_shrinks_with_threshold():
     assert errs[2] < 1e-4
 
 
+def test_tc2_large_threshold_stays_bounded():
+    """At tau = 1e-4 the filter pushes eigenvalues of X0 out of [0, 1]; with the
+    trace test alone TC2 then diverges on this cluster (X0 overflows).  With
+    the branch alternating while Tr X - ||X||^2 < -1e-10 N_occ, X0 stays
+    bounded, P0 stays a projector to the filter's accuracy and alpha keeps the
+    accuracy the threshold allows."""
+    s = make_cluster(150, opa=8, b=32, cutoff=10.0, seed=11, dirs=("x", "y", "z"))
+    h0 = s.h0.to_dense()
+    h1s = [m.to_dense() for m in s.h1]
+    p0, p1s, _, _ = exact_response(h0, h1s, s.n_occ)
+    r = tc2_response(h0, h1s, s.n_occ, s.b, tau=1e-4, tol=0.0, max_iter=40)
+    assert np.isfinite(r.p0).all()
+    assert abs(np.trace(r.p0) - s.n_occ) < 1e-3
+    assert rel_frobenius(r.p0, p0) < 1e-3
+    ae = polarizability(p1s, h1s)
+    a = polarizability(r.p1s, h1s)
+    assert np.max(np.abs(a - ae)) / np.max(np.abs(ae)) < 1e-5
+    # the safeguard acted: some step took the other branch than the trace test
+    assert any(rec["idempotency"] < -1e-10 * s.n_occ for rec in r.log)
+
+
 def test_tc2_forced_branches_replay():
     s = chain_sys(12)
     h0 = s.h0.to_dense()
