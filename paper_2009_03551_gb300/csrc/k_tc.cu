@@ -236,40 +236,133 @@ struct TileBuild {
     int ntile;
 };
 
-// one thread per (job, super-row): the union of super-columns J of the upper
-// mask blocks in block rows 4I..4I+3 (count or fill)
-__global__ void k_tile_rows(TileBuild T, int fill) {
-    const int t = T.u0 + blockIdx.x * blockDim.x + threadIdx.x;
+// upper mask range [cur, end) of block row 4I + m of job p, empty for rows
+// whose system is converged or whose job is not computed on the tensor cores
+__device__ __forceinline__ void tile_row_range(const TileBuild &T, int p, int I, int m, int &cur, int &end) {
+    const int i = 4 * I + m;
+    cur = end = 0;
+    if (i >= T.NB) return;
+    int lo = T.out_rp[p * T.NB + i], hi = T.out_rp[p * T.NB + i + 1];
+    end = hi;
+    // first column >= i (upper triangle)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T.mcol[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    cur = lo;
+    // converged systems keep their blocks through the copy path of the
+    // numeric phase, and jobs on the CUDA cores have their own launch:
+    // neither produces tiles
+    const int sys = T.sys_of_row[i];
+    if (!T.active[sys] || !((T.job_mask.m[T.sys_tier[sys] & (kMaxTiers - 1)] >> p) & 1u)) cur = end;
+}
+
+// Tiles of one (job, super-row), warp-parallel: the upper mask columns of
+// block rows 4I..4I+3 are marked in a shared-memory bitmap over their column
+// window; the rank of a column among the distinct ones (prefix popcounts)
+// gives its tile (rank / 4) and tile column (rank % 4).  Windows wider than
+// the bitmap fall back to a serial 4-way merge by lane 0 (count or fill).
+constexpr int kTileRowWarps = 8, kTileRowWords = 512;   // 16,384 columns per window
+__device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
+                                 int fill);
+__global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, int fill) {
+    __shared__ unsigned bits_s[kTileRowWarps][kTileRowWords];
+    __shared__ int rank_s[kTileRowWarps][kTileRowWords];
+    const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = T.u0 + blockIdx.x * kTileRowWarps + wq;
     if (t >= T.u1) return;
     const int p = t / T.NB4, I = t % T.NB4;
+    unsigned *bm = bits_s[wq];
+    int *wr = rank_s[wq];
+    int c0 = 0, e0 = 0;
+    if (lane < TBL) tile_row_range(T, p, I, lane, c0, e0);
     int cur[TBL], end[TBL];
+    int lo = 0x7fffffff, hi = -1;
+#pragma unroll
     for (int m = 0; m < TBL; ++m) {
-        int i = 4 * I + m;
-        cur[m] = end[m] = 0;
-        if (i >= T.NB) continue;
-        int lo = T.out_rp[p * T.NB + i], hi = T.out_rp[p * T.NB + i + 1];
-        // first column >= i (upper triangle)
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (T.mcol[mid] < i) lo = mid + 1; else hi = mid;
+        cur[m] = __shfl_sync(0xffffffffu, c0, m);
+        end[m] = __shfl_sync(0xffffffffu, e0, m);
+        if (cur[m] < end[m]) {
+            lo = min(lo, T.mcol[cur[m]]);
+            hi = max(hi, T.mcol[end[m] - 1]);
         }
-        cur[m] = lo;
-        end[m] = T.out_rp[p * T.NB + i + 1];
-        // converged systems keep their blocks through the copy path of the
-        // numeric phase, and jobs on the CUDA cores have their own launch:
-        // neither produces tiles
-        const int sys = T.sys_of_row[i];
-        if (!T.active[sys] || !((T.job_mask.m[T.sys_tier[sys] & (kMaxTiers - 1)] >> p) & 1u)) cur[m] = end[m];
     }
+    const int base = fill ? T.tile_off[t - T.u0] : 0;
+    if (hi < lo) {                         // no tile
+        if (!fill && lane == 0) T.tile_cnt[t - T.u0] = 0;
+        return;
+    }
+    const int nw = ((hi - lo) >> 5) + 1;
+    if (nw > kTileRowWords) {
+        if (lane == 0) tile_rows_serial(T, t, p, I, cur, end, fill);
+        return;
+    }
+    for (int w = lane; w < nw; w += 32) bm[w] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < TBL; ++m)
+        for (int e = cur[m] + lane; e < end[m]; e += 32) {
+            const int j = T.mcol[e] - lo;
+            atomicOr(&bm[j >> 5], 1u << (j & 31));
+        }
+    __syncwarp();
+    // exclusive prefix of the words' popcounts
+    int carry = 0;
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        const int c = w < nw ? __popc(bm[w]) : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (w < nw) wr[w] = carry + x - c;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    __syncwarp();
+    const int ndist = carry, ntile = (ndist + 3) >> 2;
+    if (!fill) {
+        if (lane == 0) T.tile_cnt[t - T.u0] = ntile;
+        return;
+    }
+    for (int q = lane; q < ntile; q += 32) {
+        int *d = T.tiles + (size_t)(base + q) * kTileInts;
+        d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
+        for (int k = 0; k < 16; ++k) d[4 + k] = -1;
+        for (int k = 0; k < TBL; ++k) d[20 + k] = -1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < TBL; ++m)
+        for (int e = cur[m] + lane; e < end[m]; e += 32) {
+            const int jc = T.mcol[e];
+            const int j = jc - lo;
+            const int r = wr[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
+            int *d = T.tiles + (size_t)(base + (r >> 2)) * kTileInts;
+            d[4 + m * 4 + (r & 3)] = e;
+            d[20 + (r & 3)] = jc;
+        }
+}
+
+// the serial 4-way merge (same tile order as the bitmap path)
+__device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
+                                 int fill) {
+    int cur[TBL], end[TBL];
+    for (int m = 0; m < TBL; ++m) { cur[m] = cur0[m]; end[m] = end0[m]; }
     // the distinct columns needed by the 4 rows, in increasing order, are packed
     // 4 at a time into tiles: every tile column is needed by at least one row
     int ncol = 0, n = 0;
     const int base = fill ? T.tile_off[t - T.u0] : 0;
     int *d = nullptr;
+    // list heads kept in registers: one load per advance
+    int head[TBL];
+#pragma unroll
+    for (int m = 0; m < TBL; ++m) head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
     while (true) {
         int jmin = 0x7fffffff;
-        for (int m = 0; m < TBL; ++m)
-            if (cur[m] < end[m]) jmin = min(jmin, T.mcol[cur[m]]);
+#pragma unroll
+        for (int m = 0; m < TBL; ++m) jmin = min(jmin, head[m]);
         if (jmin == 0x7fffffff) break;
         const int c = ncol & 3;
         if (c == 0) {
@@ -282,10 +375,12 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
             ++n;
         }
         if (fill) d[20 + c] = jmin;
+#pragma unroll
         for (int m = 0; m < TBL; ++m)
-            if (cur[m] < end[m] && T.mcol[cur[m]] == jmin) {
+            if (head[m] == jmin) {
                 if (fill) d[4 + m * 4 + c] = cur[m];
                 ++cur[m];
+                head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
             }
         ++ncol;
     }
@@ -294,9 +389,7 @@ __global__ void k_tile_rows(TileBuild T, int fill) {
 
 // one thread per tile: K-steps = union over the tile's A rows intersected with
 // the union over its B rows, for each term (count or fill)
-__global__ void k_tile_steps(TileBuild T, int fill) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T.ntile) return;
+__device__ void tile_steps_serial(const TileBuild &T, int t, int fill) {
     const int *d = T.tiles + (size_t)t * kTileInts;
     const int p = d[0], I = d[1];
     const Job &job = T.jt.job[p];
@@ -312,18 +405,24 @@ __global__ void k_tile_steps(TileBuild T, int fill) {
             if (i < T.NB) { cur[q] = T.rp[am * T.NB + i]; end[q] = T.rp[am * T.NB + i + 1]; }
             if (j >= 0) { cur[TBL + q] = T.rp[bm * T.NB + j]; end[TBL + q] = T.rp[bm * T.NB + j + 1]; }
         }
+        // list heads kept in registers: one load per advance
+        int head[2 * TBL];
+#pragma unroll
+        for (int q = 0; q < 2 * TBL; ++q) head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
         while (true) {
             int kmin = 0x7fffffff;
-            for (int q = 0; q < 2 * TBL; ++q)
-                if (cur[q] < end[q]) kmin = min(kmin, T.col[cur[q]]);
+#pragma unroll
+            for (int q = 0; q < 2 * TBL; ++q) kmin = min(kmin, head[q]);
             if (kmin == 0x7fffffff) break;
             bool anyA = false, anyB = false;
             int idx[2 * TBL];
+#pragma unroll
             for (int q = 0; q < 2 * TBL; ++q) {
                 idx[q] = -1;
-                if (cur[q] < end[q] && T.col[cur[q]] == kmin) {
+                if (head[q] == kmin) {
                     idx[q] = cur[q];
                     ++cur[q];
+                    head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
                     if (q < TBL) anyA = true; else anyB = true;
                 }
             }
@@ -338,6 +437,117 @@ __global__ void k_tile_steps(TileBuild T, int fill) {
     }
     if (!fill) T.step_cnt[t] = n;
     else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
+}
+
+// K-steps of one tile, warp-parallel: per term, the columns k of the tile's 4
+// A rows and of its 4 B rows are marked in two shared-memory bitmaps over
+// the window where both can have columns; a K-step is a k marked in both, its
+// index the rank of k among those (prefix popcounts).  Each list entry at
+// such a k writes its block index into its slot of the step; the other
+// slots stay -1 (zero block).  Same steps, same order as the serial merge,
+// which lane 0 runs for windows wider than the bitmaps.
+constexpr int kStepWarps = 4, kStepWords = 512;    // 16,384 columns per window
+__global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int fill) {
+    __shared__ unsigned ba_s[kStepWarps][kStepWords], bb_s[kStepWarps][kStepWords];
+    __shared__ int rank_s[kStepWarps][kStepWords];
+    const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kStepWarps + wq;
+    if (t >= T.ntile) return;
+    unsigned *ba = ba_s[wq], *bb = bb_s[wq];
+    int *wr = rank_s[wq];
+    const int *d = T.tiles + (size_t)t * kTileInts;
+    const int p = d[0], I = d[1];
+    const Job &job = T.jt.job[p];
+    // the window of every term must fit the bitmaps, else the serial merge
+    int lo_t[2], hi_t[2], cur[2][2 * TBL], end[2][2 * TBL];
+    bool fits = true;
+    for (int term = 0; term < job.nterm; ++term) {
+        const int am = job.a[term], bm = job.b[term];
+        int loA = 0x7fffffff, hiA = -1, loB = 0x7fffffff, hiB = -1;
+        for (int q = 0; q < TBL; ++q) {
+            const int i = 4 * I + q, j = d[20 + q];
+            cur[term][q] = end[term][q] = 0;
+            cur[term][TBL + q] = end[term][TBL + q] = 0;
+            if (i < T.NB) { cur[term][q] = T.rp[am * T.NB + i]; end[term][q] = T.rp[am * T.NB + i + 1]; }
+            if (j >= 0) { cur[term][TBL + q] = T.rp[bm * T.NB + j]; end[term][TBL + q] = T.rp[bm * T.NB + j + 1]; }
+            if (cur[term][q] < end[term][q]) {
+                loA = min(loA, T.col[cur[term][q]]);
+                hiA = max(hiA, T.col[end[term][q] - 1]);
+            }
+            if (cur[term][TBL + q] < end[term][TBL + q]) {
+                loB = min(loB, T.col[cur[term][TBL + q]]);
+                hiB = max(hiB, T.col[end[term][TBL + q] - 1]);
+            }
+        }
+        lo_t[term] = max(loA, loB);
+        hi_t[term] = min(hiA, hiB);
+        if (hi_t[term] >= lo_t[term] && ((hi_t[term] - lo_t[term]) >> 5) + 1 > kStepWords) fits = false;
+    }
+    if (!fits) {
+        if (lane == 0) tile_steps_serial(T, t, fill);
+        return;
+    }
+    int64_t w = fill ? T.step_off[t] : 0;
+    int n = 0;
+    for (int term = 0; term < job.nterm; ++term) {
+        const int lo = lo_t[term], hi = hi_t[term];
+        if (hi < lo) continue;
+        const int nw = ((hi - lo) >> 5) + 1;
+        for (int x = lane; x < nw; x += 32) { ba[x] = 0u; bb[x] = 0u; }
+        __syncwarp();
+        for (int q = 0; q < 2 * TBL; ++q) {
+            unsigned *bmap = q < TBL ? ba : bb;
+            for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
+                const int k = T.col[e];
+                if (k < lo || k > hi) continue;
+                atomicOr(&bmap[(k - lo) >> 5], 1u << ((k - lo) & 31));
+            }
+        }
+        __syncwarp();
+        int carry = 0;
+        for (int x0 = 0; x0 < nw; x0 += 32) {
+            const int x = x0 + lane;
+            unsigned both = 0u;
+            if (x < nw) {
+                both = ba[x] & bb[x];
+                ba[x] = both;
+            }
+            const int c = __popc(both);
+            int y = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            if (x < nw) wr[x] = carry + y - c;
+            carry += __shfl_sync(0xffffffffu, y, 31);
+        }
+        __syncwarp();
+        if (fill) {
+            const int64_t wend = T.step_off[t + 1];
+            for (int64_t q = w + n + lane; q < min(w + n + carry, wend); q += 32) {
+                int *st = T.steps + (size_t)q * 8;
+                for (int k = 0; k < 8; ++k) st[k] = -1;
+            }
+            __syncwarp();
+            for (int q = 0; q < 2 * TBL; ++q)
+                for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
+                    const int k = T.col[e];
+                    if (k < lo || k > hi) continue;
+                    const int kk = k - lo;
+                    const unsigned word = ba[kk >> 5];
+                    if (!((word >> (kk & 31)) & 1u)) continue;
+                    const int r = wr[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
+                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * 8 + q] = e;
+                }
+            __syncwarp();
+        }
+        n += carry;
+    }
+    if (lane == 0) {
+        if (!fill) T.step_cnt[t] = n;
+        else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
+    }
 }
 
 __global__ void k_set_nsteps(int *tiles, const int *step_cnt, int ntile) {
@@ -723,7 +933,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     T.u0 = unit0; T.u1 = unit1;
     T.sys_tier = sd.tier.p;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
-    k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 0);
+    k_tile_rows<<<(nrow4 + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();
     scan_exclusive_i32(w.tile_cnt.p, w.tile_off.p, nrow4, w.scan32.p, st);
     int ntile = 0;
@@ -733,14 +943,14 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     if (ntile == 0) return plan;
     w.tiles.ensure((size_t)ntile * kTileInts);
     T.tiles = w.tiles.p;
-    k_tile_rows<<<(nrow4 + 127) / 128, 128, 0, st>>>(T, 1);
+    k_tile_rows<<<(nrow4 + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 1);
     RDM_LAUNCH_CHECK();
     w.step_cnt.ensure(ntile + 1);
     w.step_off.ensure(ntile + 1);
     w.scan64.ensure(scan_tmp_elems(ntile + 1));
     T.ntile = ntile;
     T.step_cnt = w.step_cnt.p;
-    k_tile_steps<<<(ntile + 127) / 128, 128, 0, st>>>(T, 0);
+    k_tile_steps<<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();
     scan_exclusive_i64(w.step_cnt.p, w.step_off.p, ntile, w.scan64.p, st);
     int64_t nsteps = 0;
@@ -752,7 +962,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     T.steps = w.steps.p;
     k_set_nsteps<<<(ntile + 127) / 128, 128, 0, st>>>(w.tiles.p, w.step_cnt.p, ntile);
     RDM_LAUNCH_CHECK();
-    k_tile_steps<<<(ntile + 127) / 128, 128, 0, st>>>(T, 1);
+    k_tile_steps<<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 1);
     RDM_LAUNCH_CHECK();
     return plan;
 }
