@@ -185,33 +185,51 @@ __global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__rest
     }
 }
 
+// one thread per 8 consecutive elements of a block row (one core-matrix row):
+// 64 bytes of FP64 in, 16 bytes of hi and 16 bytes of lo out
 template <bool BF16>
 __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
                                const float *__restrict__ scale,
                                const int *__restrict__ mat_first, int nmat) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t n = nblk * kPlaneElems;
-    if (e >= n) return;
-    int64_t p = e / kPlaneElems;
-    int rc = (int)(e % kPlaneElems);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nblk * (kPlaneElems / 8)) return;
+    const int64_t p = g / (kPlaneElems / 8);
+    const int rc0 = (int)(g % (kPlaneElems / 8)) * 8;     // first element (row r, columns c0..c0+7)
+    const int r = rc0 >> 5, c0 = rc0 & 31;
     int m = 0;
     while (m + 1 < nmat && p >= mat_first[m + 1]) ++m;
-    float x = (float)val[e] * scale[m];
-    uint16_t h, l;
-    if (BF16) {
-        __nv_bfloat16 bh = __float2bfloat16_rn(x);
-        __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
-        h = __bfloat16_as_ushort(bh);
-        l = __bfloat16_as_ushort(bl);
-    } else {
-        __half hh = __float2half_rn(x);
-        __half hl = __float2half_rn(x - __half2float(hh));
-        h = __half_as_ushort(hh);
-        l = __half_as_ushort(hl);
+    const float sc = scale[m];
+    const double2 *v2 = reinterpret_cast<const double2 *>(val + p * kPlaneElems + rc0);
+    uint16_t h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double2 x2 = v2[k];
+        const float xs[2] = {(float)x2.x * sc, (float)x2.y * sc};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float x = xs[u];
+            if (BF16) {
+                const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+                const __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
+                h[2 * k + u] = __bfloat16_as_ushort(bh);
+                l[2 * k + u] = __bfloat16_as_ushort(bl);
+            } else {
+                const __half hh = __float2half_rn(x);
+                const __half hl = __float2half_rn(x - __half2float(hh));
+                h[2 * k + u] = __half_as_ushort(hh);
+                l[2 * k + u] = __half_as_ushort(hl);
+            }
+        }
     }
-    const int64_t o = p * (2 * kPlaneElems);
-    hi[o + pair_offset(rc >> 5, rc & 31, 0)] = h;
-    hi[o + pair_offset(rc >> 5, rc & 31, 1)] = l;
+    uint4 hv, lv;
+    hv.x = h[0] | ((uint32_t)h[1] << 16); hv.y = h[2] | ((uint32_t)h[3] << 16);
+    hv.z = h[4] | ((uint32_t)h[5] << 16); hv.w = h[6] | ((uint32_t)h[7] << 16);
+    lv.x = l[0] | ((uint32_t)l[1] << 16); lv.y = l[2] | ((uint32_t)l[3] << 16);
+    lv.z = l[4] | ((uint32_t)l[5] << 16); lv.w = l[6] | ((uint32_t)l[7] << 16);
+    // columns c0..c0+7 of row r are 8 consecutive elements of one core matrix
+    uint16_t *o = hi + p * (2 * kPlaneElems);
+    *reinterpret_cast<uint4 *>(o + pair_offset(r, c0, 0)) = hv;
+    *reinterpret_cast<uint4 *>(o + pair_offset(r, c0, 1)) = lv;
 }
 
 // ---------------------------------------------------------------------------
@@ -864,7 +882,7 @@ void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
     const int64_t n = in.total * kPlaneElems;
     in.ophi.ensure(std::max<int64_t>(2 * n, 1));   // hi and lo, interleaved per block
     if (n == 0) return;
-    const int64_t grid = (n + 255) / 256;
+    const int64_t grid = (n / 8 + 255) / 256;
     if (ar == AR_BF16X3)
         k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
                                                              w.mat_first.p, nmat);
