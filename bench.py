@@ -46,11 +46,11 @@ FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.
 # source file is unchanged since (SHA-256 recorded)
 PROFILED_TRAFFIC = {
     "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
-           "sha256": "ebef8a7edf8b75441359fab238decdb474bc488e3810321025dbe9d69915ac1f",
-           "bytes_per_launch": 28204126065, "workload": WORKLOAD},
+           "sha256": "af77dcc6ca2313c1c6e3c010614e43245e0ec409f1202a04dfdf9cc25cc9c773",
+           "bytes_per_launch": 28362752526, "workload": WORKLOAD},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
            "sha256": "7bfe29d47db534256e8d6f9fc960cd287df87ef4c15eeab31a803ae8a309295c",
-           "bytes_per_launch": 10232099072, "workload": WORKLOAD},
+           "bytes_per_launch": 10199553408, "workload": WORKLOAD},
 }
 
 
