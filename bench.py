@@ -42,14 +42,15 @@ FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
 # over the launches of one solve) of the product kernels on the 2,000-atom
-# cluster, from one ncu capture (profiles/); reported only while the kernel's
-# source file is unchanged since (SHA-256 recorded)
+# cluster, from one ncu capture (profiles/); reported only while the code of the
+# kernel's source file is unchanged since (SHA-256 of the file with comments and
+# whitespace removed, so that a comment edit keeps the figure and a code edit drops it)
 PROFILED_TRAFFIC = {
     "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
-           "sha256": "af77dcc6ca2313c1c6e3c010614e43245e0ec409f1202a04dfdf9cc25cc9c773",
+           "sha256": "141b42fe2cbdc641a4628b7a0155da9db1a6e676ad91826add93b96c95ba4025",
            "bytes_per_launch": 28362752526, "workload": WORKLOAD},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
-           "sha256": "7bfe29d47db534256e8d6f9fc960cd287df87ef4c15eeab31a803ae8a309295c",
+           "sha256": "1c9d3e76e36659e5d06b0d237474522761ebecc2732c37eb20f037dc4adcb12e",
            "bytes_per_launch": 10199553408, "workload": WORKLOAD},
 }
 
@@ -84,10 +85,25 @@ def profiled_traffic(cls, workload):
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["file"])
     try:
-        sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        sha = code_sha256(path)
     except OSError:
         return None
     return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+
+
+def code_sha256(path):
+    """SHA-256 of a C/C++/CUDA source file with its comments and all whitespace removed."""
+    return code_digest(open(path, encoding="utf-8").read())
+
+
+def code_digest(src):
+    """SHA-256 of C/C++/CUDA source text with its comments and all whitespace removed."""
+    import hashlib
+    import re
+    # string and character literals are kept whole; comments are dropped
+    tok = re.compile(r'"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'|//[^\n]*|/\*.*?\*/', re.S)
+    code = tok.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", src)
+    return hashlib.sha256(re.sub(r"\s+", "", code).encode()).hexdigest()
 
 
 def load_peaks():

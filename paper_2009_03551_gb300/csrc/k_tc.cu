@@ -59,9 +59,9 @@ constexpr int kSideBytes = TBL * kPairBytes; // 16 KB: 4 blocks stacked
 constexpr int kStageBytes = 2 * kSideBytes;  // A side, B side
 constexpr int kEpiWarps = 8;                 // epilogue warps: 2 per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kTileInts = 24;
+constexpr int kTileInts = 24;               // per tile: job, super-row, -, nsteps, mask slot[4 x 4], column j[4]
 constexpr int kSegSteps = 4;                 // K-steps accumulated in tensor memory per segment
-constexpr int kSegBufs = 4;                  // segment accumulators in TMEM (4 x 128 columns)                // p, I, -, nsteps, slot[16], column j of each tile column[4]
+constexpr int kSegBufs = 4;                  // segment accumulators in TMEM (4 x 128 columns)
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------------------
