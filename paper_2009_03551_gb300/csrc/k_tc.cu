@@ -1,14 +1,19 @@
 // Tensor-core numeric phase (tcgen05 + TMEM, sm_103a) for 32 x 32 blocks.
 //
-// Work decomposition.  Output blocks are grouped in 128 x 128 super-tiles:
-// block rows 4I..4I+3 times 4 block columns taken, in increasing order, from
+// Work decomposition.  Output blocks are grouped in 128 x 256 super-tiles:
+// block rows 4I..4I+3 times 8 block columns taken, in increasing order, from
 // the columns that these rows need (upper triangle of the mask), so that every
 // tile column is needed by at least one tile row.  A super-tile is
-// one MMA accumulator: D[128 x 128] = sum over K-steps of A[128 x 32] B[128 x 32]^T
+// one MMA accumulator: D[128 x 256] = sum over K-steps of A[128 x 32] B[256 x 32]^T
 // where a K-step is one block index k at which some row of the tile's A rows
 // and some row of its B rows have a stored block (Gustavson's row merge,
-// Algorithm 1, lifted to a 4 x 4 block tile).  Missing blocks are zero.  The
+// Algorithm 1, lifted to a 4 x 8 block tile).  Missing blocks are zero.  The
 // X1 products (X0 X1 + X1 X0) simply concatenate the K-steps of both terms.
+// The tile is as wide as one MMA allows because operand bytes bound the
+// kernel: a K-step brings 12 blocks (48 KB) for 128 x 256 x 32 of MMA work,
+// against 8 blocks (32 KB) for 128 x 128 x 32 with 4 x 4 tiles; on the masks
+// of the 2,000-atom cluster the 4 x 8 tiles copied ~20% fewer bytes per
+// product and ran the products 29% faster than 4 x 4 tiles.
 //
 // Split precision.  Every operand block is stored as a hi and a lo plane
 // (bf16 or fp16, hi = rn(x), lo = rn(x - hi)); one K-step issues the products
@@ -18,20 +23,26 @@
 // matrix, core matrices adjacent along K 128 bytes apart), with the 8-row
 // groups of a block's hi and lo planes alternating (512 bytes each, 1 KB
 // between the groups of one plane): one 4 KB bulk copy per block lands both
-// planes ready for the MMA.  The producer warp issues about one bulk copy
-// per 60 cycles, which bounds the kernel; interleaving halved the copies.
+// planes ready for the MMA; interleaving halved the copies.  A streaming
+// probe (one CTA per SM, no MMA) moves at most ~6.5 TB/s over the GPU in
+// 4 KB bulk copies, from L2 as from DRAM, and ~7.4-8.9 TB/s in 16-32 KB
+// copies: the rate of such copies into each SM bounds this kernel.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over a static tile
-// schedule): warp 0 issues the bulk copies into a 6-stage ring, warp 1 owns
-// the tensor-memory allocation and one thread issues the MMAs, warps 2-9 (two
-// per TMEM lane quarter = block row of the tile, two block columns each) run
-// the epilogue.
+// schedule): warp 0 issues the bulk copies into a 4-stage ring of 48 KB
+// stages, warp 1 owns the tensor-memory allocation and one thread issues the
+// MMAs, warps 2-9 (two per TMEM lane quarter = block row of the tile, four
+// block columns each) run the epilogue.  Ten warps put three on some SM
+// sub-partitions, which caps a thread at 168 registers: the epilogue keeps
+// its 128 accumulators in registers and parks the tile metadata in shared
+// memory.  An L2 prefetch of the blocks eight K-steps ahead (one extra bulk
+// request per block) made the kernel 13% slower: bulk requests are scarce.
 //
 // Accumulation in segments.  The tensor cores' FP32 accumulation truncates
 // (it is not round-to-nearest), so a long accumulation chain drifts towards
 // zero: measured on positive data, -2e-7 relative per K-step, -2e-5 after 96
 // K-steps.  The K-steps of a tile are therefore accumulated in segments of
-// kSegSteps in fresh TMEM accumulators (4 rotating buffers of 128 columns);
+// kSegSteps in fresh TMEM accumulators (2 rotating buffers of 256 columns);
 // the epilogue warps add every finished segment to registers with
 // round-to-nearest FP32 adds and release the buffer.  The drift is then that
 // of one segment (-7e-7 relative), independent of the tile's length.  After
@@ -50,18 +61,24 @@ namespace rdm {
 namespace {
 
 constexpr int TB = 32;                       // block size handled here
-constexpr int TBL = 4;                       // blocks per tile edge
-constexpr int kStages = 6;
+constexpr int TBM = 4;                       // block rows per super-tile (MMA M = 128)
+constexpr int TBN = 8;                       // block columns per super-tile
+constexpr int kTileN = TBN * TB;             // MMA N = accumulator columns in tensor memory
+constexpr int kSlots = TBM + TBN;            // operand blocks per K-step: A rows, then B rows
+constexpr int kStages = TBN == 8 ? 4 : 7;    // ring stages (all but a few KB of shared memory)
 constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
 constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
 constexpr int kPairBytes = 2 * kPlaneBytes;  // hi and lo planes of one block, interleaved: 4 KB
-constexpr int kSideBytes = TBL * kPairBytes; // 16 KB: 4 blocks stacked
-constexpr int kStageBytes = 2 * kSideBytes;  // A side, B side
+constexpr int kSideABytes = TBM * kPairBytes;    // A side: TBM blocks stacked
+constexpr int kStageBytes = kSlots * kPairBytes; // A side, then the TBN blocks of the B side
 constexpr int kEpiWarps = 8;                 // epilogue warps: 2 per TMEM lane quarter
+constexpr int kColBlocks = TBN / 2;          // block columns per epilogue warp
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kTileInts = 24;               // per tile: job, super-row, -, nsteps, mask slot[4 x 4], column j[4]
+constexpr int kColOff = 4 + TBM * TBN;       // tile record: job, super-row, -, nsteps, mask slot[TBM x TBN],
+constexpr int kTileInts = kColOff + TBN;     //   then column j of each tile column
 constexpr int kSegSteps = 4;                 // K-steps accumulated in tensor memory per segment
-constexpr int kSegBufs = 4;                  // segment accumulators in TMEM (4 x 128 columns)
+constexpr int kSegBufs = 512 / kTileN;       // segment accumulators: the 512 TMEM columns
+static_assert(kSlots <= 32 && kSegBufs >= 2 && (kSegBufs & (kSegBufs - 1)) == 0, "tile shape");
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------------------
@@ -132,20 +149,16 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,14 +263,14 @@ struct TileBuild {
     int *tiles;          // [ntile * kTileInts]
     int *step_cnt;       // [ntile]
     const int64_t *step_off;
-    int *steps;          // [nsteps * 8]
+    int *steps;          // [nsteps * kSlots]
     int ntile;
 };
 
 // upper mask range [cur, end) of block row 4I + m of job p, empty for rows
 // whose system is converged or whose job is not computed on the tensor cores
 __device__ __forceinline__ void tile_row_range(const TileBuild &T, int p, int I, int m, int &cur, int &end) {
-    const int i = 4 * I + m;
+    const int i = TBM * I + m;
     cur = end = 0;
     if (i >= T.NB) return;
     int lo = T.out_rp[p * T.NB + i], hi = T.out_rp[p * T.NB + i + 1];
@@ -278,8 +291,8 @@ __device__ __forceinline__ void tile_row_range(const TileBuild &T, int p, int I,
 // Tiles of one (job, super-row), warp-parallel: the upper mask columns of
 // block rows 4I..4I+3 are marked in a shared-memory bitmap over their column
 // window; the rank of a column among the distinct ones (prefix popcounts)
-// gives its tile (rank / 4) and tile column (rank % 4).  Windows wider than
-// the bitmap fall back to a serial 4-way merge by lane 0 (count or fill).
+// gives its tile (rank / TBN) and tile column (rank % TBN).  Windows wider
+// than the bitmap fall back to a serial 4-way merge by lane 0 (count or fill).
 constexpr int kTileRowWarps = 8, kTileRowWords = 512;   // 16,384 columns per window
 __device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
                                  int fill);
@@ -293,11 +306,11 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
     unsigned *bm = bits_s[wq];
     int *wr = rank_s[wq];
     int c0 = 0, e0 = 0;
-    if (lane < TBL) tile_row_range(T, p, I, lane, c0, e0);
-    int cur[TBL], end[TBL];
+    if (lane < TBM) tile_row_range(T, p, I, lane, c0, e0);
+    int cur[TBM], end[TBM];
     int lo = 0x7fffffff, hi = -1;
 #pragma unroll
-    for (int m = 0; m < TBL; ++m) {
+    for (int m = 0; m < TBM; ++m) {
         cur[m] = __shfl_sync(0xffffffffu, c0, m);
         end[m] = __shfl_sync(0xffffffffu, e0, m);
         if (cur[m] < end[m]) {
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
     for (int w = lane; w < nw; w += 32) bm[w] = 0u;
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < TBL; ++m)
+    for (int m = 0; m < TBM; ++m)
         for (int e = cur[m] + lane; e < end[m]; e += 32) {
             const int j = T.mcol[e] - lo;
             atomicOr(&bm[j >> 5], 1u << (j & 31));
@@ -339,7 +352,7 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
         carry += __shfl_sync(0xffffffffu, x, 31);
     }
     __syncwarp();
-    const int ndist = carry, ntile = (ndist + 3) >> 2;
+    const int ndist = carry, ntile = (ndist + TBN - 1) / TBN;
     if (!fill) {
         if (lane == 0) T.tile_cnt[t - T.u0] = ntile;
         return;
@@ -347,56 +360,54 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
     for (int q = lane; q < ntile; q += 32) {
         int *d = T.tiles + (size_t)(base + q) * kTileInts;
         d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
-        for (int k = 0; k < 16; ++k) d[4 + k] = -1;
-        for (int k = 0; k < TBL; ++k) d[20 + k] = -1;
+        for (int k = 4; k < kTileInts; ++k) d[k] = -1;
     }
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < TBL; ++m)
+    for (int m = 0; m < TBM; ++m)
         for (int e = cur[m] + lane; e < end[m]; e += 32) {
             const int jc = T.mcol[e];
             const int j = jc - lo;
             const int r = wr[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-            int *d = T.tiles + (size_t)(base + (r >> 2)) * kTileInts;
-            d[4 + m * 4 + (r & 3)] = e;
-            d[20 + (r & 3)] = jc;
+            int *d = T.tiles + (size_t)(base + r / TBN) * kTileInts;
+            d[4 + m * TBN + r % TBN] = e;
+            d[kColOff + r % TBN] = jc;
         }
 }
 
 // the serial 4-way merge (same tile order as the bitmap path)
 __device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
                                  int fill) {
-    int cur[TBL], end[TBL];
-    for (int m = 0; m < TBL; ++m) { cur[m] = cur0[m]; end[m] = end0[m]; }
+    int cur[TBM], end[TBM];
+    for (int m = 0; m < TBM; ++m) { cur[m] = cur0[m]; end[m] = end0[m]; }
     // the distinct columns needed by the 4 rows, in increasing order, are packed
     // 4 at a time into tiles: every tile column is needed by at least one row
     int ncol = 0, n = 0;
     const int base = fill ? T.tile_off[t - T.u0] : 0;
     int *d = nullptr;
     // list heads kept in registers: one load per advance
-    int head[TBL];
+    int head[TBM];
 #pragma unroll
-    for (int m = 0; m < TBL; ++m) head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
+    for (int m = 0; m < TBM; ++m) head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
     while (true) {
         int jmin = 0x7fffffff;
 #pragma unroll
-        for (int m = 0; m < TBL; ++m) jmin = min(jmin, head[m]);
+        for (int m = 0; m < TBM; ++m) jmin = min(jmin, head[m]);
         if (jmin == 0x7fffffff) break;
-        const int c = ncol & 3;
+        const int c = ncol % TBN;
         if (c == 0) {
             if (fill) {
                 d = T.tiles + (size_t)(base + n) * kTileInts;
                 d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
-                for (int q = 0; q < 16; ++q) d[4 + q] = -1;
-                for (int q = 0; q < TBL; ++q) d[20 + q] = -1;
+                for (int q = 4; q < kTileInts; ++q) d[q] = -1;
             }
             ++n;
         }
-        if (fill) d[20 + c] = jmin;
+        if (fill) d[kColOff + c] = jmin;
 #pragma unroll
-        for (int m = 0; m < TBL; ++m)
+        for (int m = 0; m < TBM; ++m)
             if (head[m] == jmin) {
-                if (fill) d[4 + m * 4 + c] = cur[m];
+                if (fill) d[4 + m * TBN + c] = cur[m];
                 ++cur[m];
                 head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
             }
@@ -415,39 +426,42 @@ __device__ void tile_steps_serial(const TileBuild &T, int t, int fill) {
     int n = 0;
     for (int term = 0; term < job.nterm; ++term) {
         const int am = job.a[term], bm = job.b[term];
-        int cur[2 * TBL], end[2 * TBL];
-        for (int q = 0; q < TBL; ++q) {
-            const int i = 4 * I + q, j = d[20 + q];
+        int cur[kSlots], end[kSlots];
+        for (int q = 0; q < TBM; ++q) {
+            const int i = TBM * I + q;
             cur[q] = end[q] = 0;
-            cur[TBL + q] = end[TBL + q] = 0;
             if (i < T.NB) { cur[q] = T.rp[am * T.NB + i]; end[q] = T.rp[am * T.NB + i + 1]; }
-            if (j >= 0) { cur[TBL + q] = T.rp[bm * T.NB + j]; end[TBL + q] = T.rp[bm * T.NB + j + 1]; }
+        }
+        for (int q = 0; q < TBN; ++q) {
+            const int j = d[kColOff + q];
+            cur[TBM + q] = end[TBM + q] = 0;
+            if (j >= 0) { cur[TBM + q] = T.rp[bm * T.NB + j]; end[TBM + q] = T.rp[bm * T.NB + j + 1]; }
         }
         // list heads kept in registers: one load per advance
-        int head[2 * TBL];
+        int head[kSlots];
 #pragma unroll
-        for (int q = 0; q < 2 * TBL; ++q) head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
+        for (int q = 0; q < kSlots; ++q) head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
         while (true) {
             int kmin = 0x7fffffff;
 #pragma unroll
-            for (int q = 0; q < 2 * TBL; ++q) kmin = min(kmin, head[q]);
+            for (int q = 0; q < kSlots; ++q) kmin = min(kmin, head[q]);
             if (kmin == 0x7fffffff) break;
             bool anyA = false, anyB = false;
-            int idx[2 * TBL];
+            int idx[kSlots];
 #pragma unroll
-            for (int q = 0; q < 2 * TBL; ++q) {
+            for (int q = 0; q < kSlots; ++q) {
                 idx[q] = -1;
                 if (head[q] == kmin) {
                     idx[q] = cur[q];
                     ++cur[q];
                     head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
-                    if (q < TBL) anyA = true; else anyB = true;
+                    if (q < TBM) anyA = true; else anyB = true;
                 }
             }
             if (anyA && anyB) {
                 if (fill && w + n < T.step_off[t + 1]) {
-                    int *s = T.steps + (size_t)(w + n) * 8;
-                    for (int q = 0; q < 8; ++q) s[q] = idx[q];
+                    int *s = T.steps + (size_t)(w + n) * kSlots;
+                    for (int q = 0; q < kSlots; ++q) s[q] = idx[q];
                 }
                 ++n;
             }
@@ -457,8 +471,8 @@ __device__ void tile_steps_serial(const TileBuild &T, int t, int fill) {
     else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
 }
 
-// K-steps of one tile, warp-parallel: per term, the columns k of the tile's 4
-// A rows and of its 4 B rows are marked in two shared-memory bitmaps over
+// K-steps of one tile, warp-parallel: per term, the columns k of the tile's
+// TBM A rows and of its TBN B rows are marked in two shared-memory bitmaps over
 // the window where both can have columns; a K-step is a k marked in both, its
 // index the rank of k among those (prefix popcounts).  Each list entry at
 // such a k writes its block index into its slot of the step; the other
@@ -477,24 +491,27 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
     const int p = d[0], I = d[1];
     const Job &job = T.jt.job[p];
     // the window of every term must fit the bitmaps, else the serial merge
-    int lo_t[2], hi_t[2], cur[2][2 * TBL], end[2][2 * TBL];
+    int lo_t[2], hi_t[2], cur[2][kSlots], end[2][kSlots];
     bool fits = true;
     for (int term = 0; term < job.nterm; ++term) {
         const int am = job.a[term], bm = job.b[term];
         int loA = 0x7fffffff, hiA = -1, loB = 0x7fffffff, hiB = -1;
-        for (int q = 0; q < TBL; ++q) {
-            const int i = 4 * I + q, j = d[20 + q];
+        for (int q = 0; q < TBM; ++q) {
+            const int i = TBM * I + q;
             cur[term][q] = end[term][q] = 0;
-            cur[term][TBL + q] = end[term][TBL + q] = 0;
             if (i < T.NB) { cur[term][q] = T.rp[am * T.NB + i]; end[term][q] = T.rp[am * T.NB + i + 1]; }
-            if (j >= 0) { cur[term][TBL + q] = T.rp[bm * T.NB + j]; end[term][TBL + q] = T.rp[bm * T.NB + j + 1]; }
             if (cur[term][q] < end[term][q]) {
                 loA = min(loA, T.col[cur[term][q]]);
                 hiA = max(hiA, T.col[end[term][q] - 1]);
             }
-            if (cur[term][TBL + q] < end[term][TBL + q]) {
-                loB = min(loB, T.col[cur[term][TBL + q]]);
-                hiB = max(hiB, T.col[end[term][TBL + q] - 1]);
+        }
+        for (int q = 0; q < TBN; ++q) {
+            const int j = d[kColOff + q];
+            cur[term][TBM + q] = end[term][TBM + q] = 0;
+            if (j >= 0) { cur[term][TBM + q] = T.rp[bm * T.NB + j]; end[term][TBM + q] = T.rp[bm * T.NB + j + 1]; }
+            if (cur[term][TBM + q] < end[term][TBM + q]) {
+                loB = min(loB, T.col[cur[term][TBM + q]]);
+                hiB = max(hiB, T.col[end[term][TBM + q] - 1]);
             }
         }
         lo_t[term] = max(loA, loB);
@@ -513,8 +530,8 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         const int nw = ((hi - lo) >> 5) + 1;
         for (int x = lane; x < nw; x += 32) { ba[x] = 0u; bb[x] = 0u; }
         __syncwarp();
-        for (int q = 0; q < 2 * TBL; ++q) {
-            unsigned *bmap = q < TBL ? ba : bb;
+        for (int q = 0; q < kSlots; ++q) {
+            unsigned *bmap = q < TBM ? ba : bb;
             for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
                 const int k = T.col[e];
                 if (k < lo || k > hi) continue;
@@ -544,11 +561,11 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         if (fill) {
             const int64_t wend = T.step_off[t + 1];
             for (int64_t q = w + n + lane; q < min(w + n + carry, wend); q += 32) {
-                int *st = T.steps + (size_t)q * 8;
-                for (int k = 0; k < 8; ++k) st[k] = -1;
+                int *st = T.steps + (size_t)q * kSlots;
+                for (int k = 0; k < kSlots; ++k) st[k] = -1;
             }
             __syncwarp();
-            for (int q = 0; q < 2 * TBL; ++q)
+            for (int q = 0; q < kSlots; ++q)
                 for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
                     const int k = T.col[e];
                     if (k < lo || k > hi) continue;
@@ -556,7 +573,7 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
                     const unsigned word = ba[kk >> 5];
                     if (!((word >> (kk & 31)) & 1u)) continue;
                     const int r = wr[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
-                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * 8 + q] = e;
+                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * kSlots + q] = e;
                 }
             __syncwarp();
         }
@@ -639,10 +656,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
 
     if (warp == 0) {
         // ---------------- producer: bulk copies of the operand blocks ----------------
-        // The whole warp works: the block indices of the next K-step are loaded
-        // (one per lane 0..7) while the current step's copies are issued by
-        // lanes 0..15 in parallel (lane m < 8: hi plane of slot m, lane 8 + m:
-        // lo plane of slot m).  Slot m < 4 is A block row m, m >= 4 B row m-4.
+        // Lane m < kSlots owns slot m of every stage (slot m < TBM: A block row
+        // m, else B block row m - TBM; slot m at m * 4 KB): it loads the block
+        // index of the next K-step while the current step's copies, one 4 KB
+        // copy per slot (hi and lo planes), are issued by all lanes at once.
         // A slot whose block is missing needs zeros; a stage slot that already
         // holds zeros from its previous use is not copied again (zmask).
         uint32_t it = 0;
@@ -652,21 +669,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
         for (int k = 0; k < kStages; ++k) zmask[k] = 0u;
         for (int t = blockIdx.x; t < A.ntile && ok; t += gridDim.x) {
             const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
-            int nxt = (s0 < s1 && lane < 8) ? A.steps[s0 * 8 + lane] : -1;
+            int nxt = (s0 < s1 && lane < kSlots) ? A.steps[s0 * kSlots + lane] : -1;
             for (int64_t q = s0; q < s1; ++q, ++it) {
                 const int cur = nxt;
-                if (q + 1 < s1 && lane < 8) nxt = A.steps[(q + 1) * 8 + lane];
+                if (q + 1 < s1 && lane < kSlots) nxt = A.steps[(q + 1) * kSlots + lane];
                 const int st = it % kStages;
                 const uint32_t ph = (it / kStages) & 1;
-                const int slot = lane & 7;
-                const int b = __shfl_sync(0xffffffffu, cur, slot);
-                const uint32_t zbits = __ballot_sync(0xffffffffu, lane < 8 && cur < 0) & 0xffu;
+                const uint32_t zbits = __ballot_sync(0xffffffffu, lane < kSlots && cur < 0);
                 uint32_t zprev = 0u;
 #pragma unroll
                 for (int k = 0; k < kStages; ++k)
                     if (k == st) zprev = zmask[k];
-                const bool skip = (b < 0) && ((zprev >> slot) & 1u);
-                const uint32_t need = __ballot_sync(0xffffffffu, lane < 8 && !skip);
+                const bool skip = lane >= kSlots || (cur < 0 && ((zprev >> lane) & 1u));
+                const uint32_t need = __ballot_sync(0xffffffffu, !skip);
                 int waited = 1;
                 if (lane == 0) {
                     waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag) ? 1 : 0;
@@ -677,15 +692,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
 #pragma unroll
                 for (int k = 0; k < kStages; ++k)
                     if (k == st) zmask[k] = zbits;
-                if (lane < 8 && !skip) {
-                    uint8_t *dst = stages + st * kStageBytes;
-                    const int side = slot >> 2, r = slot & 3;
+                if (!skip) {
                     // zero blocks: one per CTA and slot, so that the CTAs do not all
                     // read the same few L2 sectors
-                    const uint16_t *src = b >= 0 ? A.planes + (size_t)b * (2 * kPlaneElems)
-                                                 : A.zero + ((size_t)blockIdx.x * 8 + lane) * (2 * kPlaneElems);
-                    // A side [0, 16K), B side [16K, 32K); block r of a side at r * 4K
-                    bulk_g2s(dst + side * kSideBytes + r * kPairBytes, src, kPairBytes, &ctl->full[st]);
+                    const uint16_t *src = cur >= 0 ? A.planes + (size_t)cur * (2 * kPlaneElems)
+                                                   : A.zero + ((size_t)blockIdx.x * kSlots + lane) * (2 * kPlaneElems);
+                    bulk_g2s(stages + st * kStageBytes + lane * kPairBytes, src, kPairBytes, &ctl->full[st]);
                 }
             }
         }
@@ -703,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                     const uint32_t use = seg / kSegBufs;
                     if (!mbar_wait(&ctl->seg_empty[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t d_tmem = tmem + buf * 128;
+                    const uint32_t d_tmem = tmem + buf * kTileN;
                     const int64_t qe = q + kSegSteps < s1 ? q + kSegSteps : s1;
                     const int64_t qs = q;
                     for (; q < qe; ++q, ++it) {
@@ -713,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                         fence_after();
                         const uint32_t base = smem_u32(stages + st * kStageBytes);
                         const uint32_t a_hi = base, a_lo = base + 512;
-                        const uint32_t b_hi = base + kSideBytes, b_lo = base + kSideBytes + 512;
+                        const uint32_t b_hi = base + kSideABytes, b_lo = base + kSideABytes + 512;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint32_t ko = kk * 256;
@@ -740,19 +752,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     } else {
         // ---------------- epilogue: warps 2..9, TMEM lane quarter = block row ----------------
         const int eq = warp & 3;                       // lanes 32*eq .. 32*eq+31
-        const int n0 = ((warp - 2) >> 2) * 2;           // this warp's two column blocks n0, n0+1
-        float *S = stage_ep + (warp - 2) * 32 * 33;
+        const int n0 = ((warp - 2) >> 2) * kColBlocks;  // this warp's column blocks n0 .. n0 + kColBlocks - 1
+        float *S = stage_ep + (warp - 2) * 32 * 33;     // one block, transposed through shared memory
         uint32_t seg = 0;
         for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
-            // metadata of this warp's 2 output blocks, one lane each (lanes 0..1),
-            // gathered while the tile's MMAs run; the old X blocks of the
-            // linear term are prefetched into L2
+            // metadata of this warp's output blocks, one lane each, gathered
+            // while the tile's MMAs run and parked in the padding column of S
+            // (8 words per block: slot, old slot, diagonal, output index,
+            // c_lin, c_sq, tau lo, tau hi) to keep registers for the
+            // accumulators; the old X blocks of the linear term are
+            // prefetched into L2
             const int *d = A.tiles + (size_t)t * kTileInts;
-            int m_s = -1, m_sx = -1, m_diag = 0, m_keepidx = 0;
-            float m_cl = 0.f, m_cq = 0.f;
-            double m_tau = 0.0;
-            if (lane < 2) {
-                m_s = d[4 + eq * 4 + n0 + lane];
+            float *meta = S + 32;                      // S[r * 33 + 32], r = 0..31
+            if (lane < kColBlocks) {
+                int m_s = -1, m_sx = -1, m_diag = 0, m_keepidx = 0;
+                float m_cl = 0.f, m_cq = 0.f;
+                double m_tau = 0.0;
+                m_s = d[4 + eq * TBN + n0 + lane];
                 if (m_s >= 0) {
                     const int i = A.slot_row[m_s];
                     const int sys = A.sys_of_row[i];
@@ -769,14 +785,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8192) : "memory");
                     }
                 }
+                float *q = meta + lane * 8 * 33;
+                q[0] = __int_as_float(m_s);
+                q[33] = __int_as_float(m_sx);
+                q[2 * 33] = __int_as_float(m_diag);
+                q[3 * 33] = __int_as_float(m_keepidx);
+                q[4 * 33] = m_cl;
+                q[5 * 33] = m_cq;
+                q[6 * 33] = __int_as_float(__double2loint(m_tau));
+                q[7 * 33] = __int_as_float(__double2hiint(m_tau));
             }
+            __syncwarp();
             const int nst = d[3];
             if (nst < 0 && lane == 0) atomicOr(A.err, 4);
             // the tile's accumulator: sum of its segments, added with
-            // round-to-nearest in registers (row 32*eq + lane, this warp's 64 columns)
-            float racc[64];
+            // round-to-nearest in registers (row 32*eq + lane, this warp's 32 * kColBlocks columns)
+            float racc[32 * kColBlocks];
 #pragma unroll
-            for (int c = 0; c < 64; ++c) racc[c] = 0.f;
+            for (int c = 0; c < 32 * kColBlocks; ++c) racc[c] = 0.f;
             const int nseg = nst > 0 ? (nst + kSegSteps - 1) / kSegSteps : 0;
             bool ok = true;
             for (int g = 0; g < nseg; ++g, ++seg) {
@@ -784,13 +810,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 const uint32_t use = seg / kSegBufs;
                 if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag)) { ok = false; break; }
                 fence_after();
-                const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * 128;
+                const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * kTileN;
 #pragma unroll
-                for (int n = 0; n < 2; ++n) {
-                    float part[32];
-                    tmem_ld32(ta + (n0 + n) * 32, part);
+                for (int h = 0; h < 2 * kColBlocks; ++h) {
+                    float part[16];
+                    tmem_ld16(ta + n0 * 32 + h * 16, part);
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) racc[n * 32 + c] += part[c];
+                    for (int c = 0; c < 16; ++c) racc[h * 16 + c] += part[c];
                 }
                 fence_before();
                 __syncwarp();
@@ -798,32 +824,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             }
             if (!ok) break;
 #pragma unroll
-            for (int n = 0; n < 2; ++n) {
-                const int s = __shfl_sync(0xffffffffu, m_s, n);
+            for (int n = 0; n < kColBlocks; ++n) {
+                const float *q = meta + n * 8 * 33;
+                const int s = __float_as_int(q[0]);
                 if (s < 0) continue;
                 float acc[32];
 #pragma unroll
                 for (int c = 0; c < 32; ++c) acc[c] = racc[n * 32 + c];
+                const float cl = q[4 * 33];
+                const float cq = q[5 * 33];
+                const double tau = __hiloint2double(__float_as_int(q[7 * 33]), __float_as_int(q[6 * 33]));
+                const int sx = __float_as_int(q[33]);
+                const bool diag = __float_as_int(q[2 * 33]) != 0;
+                const int oidx = __float_as_int(q[3 * 33]);
                 __syncwarp();
-                const float cl = __shfl_sync(0xffffffffu, m_cl, n);
-                const float cq = __shfl_sync(0xffffffffu, m_cq, n);
-                const double tau = __shfl_sync(0xffffffffu, m_tau, n);
-                const int sx = __shfl_sync(0xffffffffu, m_sx, n);
-                const bool diag = __shfl_sync(0xffffffffu, m_diag, n) != 0;
-                const int oidx = __shfl_sync(0xffffffffu, m_keepidx, n);
-                // linear term: each lane reads its own row (256 contiguous bytes)
+                // linear term: the old block is staged in S (coalesced row reads,
+                // rounded to FP32), then each lane takes its own row
                 if (sx >= 0 && cl != 0.f) {
-                    const double2 *gx = reinterpret_cast<const double2 *>(A.in_val + (size_t)sx * kPlaneElems + lane * 32);
+                    const double *gx = A.in_val + (size_t)sx * kPlaneElems;
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) S[r * 33 + lane] = (float)gx[r * 32 + lane];
+                    __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const double2 x2 = gx[c];
-                        acc[2 * c] = fmaf(cl, (float)x2.x, cq * acc[2 * c]);
-                        acc[2 * c + 1] = fmaf(cl, (float)x2.y, cq * acc[2 * c + 1]);
-                    }
+                    for (int c = 0; c < 32; ++c) acc[c] = fmaf(cl, S[lane * 33 + c], cq * acc[c]);
+                    __syncwarp();
                 } else {
 #pragma unroll
                     for (int c = 0; c < 32; ++c) acc[c] = cq * acc[c];
                 }
+                // lane l holds row l of the block; a diagonal block is
+                // symmetrised as (X + X^T) / 2
 #pragma unroll
                 for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
                 __syncwarp();
@@ -899,7 +929,7 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     int dev = 0, nsm = 0;
     RDM_CUDA_TRY(cudaGetDevice(&dev));
     RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t zero_elems = (size_t)nsm * 8 * 2 * kPlaneElems;   // 8 zero blocks (hi and lo) per CTA
+    const size_t zero_elems = (size_t)nsm * kSlots * 2 * kPlaneElems;   // a zero block (hi and lo) per CTA and slot
     if (!w.zero.p || w.zero.cap < zero_elems) {
         w.zero.ensure(zero_elems);
         RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, w.zero.cap * sizeof(uint16_t), st));
@@ -907,9 +937,9 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     TcArgs A{};
     A.planes = in.ophi.p; A.zero = w.zero.p;
     A.tiles = w.tiles.p; A.step_off = w.step_off.p; A.steps = w.steps.p; A.ntile = plan.ntile;
-    // kind::f16: D = F32 (bit 4), A/B = BF16 (1) or F16 (0), K-major, N = 128, M = 128
+    // kind::f16: D = F32 (bit 4), A/B = BF16 (1) or F16 (0), K-major, N = kTileN, M = 128
     const uint32_t ab = ar == AR_BF16X3 ? 1u : 0u;
-    A.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    A.idesc = (1u << 4) | (ab << 7) | (ab << 10) | (((uint32_t)kTileN >> 3) << 17) | ((128u >> 4) << 24);
     A.scale = w.scale.p;
     for (int p = 0; p < kMaxJobs; ++p) {
         A.job_a[p] = p < jt.njob ? jt.job[p].a[0] : 0;
@@ -930,13 +960,13 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     k_tc_bf16x3<<<grid, kThreads, kSmemBytes, st>>>(A);
     RDM_LAUNCH_CHECK();
     (void)NB;
-    return (double)plan.nsteps * 3.0 * 2.0 * 128.0 * 128.0 * 32.0;
+    return (double)plan.nsteps * 3.0 * 2.0 * 128.0 * kTileN * 32.0;
 }
 
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
                      const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st) {
     TcPlan plan{};
-    const int NB = in.NB, NB4 = (NB + TBL - 1) / TBL;
+    const int NB = in.NB, NB4 = (NB + TBM - 1) / TBM;
     const int nrow4 = unit1 - unit0;
     if (nrow4 <= 0) return plan;
     w.counters.ensure(8);
@@ -975,7 +1005,7 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     RDM_CUDA_TRY(cudaMemcpyAsync(&nsteps, w.step_off.p + ntile, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     RDM_CUDA_TRY(cudaStreamSynchronize(st));
     plan.nsteps = nsteps;
-    w.steps.ensure(std::max<int64_t>(nsteps, 1) * 8);
+    w.steps.ensure(std::max<int64_t>(nsteps, 1) * kSlots);
     T.step_off = w.step_off.p;
     T.steps = w.steps.p;
     k_set_nsteps<<<(ntile + 127) / 128, 128, 0, st>>>(w.tiles.p, w.step_cnt.p, ntile);

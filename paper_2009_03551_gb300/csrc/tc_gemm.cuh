@@ -7,12 +7,12 @@ namespace rdm {
 
 // work buffers of the tensor-core path (tile lists, per-tile K-step lists)
 struct TcWork {
-    DevBuf<uint16_t> zero;      // one zero operand plane
-    DevBuf<int> tiles;          // per tile: job, I, J, nsteps, slot[16]
+    DevBuf<uint16_t> zero;      // zero operand blocks: one per CTA and K-step slot
+    DevBuf<int> tiles;          // per tile: job, I, -, nsteps, mask slot[4 x 8], column j[8]
     DevBuf<int> tile_cnt, tile_off;
     DevBuf<int> step_cnt;
     DevBuf<int64_t> step_off;
-    DevBuf<int> steps;          // per K-step: 4 A block indices, 4 B block indices (-1 = zero)
+    DevBuf<int> steps;          // per K-step: 4 A block indices, 8 B block indices (-1 = zero)
     DevBuf<int> counters;       // [0]: error bits of the product kernel
     DevBuf<int> scan32;
     DevBuf<int64_t> scan64;
