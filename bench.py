@@ -47,11 +47,11 @@ FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.
 # whitespace removed, so that a comment edit keeps the figure and a code edit drops it)
 PROFILED_TRAFFIC = {
     "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
-           "sha256": "141b42fe2cbdc641a4628b7a0155da9db1a6e676ad91826add93b96c95ba4025",
-           "bytes_per_launch": 28362752526, "workload": WORKLOAD},
+           "sha256": "6a82385f0d0a5f5e14c70eba34567217d1377dd7c2340b3f90a7116d34ac1682",
+           "bytes_per_launch": 24744794482, "workload": WORKLOAD},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
            "sha256": "1c9d3e76e36659e5d06b0d237474522761ebecc2732c37eb20f037dc4adcb12e",
-           "bytes_per_launch": 10199553408, "workload": WORKLOAD},
+           "bytes_per_launch": 10398166912, "workload": WORKLOAD},
 }
 
 
