@@ -209,7 +209,6 @@ def cores():
 def run_reference(args, sys_, rank):
     if rank != 0:
         return
-    t_w = []
     for _ in range(args.warmup):
         oracle_sample(sys_)
     vals = []
@@ -226,7 +225,6 @@ def run_reference(args, sys_, rank):
                        "directions": 3},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    del t_w
     print(json.dumps(line), flush=True)
 
 
@@ -244,6 +242,31 @@ def to_device(sys_, torch, dev):
         o.row_ptr = torch.from_numpy(m.row_ptr).to(dev)
         o.col_idx = torch.from_numpy(m.col_idx).to(dev)
         o.vals = torch.from_numpy(m.vals).to(dev)
+        return o
+
+    class S:
+        pass
+
+    s = S()
+    s.h0 = conv(sys_.h0)
+    s.h1 = [conv(m) for m in sys_.h1]
+    s.dirs = sys_.dirs
+    s.n_electrons = sys_.n_electrons
+    return s
+
+
+def pinned_system(sys_, torch):
+    """The system with its matrices copied into pinned host memory (numpy
+    views of pinned torch tensors)."""
+    class M:
+        pass
+
+    def conv(m):
+        o = M()
+        o.nb, o.b, o.n = m.nb, m.b, m.n
+        o.row_ptr = torch.from_numpy(np.ascontiguousarray(m.row_ptr)).pin_memory().numpy()
+        o.col_idx = torch.from_numpy(np.ascontiguousarray(m.col_idx)).pin_memory().numpy()
+        o.vals = torch.from_numpy(np.ascontiguousarray(m.vals)).pin_memory().numpy()
         return o
 
     class S:
@@ -346,25 +369,36 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
                 "speedup_mixed_vs_fp64": t64 / s_per_solve}
         s64.close()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the inputs and the
+    # P1 outputs live in pinned host memory, allocated once before the timed
+    # region (as an application that solves repeatedly would keep them)
     e2e = None
     if args.e2e_steps > 0:
         h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for s in systems for m in [s.h0, *s.h1])
+        hsys = [pinned_system(s, torch) for s in systems]
         se = rdm.Solver(dev.index, stream.cuda_stream)
         se.set_params(**params)
-        se.load(systems)
+        se.load(hsys)
         se.solve()   # warm-up of the host path
         torch.cuda.synchronize()
+        outs = {}
+        for k in range(nsys):
+            for d in range(len(systems[k].h1)):
+                cap = rdm.rdm_get_p1_nnzb(se.h, k, d) * 11 // 10 + 16
+                nb, b = systems[k].h0.nb, systems[k].h0.b
+                outs[k, d] = (torch.empty(nb + 1, dtype=torch.int32, pin_memory=True).numpy(),
+                              torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy(),
+                              torch.empty(cap * b * b, dtype=torch.float64, pin_memory=True).numpy())
         d2h = 0
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
-            se.load(systems)
+            se.load(hsys)
             se.solve()
             d2h = 0
             for k in range(nsys):
                 d2h += 72
                 for d in range(len(systems[k].h1)):
-                    p = se.p1(k, d)
+                    p = se.p1(k, d, out=outs[k, d])
                     d2h += p.row_ptr.nbytes + p.col_idx.nbytes + p.vals.nbytes
                 _ = se.alpha(k)
         torch.cuda.synchronize()

@@ -117,7 +117,8 @@ typedef struct {
     int32_t max_iter;       /* iteration cap; reaching it returns RDM_NOT_CONVERGED */
     int32_t mode;           /* RDM_MODE_* */
     int32_t min_iter;       /* never stop before this many iterations */
-    int32_t use_graphs;     /* 1: capture the iteration in CUDA graphs when possible */
+    int32_t use_graphs;     /* reserved, must be 0 (else RDM_EINVAL): the iteration is not captured in
+                               CUDA graphs, since it takes host decisions (sizes, branch, tier) every step */
     int32_t verbose;        /* 1: per-iteration log to stderr */
     int32_t refine_x1;      /* mixed modes, final tier, arithmetic of the first-order products
                                (RDM_REFINE_*) */
@@ -199,7 +200,9 @@ const char *rdm_last_error(const rdm_handle *h);
  * stall_tol 0, spin 2, max_iter 100, mode FP64, min_iter 1, graphs 0. */
 int rdm_default_params(rdm_params *p);
 
-/* Set the solve parameters (validated: tau >= 0, max_iter >= 1, known mode). */
+/* Set the solve parameters.  Validated: tau >= 0, tol >= 0, max_iter >= 1, a
+ * known mode, refine_x1 in 0..4, refine_x0 in {0, 1, 3, 4}, chunk_mb >= 0,
+ * use_graphs == 0; anything else returns RDM_EINVAL and keeps the old set. */
 int rdm_set_params(rdm_handle *h, const rdm_params *p);
 
 /* ---- problem definition ------------------------------------------------ */

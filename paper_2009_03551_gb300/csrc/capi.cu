@@ -1161,9 +1161,10 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
     if (!p) return fail(h, RDM_EINVAL, "null params");
     if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 3 ||
         !(p->spin_factor > 0) || p->min_iter < 0 || p->refine_x1 < 0 || p->refine_x1 > 4 ||
-        p->refine_x0 < 0 || p->refine_x0 > 4 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0)
+        p->refine_x0 < 0 || p->refine_x0 > 4 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
+        p->use_graphs != 0)
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
-                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0)");
+                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0, use_graphs 0)");
     h->prm = *p;
     return RDM_OK;
 }

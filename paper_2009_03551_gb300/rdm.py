@@ -253,16 +253,29 @@ class BsrResult:
         return a if padded else a[: self.n, : self.n]
 
 
-def _fetch(h, getter, *idx) -> BsrResult:
+def _fetch(h, getter, *idx, out=None) -> BsrResult:
+    """Size query, then one copy into host arrays: fresh ones, or the
+    caller's ``out = (row_ptr, col_idx, vals)`` (e.g. views of pinned
+    memory reused across solves; C-contiguous int32 / int32 / float64, with
+    room for nb + 1, nnzb and nnzb*b*b entries).  The result's arrays are
+    views of exactly nb + 1, nnzb and (nnzb, b, b) entries."""
     q = rdm_bsr_out()                      # size query (row_ptr = NULL)
     _check(h, getter(h, *idx, C.byref(q)))
     nb, b, nnz = int(q.nb), int(q.b), int(q.nnzb)
-    rp = np.zeros(nb + 1, dtype=np.int32)
-    ci = np.zeros(max(nnz, 1), dtype=np.int32)
-    va = np.zeros((max(nnz, 1), b, b), dtype=np.float64)
-    out = rdm_bsr_out(nb, b, 0, nnz, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
-    _check(h, getter(h, *idx, C.byref(out)))
-    return BsrResult(nb, b, int(out.n), rp, ci[:nnz].copy(), va[:nnz].copy())
+    if out is None:
+        rp = np.empty(nb + 1, dtype=np.int32)
+        ci = np.empty(max(nnz, 1), dtype=np.int32)
+        va = np.empty((max(nnz, 1), b, b), dtype=np.float64)
+    else:
+        rp, ci, va = out
+        for a, dt, need in ((rp, np.int32, nb + 1), (ci, np.int32, nnz), (va, np.float64, nnz * b * b)):
+            if a.dtype != dt or not a.flags.c_contiguous or a.size < need:
+                raise ValueError(f"output buffer: need a C-contiguous {np.dtype(dt).name} array of "
+                                 f">= {need} elements")
+        va = va.reshape(-1)[: max(nnz, 1) * b * b].reshape(max(nnz, 1), b, b) if va.size else va
+    o = rdm_bsr_out(nb, b, 0, nnz, rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+    _check(h, getter(h, *idx, C.byref(o)))
+    return BsrResult(nb, b, int(o.n), rp[: nb + 1], ci[:nnz], va[:nnz])
 
 
 def rdm_get_p0_nnzb(h, sys: int = 0) -> int:
@@ -277,12 +290,12 @@ def rdm_get_p1_nnzb(h, sys: int = 0, direction: int = 0) -> int:
     return int(n.value)
 
 
-def rdm_get_p0(h, sys: int = 0) -> BsrResult:
-    return _fetch(h, _lib.rdm_get_p0, sys)
+def rdm_get_p0(h, sys: int = 0, out=None) -> BsrResult:
+    return _fetch(h, _lib.rdm_get_p0, sys, out=out)
 
 
-def rdm_get_p1(h, sys: int = 0, direction: int = 0) -> BsrResult:
-    return _fetch(h, _lib.rdm_get_p1, sys, direction)
+def rdm_get_p1(h, sys: int = 0, direction: int = 0, out=None) -> BsrResult:
+    return _fetch(h, _lib.rdm_get_p1, sys, direction, out=out)
 
 
 def rdm_get_alpha(h, sys: int = 0) -> np.ndarray:
@@ -390,11 +403,11 @@ class Solver:
         code, info = rdm_solve(self.h)
         return code, info
 
-    def p0(self, sys: int = 0) -> BsrResult:
-        return rdm_get_p0(self.h, sys)
+    def p0(self, sys: int = 0, out=None) -> BsrResult:
+        return rdm_get_p0(self.h, sys, out=out)
 
-    def p1(self, sys: int = 0, direction: int = 0) -> BsrResult:
-        return rdm_get_p1(self.h, sys, direction)
+    def p1(self, sys: int = 0, direction: int = 0, out=None) -> BsrResult:
+        return rdm_get_p1(self.h, sys, direction, out=out)
 
     def alpha(self, sys: int = 0) -> np.ndarray:
         return rdm_get_alpha(self.h, sys)

@@ -98,3 +98,48 @@ def test_null_handle_is_rejected(rdm):
     assert rdm._lib.rdm_default_params(None) == rdm.RDM_EINVAL
     n = C.c_int()
     assert rdm._lib.rdm_get_log(None, None, 0, C.byref(n)) == rdm.RDM_EINVAL
+
+
+def _fake_getter(rdm, nb, b, nnz):
+    """A stand-in for rdm_get_p0/p1 that follows the C contract (size query
+    with row_ptr == NULL, then a copy into the caller's buffers)."""
+    import ctypes as C
+    import numpy as np
+
+    def getter(h, *args):
+        out = C.cast(args[-1], C.POINTER(rdm.rdm_bsr_out)).contents
+        if not out.row_ptr:
+            out.nb, out.b, out.n, out.nnzb = nb, b, nb * b, nnz
+            return 0
+        assert out.nnzb >= nnz
+        def view(addr, ctype, n):
+            return np.ctypeslib.as_array(C.cast(addr, C.POINTER(ctype)), shape=(n,))
+        view(out.row_ptr, C.c_int32, nb + 1)[:] = np.linspace(0, nnz, nb + 1).astype(np.int32)
+        if nnz:
+            view(out.col_idx, C.c_int32, nnz)[:] = np.arange(nnz) % nb
+            view(out.vals, C.c_double, nnz * b * b)[:] = np.arange(nnz * b * b)
+        out.n = nb * b
+        return 0
+    return getter
+
+
+def test_getter_fills_fresh_or_caller_buffers(rdm):
+    """The binding's getters copy once: into fresh arrays, or into the
+    caller's (e.g. pinned) buffers, returning views of exactly the result."""
+    import numpy as np
+    nb, b, nnz = 5, 4, 7
+    g = _fake_getter(rdm, nb, b, nnz)
+    r = rdm._fetch(None, g, 0)
+    assert r.row_ptr.shape == (nb + 1,) and r.col_idx.shape == (nnz,) and r.vals.shape == (nnz, b, b)
+    assert np.array_equal(r.vals.reshape(-1), np.arange(nnz * b * b))
+    bufs = (np.zeros(nb + 1, np.int32), np.zeros(nnz + 3, np.int32), np.zeros((nnz + 3) * b * b))
+    r2 = rdm._fetch(None, g, 0, out=bufs)
+    assert np.shares_memory(r2.vals, bufs[2]) and np.shares_memory(r2.col_idx, bufs[1])
+    assert r2.vals.shape == (nnz, b, b) and np.array_equal(r2.vals, r.vals)
+    assert np.array_equal(r2.col_idx, r.col_idx) and np.array_equal(r2.row_ptr, r.row_ptr)
+    with pytest.raises(ValueError):
+        rdm._fetch(None, g, 0, out=(bufs[0], bufs[1][: nnz - 1], bufs[2]))
+    with pytest.raises(ValueError):
+        rdm._fetch(None, g, 0, out=(bufs[0], bufs[1], bufs[2].astype(np.float32)))
+    empty = rdm._fetch(None, _fake_getter(rdm, nb, b, 0), 0)
+    assert empty.col_idx.shape == (0,) and empty.vals.shape == (0, b, b)

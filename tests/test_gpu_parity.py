@@ -299,6 +299,11 @@ def test_bad_inputs_are_rejected(rdm):
         with pytest.raises(rdm.RdmError) as e:
             rdm.rdm_get_alpha(h, 0)                   # no solve yet
         assert e.value.code == rdm.RDM_ESTATE
+        p = rdm.rdm_default_params()
+        p.use_graphs = 1                              # reserved: graph capture is not implemented
+        with pytest.raises(rdm.RdmError) as e:
+            rdm.rdm_set_params(h, p)
+        assert e.value.code == rdm.RDM_EINVAL
     finally:
         rdm.rdm_destroy(h)
 
