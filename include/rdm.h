@@ -125,9 +125,10 @@ typedef struct {
     int32_t symbolic_hash;  /* 1: use the hash-table symbolic phase (otherwise chosen only for
                                systems above 8,192 block rows); results are identical */
     int32_t chunk_mb;       /* cap in MiB on the buffer of untruncated product blocks (8 b^2 + 5
-                               bytes per block); the jobs of a step (X0^2, each X1 product) are
-                               then multiplied in groups of consecutive jobs that fit it (at
-                               least one job per group).  0: automatic, from the free device
+                               bytes per upper-triangle block); the products of a step (X0^2,
+                               each X1 product) are then computed in groups of consecutive
+                               super-rows (4 block rows of one product) that fit it (at least
+                               one super-row per group).  0: automatic, from the free device
                                memory.  Results do not depend on the grouping. */
     int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT
                                (RDM_REFINE_FP32X2 for RDM_MODE_MIXED_FP16, RDM_REFINE_FP64 for
@@ -167,7 +168,7 @@ typedef struct {
                                blocks written (8 bytes/element) */
     int64_t device_bytes_peak; /* largest device memory held by the library's buffers during
                                   the solve (all handles of the process) */
-    int32_t product_groups;    /* most job groups a step of the solve was split into (chunk_mb) */
+    int32_t product_groups;    /* most super-row groups a step of the solve was split into (chunk_mb) */
     int32_t pad0;
 } rdm_info;
 
