@@ -206,7 +206,7 @@ def cores():
         return os.cpu_count() or 1
 
 
-def run_reference(args, sys_, rank):
+def run_reference(args, sys_, rank, wname):
     if rank != 0:
         return
     for _ in range(args.warmup):
@@ -221,8 +221,8 @@ def run_reference(args, sys_, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "atoms": args.atoms, "N": sys_.n, "b": sys_.b, "tau": 1e-6,
-                       "directions": 3},
+            "config": {"workload": wname, "atoms": sys_.n_atoms, "N": sys_.n, "b": sys_.b, "tau": args.tau,
+                       "directions": len(sys_.h1)},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -493,7 +493,7 @@ def main():
     sys_ = systems[0]
 
     if args.impl == "reference":
-        run_reference(args, sys_, rank)
+        run_reference(args, sys_, rank, wname)
         return
 
     import torch

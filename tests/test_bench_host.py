@@ -29,3 +29,23 @@ def test_code_edits_change_the_digest():
 def test_recorded_traffic_only_for_its_workload():
     assert bench.profiled_traffic("tc", "some other workload") is None
     assert bench.profiled_traffic("no such class", bench.WORKLOAD) is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the CPU oracle (no GPU needed) and
+    prints one JSON line with the keys the benchmark contract asks for."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--atoms", "60", "--steps", "1",
+                        "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "s" and line["value"] > 0
+    assert line["higher_is_better"] is False and line["steps"] == 1 and line["warmup"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("cluster-60-atoms") and line["config"]["atoms"] == 60
