@@ -65,7 +65,7 @@ constexpr int TBM = 4;                       // block rows per super-tile (MMA M
 constexpr int TBN = 8;                       // block columns per super-tile
 constexpr int kTileN = TBN * TB;             // MMA N = accumulator columns in tensor memory
 constexpr int kSlots = TBM + TBN;            // operand blocks per K-step: A rows, then B rows
-constexpr int kStages = TBN == 8 ? 4 : 7;    // ring stages (all but a few KB of shared memory)
+constexpr int kStages = TBN == 8 ? 4 : 7;    // ring stages: 4 x 48 KB beside the epilogue staging (fit checked below)
 constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
 constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
 constexpr int kPairBytes = 2 * kPlaneBytes;  // hi and lo planes of one block, interleaved: 4 KB
