@@ -2,17 +2,24 @@
 
 One step = one full solve (Gershgorin bounds, initial matrices, every TC2 /
 first-order iteration with its block-sparse products and truncation, the
-polarizability) of the 2,000-atom random-packed cluster (8 orbitals per atom,
-N = 16,000, 32 x 32 blocks, truncation 1e-6, H1 for x, y and z).  Inputs are
-resident in HBM before the timed region; the working set (X0, X1 for three
-directions, ~1 GB in FP64) is far larger than L2, so no flush is needed.
+polarizability) of the default workload: a batch of 24 independent systems of
+uneven size (300-8,000 atoms each, 84,131 atoms in all, 8 orbitals per atom,
+chains and random-packed clusters, 32 x 32 blocks, truncation 1e-6, H1 for x,
+y and z), solved together as one block-diagonal problem in the mixed
+fp16 / FP64 ladder.  Inputs are resident in HBM before the timed region; the
+working set (hundreds of GB) is far larger than L2, so no flush is needed.
+The plain FP64 GPU solve of the same workload runs once beside it, and
+|dalpha|/alpha is measured between the two.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode M] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode M] [--workload W] [--impl ours|reference]
 
-Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
-copy of the workload (independent problems, weak scaling, no collective on
-the data path).  ``--impl reference`` times the CPU oracle (dense FP64 TC2)
-on a bounded sample of the same workload.
+Prints ONE JSON line (rank 0).  Under torchrun a batch is partitioned: every
+rank solves the systems that a greedy work estimate assigns to it (no
+collective on the data path; the polarizabilities are gathered afterwards),
+so the job's total work is fixed (strong scaling); a single-system workload
+runs one replica per rank (weak scaling).  ``--impl reference`` times the CPU
+oracle (dense FP64 TC2, oracle B) end to end on a bounded sample of the
+workload: a carve-out of one of its clusters.
 """
 
 from __future__ import annotations
@@ -32,26 +39,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "s per P1 solve (block-SpGEMM TFLOP/s alongside), FP64 vs mixed, at |dalpha|/alpha <= 1e-6"
-WORKLOAD = "cluster-2000-atoms-N16000-b32-tau1e-6-xyz"
-# TC2 iterations of the oracle's stopping rule on this workload, predicted by
-# tests/golden/make_golden.py from the spectrum of H0 (oracle only)
-ORACLE_ITERS_FILE = os.path.join(ROOT, "tests", "golden", "cfg2_oracle.json")
 FP64_PEAK_NOTE = ("GB300 FP64: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
                   "(nominal 1.25 TFLOP/s)")
 FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.5 TFLOP/s"
+DENSE_MAX_N = 16000       # largest system the dense CPU oracle may be given (N x N FP64: 2 GB)
+SAMPLE_ATOMS = 250        # atoms of the carve-out the CPU oracle solves (N = 2,000)
+# MMA work of one K-step of the tensor-core kernel: 3 products of 128 x 256 x 32
+TC_FLOPS_PER_KSTEP = 3 * 2 * 128 * 256 * 32
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged
-# over the launches of one solve) of the product kernels on the 2,000-atom
-# cluster, from one ncu capture (profiles/); reported only while the code of the
-# kernel's source file is unchanged since (SHA-256 of the file with comments and
-# whitespace removed, so that a comment edit keeps the figure and a code edit drops it)
+# DRAM traffic of the product kernels, from one ncu capture each (profiles/):
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, divided by the work
+# units of that launch (K-steps for the tensor-core kernel, block triples for
+# the CUDA-core kernels), so that a capture on a small case scales to the
+# launches of the bench workload by the units they process.  A figure is
+# reported only while the code of the kernel's source file is unchanged since
+# the capture (SHA-256 of the file with comments and whitespace removed).
 PROFILED_TRAFFIC = {
     "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
            "sha256": "6a82385f0d0a5f5e14c70eba34567217d1377dd7c2340b3f90a7116d34ac1682",
-           "bytes_per_launch": 24744794482, "workload": WORKLOAD},
+           "bytes_per_unit": None, "unit": "K-step"},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
            "sha256": "1c9d3e76e36659e5d06b0d237474522761ebecc2732c37eb20f037dc4adcb12e",
-           "bytes_per_launch": 10398166912, "workload": WORKLOAD},
+           "bytes_per_unit": None, "unit": "block triple"},
 }
 
 
@@ -64,9 +73,9 @@ def parse():
     ap.add_argument("--mode", default=os.environ.get("RDM_BENCH_MODE", "mixed_fp16"),
                     choices=["fp64", "fp32", "mixed_bf16", "mixed_fp16"])
     ap.add_argument("--atoms", type=int, default=2000, help="atoms of the cluster workload")
-    ap.add_argument("--workload", default="cluster",
-                    help="cluster (default: the 2,000-atom cluster, or --atoms), batch24 (24 uneven "
-                         "chains/clusters, 300-8,000 atoms), slab<N> (30-bohr slab of N atoms)")
+    ap.add_argument("--workload", default="batch24",
+                    help="batch24 (default: 24 uneven chains/clusters, 300-8,000 atoms, 84,131 in all), "
+                         "cluster (the 2,000-atom cluster, or --atoms), slab<N> (30-bohr slab of N atoms)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -74,21 +83,25 @@ def parse():
     ap.add_argument("--tau-refine", type=float, default=-1.0,
                     help="threshold of the final (FP64/FP32) tier of the mixed modes (< 0: --tau); the "
                          "FP64 comparison solve runs at this threshold throughout")
+    ap.add_argument("--sweep", default="",
+                    help="tau or tol: instead of the timed solve, sweep the truncation threshold (or the "
+                         "band-energy tolerance) on --workload and print one JSON line per point")
     return ap.parse_args()
 
 
-def profiled_traffic(cls, workload):
-    """Bytes per launch of the class's kernel from the committed capture, or None."""
-    import hashlib
+def profiled_traffic(cls, units_per_launch):
+    """DRAM bytes per launch of the class's kernel, scaled from the committed
+    capture by the units the launch processes; None if there is no capture of
+    the current code."""
     rec = PROFILED_TRAFFIC.get(cls)
-    if rec is None or rec["workload"] != workload:
+    if rec is None or rec["bytes_per_unit"] is None or not units_per_launch:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["file"])
     try:
         sha = code_sha256(path)
     except OSError:
         return None
-    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+    return rec["bytes_per_unit"] * units_per_launch if sha == rec["sha256"] else None
 
 
 def code_sha256(path):
@@ -171,34 +184,6 @@ class ClockSampler:
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_iterations():
-    try:
-        with open(ORACLE_ITERS_FILE) as f:
-            return int(json.load(f)["tc2_iterations"])
-    except Exception:
-        return 17
-
-
-def oracle_sample(sys_, reps: int = 1):
-    """Time the oracle's dominant operation on this workload: one dense FP64
-    product X0 X0 of the full N x N matrix (numpy / threaded BLAS), then scale
-    to one solve = (1 + 2 * n_dirs) products per iteration x iterations."""
-    from oracle.tc2 import gershgorin_bounds
-    h0 = sys_.h0.to_dense()
-    lo, hi = gershgorin_bounds(h0)
-    x0 = (hi * np.eye(h0.shape[0]) - h0) / (hi - lo)
-    del h0
-    times = []
-    for _ in range(reps):
-        t = time.perf_counter()
-        _ = x0 @ x0
-        times.append(time.perf_counter() - t)
-    iters = oracle_iterations()
-    per_product = min(times)
-    n_prod = 1 + 2 * len(sys_.h1)
-    return per_product, per_product * n_prod * iters, iters, n_prod
-
-
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -206,31 +191,139 @@ def cores():
         return os.cpu_count() or 1
 
 
-def run_reference(args, sys_, rank, wname):
+def dense(m):
+    """Dense copy of a BSR matrix for the CPU oracle; refuses systems whose
+    dense form would not fit comfortably in host memory."""
+    if m.n > DENSE_MAX_N:
+        raise ValueError(f"dense oracle refused: N = {m.n} > {DENSE_MAX_N}")
+    return m.to_dense()
+
+
+def oracle_sample_system(systems):
+    """The bounded sample the CPU oracle solves: the SAMPLE_ATOMS atoms nearest
+    the centre of the smallest cluster of the workload (of its first system if
+    it has no cluster), with the same matrix elements (synth.carve_sphere)."""
+    from synth import carve_sphere
+    clusters = [k for k, s in enumerate(systems) if s.kind != "chain"] or [0]
+    k = min(clusters, key=lambda i: systems[i].n_atoms)
+    parent = systems[k]
+    n_keep = min(SAMPLE_ATOMS, parent.n_atoms)
+    s = carve_sphere(parent, n_keep) if n_keep < parent.n_atoms else parent
+    desc = (f"oracle B (dense FP64 TC2 with the first-order recursion for x, y, z, block truncation, band-energy "
+            f"stop) solved end to end on the {n_keep} atoms nearest the centre of system {k} of the workload "
+            f"({parent.kind}, {parent.n_atoms} atoms): N = {s.n}, b = {s.b}")
+    return s, k, desc
+
+
+def timed_oracle_solve(sample, tau, tol=1e-9):
+    """Wall time of one full oracle-B solve of the sample (dense FP64, numpy
+    with the host's threaded BLAS), and its iteration count."""
+    from oracle import tc2_response
+    h0 = dense(sample.h0)
+    h1s = [dense(m) for m in sample.h1]
+    t = time.perf_counter()
+    r = tc2_response(h0, h1s, sample.n_occ, sample.b, tau=tau, tol=tol, max_iter=100)
+    return time.perf_counter() - t, r.iterations
+
+
+def dense_cost_model(t_sample, sample, systems):
+    """Context only: the sample's time scaled to the whole workload by the
+    dense oracle's N^3 cost (iteration counts assumed equal)."""
+    return t_sample * sum((s.n / sample.n) ** 3 for s in systems)
+
+
+def run_reference(args, systems, rank, wname):
     if rank != 0:
         return
+    sample, k, desc = oracle_sample_system(systems)
     for _ in range(args.warmup):
-        oracle_sample(sys_)
-    vals = []
+        timed_oracle_solve(sample, args.tau)
+    vals, iters = [], 0
     for _ in range(args.steps):
-        per_prod, per_solve, iters, n_prod = oracle_sample(sys_)
-        vals.append(per_solve)
+        t, iters = timed_oracle_solve(sample, args.tau)
+        vals.append(t)
     v = float(np.mean(vals))
-    sample = (f"one dense FP64 {sys_.n}x{sys_.n} product X0*X0 per step (numpy, threaded BLAS), "
-              f"scaled by {n_prod} products/iteration x {iters} iterations")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "higher_is_better": False,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "atoms": sys_.n_atoms, "N": sys_.n, "b": sys_.b, "tau": args.tau,
-                       "directions": len(sys_.h1)},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": cores(), "kind": "oracle", "sample": sample},
+            "config": {"workload": wname, "systems": len(systems),
+                       "atoms": int(sum(s.n_atoms for s in systems)), "b": systems[0].b, "tau": args.tau,
+                       "directions": len(systems[0].h1),
+                       "sample": {"system": k, "atoms": sample.n_atoms, "N": sample.n, "iterations": iters}},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores(), "kind": "oracle",
+                             "sample": desc + f"; one such solve per step ({iters} iterations)"},
+            "scaled_to_workload": {"kind": "model", "value": dense_cost_model(v, sample, systems), "unit": "s",
+                                   "basis": "the timed sample scaled by the dense N^3 cost to every system of "
+                                            "the workload (not measured)"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
+# partition of a batch over ranks
+# ---------------------------------------------------------------------------
+
+def work_estimate(s):
+    """Cost proxy of one system's solve: the block triples of H0 H0
+    (sum over block rows of the squared blocks per row)."""
+    rp = np.asarray(s.h0.row_ptr, dtype=np.int64)
+    k = np.diff(rp)
+    return float(np.sum(k * k))
+
+
+def partition(works, world):
+    """Greedy longest-processing-time partition: systems in decreasing order
+    of work, each to the rank with the least work so far (ties: lowest rank).
+    Returns, per rank, the sorted indices of its systems."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(works)), key=lambda i: (-works[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += works[i]
+    return [sorted(x) for x in out]
+
+
+def gather_results(local, world, dist):
+    """{system index: result} of every rank, merged (all ranks get the merge)."""
+    if dist is None or world == 1:
+        return dict(local)
+    parts = [None] * world
+    dist.all_gather_object(parts, dict(local))
+    merged = {}
+    for p in parts:
+        merged.update(p)
+    return merged
+
+
+def job_seconds_per_solve(t_local, steps, world, dist, torch, device, replicas=True):
+    """Whole-job time per solve: the slowest rank's timed region divided by
+    the solves of the whole workload that all ranks completed (with replicas
+    every rank completes `steps` solves; with a partition the ranks together
+    complete `steps` solves of the one workload)."""
+    t = t_local
+    if dist is not None:
+        x = torch.tensor([t_local], device=device, dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t / (steps * (world if replicas else 1))
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def _copy_system(sys_, conv):
+    class S:
+        pass
+
+    s = S()
+    s.h0 = conv(sys_.h0)
+    s.h1 = [conv(m) for m in sys_.h1]
+    s.dirs = sys_.dirs
+    s.n_electrons = sys_.n_electrons
+    return s
+
 
 def to_device(sys_, torch, dev):
     class M:
@@ -244,15 +337,7 @@ def to_device(sys_, torch, dev):
         o.vals = torch.from_numpy(m.vals).to(dev)
         return o
 
-    class S:
-        pass
-
-    s = S()
-    s.h0 = conv(sys_.h0)
-    s.h1 = [conv(m) for m in sys_.h1]
-    s.dirs = sys_.dirs
-    s.n_electrons = sys_.n_electrons
-    return s
+    return _copy_system(sys_, conv)
 
 
 def pinned_system(sys_, torch):
@@ -269,31 +354,16 @@ def pinned_system(sys_, torch):
         o.vals = torch.from_numpy(np.ascontiguousarray(m.vals)).pin_memory().numpy()
         return o
 
-    class S:
-        pass
-
-    s = S()
-    s.h0 = conv(sys_.h0)
-    s.h1 = [conv(m) for m in sys_.h1]
-    s.dirs = sys_.dirs
-    s.n_electrons = sys_.n_electrons
-    return s
-
-
-def job_seconds_per_solve(t_local, steps, world, dist, torch, device):
-    """Whole-job time per solve: the slowest rank's timed region (every rank
-    solves its own replica of the workload, `steps` times) divided by the
-    solves all ranks completed."""
-    t = t_local
-    if dist is not None:
-        x = torch.tensor([t_local], device=device, dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        t = float(x.item())
-    return t / (steps * world)
+    return _copy_system(sys_, conv)
 
 
 def alphas(sol, nsys):
     return np.stack([sol.alpha(k) for k in range(nsys)])
+
+
+def rel_alpha_diff(a, b):
+    """Largest |a - b| over the 3 x 3 tensor, relative to max |b|, worst over systems."""
+    return float(max(np.max(np.abs(a[k] - b[k])) / np.max(np.abs(b[k])) for k in range(len(b))))
 
 
 def run_ours(args, systems, wname, rank, world, torch, dist):
@@ -302,18 +372,26 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    nsys = len(systems)
+    # a batch is partitioned over the ranks; a single system is replicated
+    replicas = len(systems) == 1 or world == 1
+    if replicas:
+        mine = list(range(len(systems)))
+    else:
+        mine = partition([work_estimate(s) for s in systems], world)[rank]
+    local = [systems[k] for k in mine]
+    nsys = len(local)
     sys_ = systems[0]
-    dsys = [to_device(s, torch, dev) for s in systems]
+    dsys = [to_device(s, torch, dev) for s in local]
     torch.cuda.synchronize()
 
     sol = rdm.Solver(dev.index, stream.cuda_stream)
     params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100)
     tau64 = args.tau_refine if args.tau_refine > 0 else args.tau
     sol.set_params(**params)
-    sol.load(dsys)
-    for _ in range(args.warmup):
-        sol.solve()
+    if nsys:
+        sol.load(dsys)
+        for _ in range(args.warmup):
+            sol.solve()
 
     def barrier():
         if dist is not None:
@@ -328,7 +406,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     infos = []
-    for _ in range(args.steps):
+    for _ in range(args.steps if nsys else 0):
         code, info = sol.solve()
         infos.append(info)
     e1.record(stream)
@@ -336,12 +414,15 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    s_per_solve = job_seconds_per_solve(ms / 1e3, args.steps, world, dist, torch, dev)
-    alpha_m = alphas(sol, nsys)
+    s_per_solve = job_seconds_per_solve(ms / 1e3, args.steps, world, dist, torch, dev, replicas)
+    alpha_m = alphas(sol, nsys) if nsys else np.zeros((0, 3, 3))
+    infos = infos or [rdm.rdm_info()]
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
+    issued = float(np.mean([i.issued_flops for i in infos]))
     kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(7)]
     kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(4)]
+    tc_launches = float(np.mean([i.tc_launches for i in infos]))
     launches = int(sum(i.kernel_launches for i in infos))
     sinfo = [sol.info(k) for k in range(nsys)]
     sol.close()   # frees the device buffers before the comparison solves
@@ -349,60 +430,74 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     # FP64 comparison solve (context for the metric's "FP64 vs mixed")
     fp64 = None
     if not args.no_fp64 and args.mode != "fp64":
-        s64 = rdm.Solver(dev.index, stream.cuda_stream)
-        s64.set_params(tau=tau64, tol=1e-9, mode="fp64", max_iter=100)
-        s64.load(dsys)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        _, i64 = s64.solve()
-        a1.record(stream)
-        torch.cuda.synchronize()
-        t64 = a0.elapsed_time(a1) / 1e3
-        alpha64 = alphas(s64, nsys)
-        # largest relative alpha error over the systems (each normalised by its own max |alpha|)
-        rel = float(max(np.max(np.abs(alpha_m[k] - alpha64[k])) / np.max(np.abs(alpha64[k]))
-                        for k in range(nsys)))
-        fp64 = {"s_per_solve": t64, "steps": 1, "warmup": 0, "iterations": i64.iterations,
-                "tflops": i64.useful_flops / t64 / 1e12, "alpha_rel_diff_mixed_vs_fp64": rel,
+        t64, it64, fl64 = 0.0, 0, 0.0
+        alpha64 = np.zeros((0, 3, 3))
+        if nsys:
+            s64 = rdm.Solver(dev.index, stream.cuda_stream)
+            s64.set_params(tau=tau64, tol=1e-9, mode="fp64", max_iter=100)
+            s64.load(dsys)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            _, i64 = s64.solve()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t64 = a0.elapsed_time(a1) / 1e3
+            it64, fl64 = i64.iterations, i64.useful_flops
+            alpha64 = alphas(s64, nsys)
+            s64.close()
+        t64 = job_seconds_per_solve(t64, 1, world, dist, torch, dev, replicas=False)
+        a_m = gather_results({k: alpha_m[q] for q, k in enumerate(mine)}, world, dist)
+        a_64 = gather_results({k: alpha64[q] for q, k in enumerate(mine)}, world, dist)
+        ks = sorted(a_64)
+        fp64 = {"s_per_solve": t64, "steps": 1, "warmup": 0, "iterations": it64,
+                "tflops": fl64 / t64 / 1e12 if t64 > 0 and world == 1 else None,
+                "alpha_rel_diff_mixed_vs_fp64": rel_alpha_diff([a_m[k] for k in ks], [a_64[k] for k in ks]),
                 "speedup_mixed_vs_fp64": t64 / s_per_solve}
-        s64.close()
 
     # end to end through the public API with host buffers: the inputs and the
     # P1 outputs live in pinned host memory, allocated once before the timed
     # region (as an application that solves repeatedly would keep them)
     e2e = None
     if args.e2e_steps > 0:
-        h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for s in systems for m in [s.h0, *s.h1])
-        hsys = [pinned_system(s, torch) for s in systems]
+        h2d = sum(m.row_ptr.nbytes + m.col_idx.nbytes + m.vals.nbytes for s in local for m in [s.h0, *s.h1])
+        hsys = [pinned_system(s, torch) for s in local]
         se = rdm.Solver(dev.index, stream.cuda_stream)
         se.set_params(**params)
-        se.load(hsys)
-        se.solve()   # warm-up of the host path
-        torch.cuda.synchronize()
         outs = {}
-        for k in range(nsys):
-            for d in range(len(systems[k].h1)):
-                cap = rdm.rdm_get_p1_nnzb(se.h, k, d) * 11 // 10 + 16
-                nb, b = systems[k].h0.nb, systems[k].h0.b
-                outs[k, d] = (torch.empty(nb + 1, dtype=torch.int32, pin_memory=True).numpy(),
-                              torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy(),
-                              torch.empty(cap * b * b, dtype=torch.float64, pin_memory=True).numpy())
+        if nsys:
+            se.load(hsys)
+            se.solve()   # warm-up of the host path
+            torch.cuda.synchronize()
+            for k in range(nsys):
+                for d in range(len(local[k].h1)):
+                    cap = rdm.rdm_get_p1_nnzb(se.h, k, d) * 11 // 10 + 16
+                    nb, b = local[k].h0.nb, local[k].h0.b
+                    outs[k, d] = (torch.empty(nb + 1, dtype=torch.int32, pin_memory=True).numpy(),
+                                  torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy(),
+                                  torch.empty(cap * b * b, dtype=torch.float64, pin_memory=True).numpy())
+        barrier()
         d2h = 0
         t = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(args.e2e_steps if nsys else 0):
             se.load(hsys)
             se.solve()
             d2h = 0
             for k in range(nsys):
                 d2h += 72
-                for d in range(len(systems[k].h1)):
+                for d in range(len(local[k].h1)):
                     p = se.p1(k, d, out=outs[k, d])
                     d2h += p.row_ptr.nbytes + p.col_idx.nbytes + p.vals.nbytes
                 _ = se.alpha(k)
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t) / args.e2e_steps
+        te = job_seconds_per_solve((time.perf_counter() - t), args.e2e_steps, world, dist, torch, dev, replicas)
+        if dist is not None:
+            x = torch.tensor([float(h2d), float(d2h)], device=dev, dtype=torch.float64)
+            dist.all_reduce(x)
+            h2d, d2h = x.tolist()
+            if replicas:
+                h2d, d2h = h2d / world, d2h / world
         e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         se.close()
 
@@ -411,6 +506,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     # dominant kernel of the solve (by device time) among the product kernels:
     # tensor-core split products, FP64, FP32 and double-FP32 CUDA-core products
     tc_ms, f64_ms, f32_ms, ff_ms = kms[1], kms[2], kms[3], kms[6]
+    issued_tc = max(0.0, issued - (kfl[1] + kfl[2] + kfl[3]))
+    ksteps_per_launch = issued_tc / TC_FLOPS_PER_KSTEP / tc_launches if tc_launches else 0.0
     classes = {
         "tc": ("k_tc_bf16x3 (tcgen05 split-precision block SpGEMM + fused truncation)", tc_ms, kfl[0],
                peaks["bf16_tflops"] * 1e12 / 3.0, "tensor",
@@ -427,10 +524,12 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     dom = max(classes, key=lambda k: classes[k][1])
     kname, k_ms, k_fl, peak, bound, peak_note = classes[dom]
     achieved = k_fl / (k_ms / 1e3) if k_ms > 0 else 0.0
+    traffic = profiled_traffic("tc", ksteps_per_launch) if dom == "tc" else None
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                "traffic": profiled_traffic(dom, wname),
+                "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
                 "ms_per_solve": k_ms, "peak_source": peak_note, "share_of_solve": k_ms / (s_per_solve * 1e3),
+                "launches_per_solve": tc_launches if dom == "tc" else None,
+                "ksteps_per_launch": ksteps_per_launch if dom == "tc" else None,
                 "per_class": {k: {"ms": v[1], "tflops": (v[2] / (v[1] / 1e3) / 1e12) if v[1] > 0 else None,
                                   "frac": ((v[2] / (v[1] / 1e3)) / v[3]) if v[1] > 0 else None}
                               for k, v in classes.items() if v[2] > 0}}
@@ -439,21 +538,23 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
 
     line = {"metric": METRIC, "value": s_per_solve, "unit": "s", "higher_is_better": False,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_per_solve * 1e3,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed_bf16": "bf16x3+f64",
-                                                                "mixed_fp16": "fp16x3+f64"}[mode],
+            "scaling": "weak" if replicas else "strong", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed_bf16": "bf16x3+f64", "mixed_fp16": "fp16x3+f64"}[mode],
             "data": "synthetic",
-            "config": {"workload": wname, "mode": mode, "systems": nsys,
+            "config": {"workload": wname, "mode": mode, "systems": len(systems),
                        "atoms": int(sum(s.n_atoms for s in systems)), "N": int(sum(s.n for s in systems)),
                        "b": sys_.b, "tau": args.tau, "tau_refine": tau64, "tol": 1e-9, "directions": 3,
-                       "iterations": int(max(i.iterations for i in sinfo)),
+                       "iterations": int(max([i.iterations for i in sinfo], default=0)),
                        "nnzb_p0": int(sum(i.nnzb_p0 for i in sinfo)),
                        "nnzb_p1": [int(sum(i.nnzb_p1[d] for i in sinfo)) for d in range(3)],
                        "nnzb_per_block_row_p0": float(sum(i.nnzb_p0 for i in sinfo) /
-                                                      sum(s.h0.nb for s in systems)),
-                       "l2": "working set >> L2 (no flush needed)", "parallelism": f"replicas{world}"},
-            "tflops": useful / s_per_solve / 1e12 * 1.0 if world == 1 else None,
+                                                      max(1, sum(s.h0.nb for s in local))),
+                       "l2": "working set >> L2 (no flush needed)",
+                       "parallelism": f"replicas{world}" if replicas else f"partition{world}",
+                       "systems_on_rank0": mine if rank == 0 else None},
+            "tflops": useful / s_per_solve / 1e12 if world == 1 else None,
             "block_spgemm_tflops": achieved_all / 1e12,
-            "alpha_diag": [float(alpha_m[0][k, k]) for k in range(3)],
+            "alpha_diag": [float(alpha_m[0][k, k]) for k in range(3)] if nsys else None,
             "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
@@ -462,6 +563,78 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "device_gb_peak": last.device_bytes_peak / 1e9, "product_groups": int(last.product_groups),
             "clocks": clocks}
     return line
+
+
+def gpu_sample_seconds(args, sample, torch, reps=3):
+    """Device time of one solve of the oracle's sample alone, in the bench's
+    mode (the like-for-like partner of cpu_baseline)."""
+    from paper_2009_03551_gb300 import rdm
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream(dev)
+    sol = rdm.Solver(dev.index, stream.cuda_stream)
+    sol.set_params(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100)
+    sol.load([to_device(sample, torch, dev)])
+    sol.solve()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sol.solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sol.close()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def sweep(args, systems, wname, torch):
+    """Threshold (or tolerance) study on one GPU: for every point, the mixed
+    and the FP64 solve of the workload, their times and |dalpha|/alpha against
+    the exact sum-over-states alpha when the workload is small enough for the
+    dense oracle (else against the FP64 solve at the smallest threshold)."""
+    from paper_2009_03551_gb300 import rdm
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    dsys = [to_device(s, torch, dev) for s in systems]
+    exact = None
+    if all(s.n <= 8000 for s in systems):
+        from oracle import exact_response, polarizability
+        exact = []
+        for s in systems:
+            h0 = dense(s.h0)
+            h1s = [dense(m) for m in s.h1]
+            _, p1s, _, _ = exact_response(h0, h1s, s.n_occ)
+            exact.append(polarizability(p1s, h1s))
+    pts = [1e-4, 1e-5, 1e-6, 1e-7, 1e-8] if args.sweep == "tau" else [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-9]
+    rows = []
+    for x in pts:
+        for mode in (args.mode, "fp64"):
+            tau, tol = (x, 1e-9) if args.sweep == "tau" else (args.tau, x)
+            sol = rdm.Solver(dev.index, stream.cuda_stream)
+            sol.set_params(tau=tau, tol=tol, mode=mode, max_iter=100)
+            sol.load(dsys)
+            sol.solve()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            code, info = sol.solve()
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            a = alphas(sol, len(systems))
+            infos = [sol.info(k) for k in range(len(systems))]
+            sol.close()
+            rows.append({"sweep": args.sweep, "value": x, "mode": mode, "tau": tau, "tol": tol, "s_per_solve": t,
+                         "iterations": int(max(i.iterations for i in infos)),
+                         "nnzb_per_block_row_p0": float(sum(i.nnzb_p0 for i in infos) /
+                                                        sum(s.h0.nb for s in systems)),
+                         "tflops": info.useful_flops / t / 1e12, "alpha": a})
+    # without the exact alpha: the FP64 solve at the last (tightest) point
+    ref = exact if exact is not None else [r for r in rows if r["mode"] == "fp64"][-1]["alpha"]
+    for r in rows:
+        r["alpha_rel_err"] = rel_alpha_diff(r.pop("alpha"), ref)
+        r["alpha_ref"] = "exact (sum over states, oracle A)" if exact is not None else "FP64 GPU solve"
+        r["workload"] = wname
+        print(json.dumps(r), flush=True)
 
 
 def make_workload(args):
@@ -489,11 +662,12 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference" and rank != 0:
+        return    # the CPU oracle runs on rank 0 alone
     wname, systems = make_workload(args)
-    sys_ = systems[0]
 
     if args.impl == "reference":
-        run_reference(args, sys_, rank, wname)
+        run_reference(args, systems, rank, wname)
         return
 
     import torch
@@ -508,12 +682,23 @@ def main():
         b.build()
     if dist is not None:
         dist.barrier()
+    if args.sweep:
+        if rank == 0:
+            sweep(args, systems, wname, torch)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     line = run_ours(args, systems, wname, rank, world, torch, dist)
-    if rank == 0 and world == 1 and not args.no_cpu and len(systems) == 1 and sys_.n <= 16000:
-        per_prod, per_solve, iters, n_prod = oracle_sample(sys_)
-        line["cpu_baseline"] = {"value": per_solve, "unit": "s", "cores": cores(), "kind": "oracle",
-                                "sample": f"one dense FP64 {sys_.n}x{sys_.n} product of the oracle's TC2 "
-                                          f"({per_prod:.2f} s), scaled by {n_prod} products x {iters} iterations"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample, k, desc = oracle_sample_system(systems)
+        t_cpu, iters = timed_oracle_solve(sample, args.tau)
+        line["cpu_baseline"] = {"value": t_cpu, "unit": "s", "cores": cores(), "kind": "oracle",
+                                "sample": desc + f" ({iters} iterations), timed once",
+                                "gpu_same_sample_s": gpu_sample_seconds(args, sample, torch),
+                                "scaled_to_workload": {"kind": "model",
+                                                       "value": dense_cost_model(t_cpu, sample, systems),
+                                                       "basis": "the timed sample scaled by the dense N^3 cost "
+                                                                "to every system of the workload (not measured)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -288,8 +288,13 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
  * The call allocates nothing: its scratch (one double per block row) is a
  * file-scope device array of at most 262,144 block rows, held by every GPU
  * that loads the library until exit.
- *  - A and B: device BSR (on_device = 1) with the same nb and b; nb above
+ *  - A and B: device BSR (on_device = 1) with the same nb, b and n; nb above
  *    262,144 returns RDM_EINVAL, as do null pointers and host matrices.
+ *  - The call cannot inspect device data, so it trusts the layout: each
+ *    row_ptr must have nb+1 non-decreasing entries from 0 to that matrix's
+ *    nnzb, and the column indices of every block row must be strictly
+ *    increasing and in [0, nb) (B's columns are binary-searched).  A
+ *    malformed matrix gives a wrong result or out-of-range reads.
  *  - The first call on a device looks up the array's device address (once,
  *    with that device current); make it before any stream capture.
  *  - All calls share the array: calls whose kernels overlap on the GPU race
@@ -297,6 +302,29 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
  *    at zero (every call writes each partial it reads).
  * Returns RDM_OK, RDM_EINVAL or RDM_ECUDA (launch failure). */
 int rdm_bsr_dot_noalloc(const rdm_bsr *A, const rdm_bsr *B, double *out_device, void *cuda_stream);
+
+/* ---- test settings (kernel-level tests; no counterpart in the paper) ------ */
+
+/* Settings that tests use to reach paths a production solve rarely takes.
+ * All zeros (the state of a new handle) is production behaviour. */
+typedef struct {
+    int64_t tc_wait_cycles;  /* bound of every wait inside the tensor-core product kernel, in SM clock
+                                cycles; 0 = the default (~2 s).  A wait that runs out makes the kernel
+                                raise its abort flag, let its copies and MMAs in flight finish, free
+                                its tensor memory and return; the solve then fails with RDM_ETIMEOUT
+                                and the handle stays usable. */
+    int32_t tc_hold;         /* 1: the tensor-core kernel's copy warp first waits for a device flag that
+                                nothing sets, so that its wait runs out (with tc_wait_cycles) and the
+                                solve returns RDM_ETIMEOUT without a fault */
+    int32_t tc_window_cols;  /* column window (a multiple of 32, at most 16,384) of the warp-parallel
+                                builders of the tensor-core tile and K-step lists; rows whose columns
+                                span more take the serial merges.  0 = 16,384.  Results do not depend
+                                on it. */
+} rdm_test_knobs;
+
+/* Set the test settings of h (NULL restores all zeros).  RDM_EINVAL for a
+ * negative value or a window that is not a multiple of 32 up to 16,384. */
+int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k);
 
 /* Library version string. */
 const char *rdm_version(void);

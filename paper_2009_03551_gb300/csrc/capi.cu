@@ -378,6 +378,11 @@ struct StepStats {
 
 bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
 
+// the mixed modes need a block size that the tensor-core kernel handles
+bool tc_block_ok(int mode, int b) {
+    return !(mode == RDM_MODE_MIXED_BF16 || mode == RDM_MODE_MIXED_FP16) || b == 0 || b == 32;
+}
+
 // Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
 // Mixed modes: tier 0 runs every product as a split product on the tensor
 // cores.  In the final tier the purification X0^2 is refined on the CUDA
@@ -764,6 +769,8 @@ std::vector<double> stats(rdm_handle *h, MatSet &X) {
 int run_solve(rdm_handle *h, rdm_info *info_out) {
     DeviceGuard dg(h->device);
     if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
+    if (!tc_block_ok(h->prm.mode, h->b))
+        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 blocks");
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_kernel_launches;
     assemble(h);
@@ -887,13 +894,21 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                 y.tier++;
                 y.tier_start = n;
             }
-            // branch: trace test of Eq. TC2 (tie -> square); forced by the test hook;
-            // in the reduced-precision modes a negative idempotency error (spectrum
-            // outside [0,1]) alternates the branch so that both edges contract
+            // branch: trace test of Eq. TC2 (tie -> square, the ">=" of Eq. TC2);
+            // forced by the test hook.  Reading where the paper is silent (what TC2
+            // does once rounding or the filter pushes eigenvalues out of [0, 1],
+            // i.e. e = Tr X - ||X||^2 < 0): the branch alternates with the previous
+            // one, so that both spectral edges contract instead of an eigenvalue
+            // above 1 being squared again and again.
+            //  - FP64 mode: only a clearly negative error, e < -1e-10 N_occ, the
+            //    rule of the oracle; rounding at tau = 0 never reaches that level,
+            //    the filter at large thresholds does (the trace test alone then
+            //    diverges), so FP64 runs follow the oracle step for step.
+            //  - reduced-precision modes: any e < 0, since their rounding alone
+            //    leaves eigenvalues slightly outside [0, 1].  These trajectories
+            //    have no oracle counterpart step for step; only their limits (P0,
+            //    P1, alpha) are compared with the oracle.
             int branch = (tr >= nocc[s]) ? 1 : 2;
-            // (FP64: only a clearly negative error, e < -1e-10 N_occ, as in the
-            // oracle; that level is out of reach of rounding but the filter at
-            // large thresholds reaches it, and the trace test alone then diverges)
             if (n > 0 && (lowprec ? e < 0 : e < -1e-10 * std::max(1.0, nocc[s])))
                 branch = y.prev_branch == 1 ? 2 : 1;
             if (n < (int)h->forced.size()) branch = h->forced[n];
@@ -1165,6 +1180,9 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
         p->use_graphs != 0)
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
                                    "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0, use_graphs 0)");
+    if (!tc_block_ok(p->mode, h->b))
+        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 "
+                                   "blocks (the uploaded matrices have b = " + std::to_string(h->b) + ")");
     h->prm = *p;
     return RDM_OK;
 }
@@ -1191,6 +1209,9 @@ int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons
         if (!H0) return fail(h, RDM_EINVAL, "null matrix");
         if (n_electrons <= 0 || (n_electrons & 1) || n_electrons / 2 >= H0->n)
             return fail(h, RDM_EINVAL, "electron count must be even with 0 < N_e/2 < n");
+        if (!tc_block_ok(h->prm.mode, H0->b))
+            return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 "
+                                       "blocks; set another mode first to upload b = " + std::to_string(H0->b));
         HostSys &y = h->hs[sys];
         int saved_b = h->b;
         if (h->S == 1) h->b = 0;
@@ -1242,6 +1263,19 @@ int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len) {
 int rdm_solve(rdm_handle *h, rdm_info *info) {
     if (!h) return RDM_EINVAL;
     return guarded(h, [&] { return run_solve(h, info); });
+}
+
+int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k) {
+    if (!h) return RDM_EINVAL;
+    rdm_test_knobs z{};
+    if (!k) k = &z;
+    if (k->tc_wait_cycles < 0 || k->tc_hold < 0 || k->tc_hold > 1 || k->tc_window_cols < 0 ||
+        k->tc_window_cols > 16384 || (k->tc_window_cols & 31))
+        return fail(h, RDM_EINVAL, "invalid test settings");
+    h->tcw.knobs.wait_cycles = k->tc_wait_cycles;
+    h->tcw.knobs.hold = k->tc_hold;
+    h->tcw.knobs.window_words = k->tc_window_cols / 32;
+    return RDM_OK;
 }
 
 int rdm_get_info(rdm_handle *h, int sys, rdm_info *info) {

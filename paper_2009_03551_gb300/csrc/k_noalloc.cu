@@ -111,7 +111,8 @@ extern "C" int rdm_bsr_dot_noalloc(const rdm_bsr *A, const rdm_bsr *B, double *o
     using namespace rdm;
     if (!A || !B || !out_device) return RDM_EINVAL;
     if (!A->on_device || !B->on_device) return RDM_EINVAL;
-    if (A->nb != B->nb || A->b != B->b || A->nb <= 0 || A->b <= 0 || A->b > 64) return RDM_EINVAL;
+    if (A->nb != B->nb || A->b != B->b || A->n != B->n || A->nb <= 0 || A->b <= 0 || A->b > 64)
+        return RDM_EINVAL;
     if (A->nb > kNoAllocMaxRows) return RDM_EINVAL;   // beyond the scratch array
     if (!A->row_ptr || !B->row_ptr || (A->nnzb && (!A->col_idx || !A->vals)) ||
         (B->nnzb && (!B->col_idx || !B->vals)))

@@ -79,7 +79,11 @@ constexpr int kTileInts = kColOff + TBN;     //   then column j of each tile col
 constexpr int kSegSteps = 4;                 // K-steps accumulated in tensor memory per segment
 constexpr int kSegBufs = 512 / kTileN;       // segment accumulators: the 512 TMEM columns
 static_assert(kSlots <= 32 && kSegBufs >= 2 && (kSegBufs & (kSegBufs - 1)) == 0, "tile shape");
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;   // default bound of a wait: ~2 s at 2 GHz
+
+// Stays 0 for the life of the program: the test setting `hold` makes the
+// producer wait for it, so that every wait of the kernel runs out.
+__device__ int g_never_set = 0;
 
 // ---------------------------------------------------------------------------
 // PTX helpers
@@ -107,15 +111,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // bounded wait; false on timeout or when another role has aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit) {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
     }
+    return true;
+}
+// bounded wait that ignores the abort flag (draining after an abort)
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity, long long limit) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -265,6 +277,7 @@ struct TileBuild {
     const int64_t *step_off;
     int *steps;          // [nsteps * kSlots]
     int ntile;
+    int max_words;       // bitmap window in 32-column words (<= 512); wider windows: serial merge
 };
 
 // upper mask range [cur, end) of block row 4I + m of job p, empty for rows
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
         return;
     }
     const int nw = ((hi - lo) >> 5) + 1;
-    if (nw > kTileRowWords) {
+    if (nw > T.max_words) {
         if (lane == 0) tile_rows_serial(T, t, p, I, cur, end, fill);
         return;
     }
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         }
         lo_t[term] = max(loA, loB);
         hi_t[term] = min(hiA, hiB);
-        if (hi_t[term] >= lo_t[term] && ((hi_t[term] - lo_t[term]) >> 5) + 1 > kStepWords) fits = false;
+        if (hi_t[term] >= lo_t[term] && ((hi_t[term] - lo_t[term]) >> 5) + 1 > T.max_words) fits = false;
     }
     if (!fits) {
         if (lane == 0) tile_steps_serial(T, t, fill);
@@ -615,6 +628,8 @@ struct TcArgs {
     const int *uidx;
     int64_t u0;
     int *err;
+    long long wait_cycles;        // bound of every mbarrier wait
+    int hold;                     // test setting: the producer waits for g_never_set first
 };
 
 struct __align__(8) SmemCtl {
@@ -664,6 +679,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
         // holds zeros from its previous use is not copied again (zmask).
         uint32_t it = 0;
         bool ok = true;
+        if (A.hold) {
+            // test setting: wait (bounded) for a flag that nothing sets; the
+            // wait runs out, raises the abort flag and nothing is issued
+            int held = 1;
+            if (lane == 0) {
+                const long long t0 = clock64();
+                while (*(volatile int *)&g_never_set == 0) {
+                    if (clock64() - t0 > A.wait_cycles) {
+                        *abort_flag = 1;
+                        held = 0;
+                        break;
+                    }
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, held, 0) != 0;
+        }
         uint32_t zmask[kStages];
 #pragma unroll
         for (int k = 0; k < kStages; ++k) zmask[k] = 0u;
@@ -684,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 const uint32_t need = __ballot_sync(0xffffffffu, !skip);
                 int waited = 1;
                 if (lane == 0) {
-                    waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag) ? 1 : 0;
+                    waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag, A.wait_cycles) ? 1 : 0;
                     if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * kPairBytes);
                 }
                 waited = __shfl_sync(0xffffffffu, waited, 0);
@@ -701,6 +732,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 }
             }
         }
+        if (!ok && lane == 0) {
+            // after an abort, wait (bounded) until the copies of the stages
+            // still in flight have landed before the CTA leaves: the last
+            // min(it, kStages) issued stages, each at the phase of its last use
+            const uint32_t n = it < (uint32_t)kStages ? it : (uint32_t)kStages;
+            for (uint32_t q = it - n; q < it; ++q)
+                mbar_wait_drain(&ctl->full[q % kStages], (q / kStages) & 1, A.wait_cycles);
+        }
+        __syncwarp();
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -713,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                     // one segment: up to kSegSteps K-steps into a fresh accumulator
                     const int buf = seg & (kSegBufs - 1);
                     const uint32_t use = seg / kSegBufs;
-                    if (!mbar_wait(&ctl->seg_empty[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(&ctl->seg_empty[buf], (use & 1) ^ 1, abort_flag, A.wait_cycles)) { ok = false; break; }
                     fence_after();
                     const uint32_t d_tmem = tmem + buf * kTileN;
                     const int64_t qe = q + kSegSteps < s1 ? q + kSegSteps : s1;
@@ -721,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                     for (; q < qe; ++q, ++it) {
                         const int st = it % kStages;
                         const uint32_t ph = (it / kStages) & 1;
-                        if (!mbar_wait(&ctl->full[st], ph, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait(&ctl->full[st], ph, abort_flag, A.wait_cycles)) { ok = false; break; }
                         fence_after();
                         const uint32_t base = smem_u32(stages + st * kStageBytes);
                         const uint32_t a_hi = base, a_lo = base + 512;
@@ -745,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 // drain: wait (bounded) until every MMA this thread issued has completed
                 mma_commit(&ctl->drain);
                 long long t0 = clock64();
-                while (!mbar_try_wait(&ctl->drain, 0) && clock64() - t0 < kWaitCycles) {
+                while (!mbar_try_wait(&ctl->drain, 0) && clock64() - t0 < A.wait_cycles) {
                 }
             }
         }
@@ -808,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             for (int g = 0; g < nseg; ++g, ++seg) {
                 const int buf = seg & (kSegBufs - 1);
                 const uint32_t use = seg / kSegBufs;
-                if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag, A.wait_cycles)) { ok = false; break; }
                 fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * kTileN;
 #pragma unroll
@@ -951,6 +991,8 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     for (int p = 0; p < kMaxJobs; ++p) A.job_tau_sel[p] = a.job_tau_sel[p];
     A.out_val = a.out_val; A.out_nrm = a.out_nrm; A.keep = a.keep; A.uidx = a.uidx; A.u0 = a.u0;
     A.err = w.counters.p;
+    A.wait_cycles = w.knobs.wait_cycles > 0 ? w.knobs.wait_cycles : kWaitCycles;
+    A.hold = w.knobs.hold;
     static bool attr = false;
     if (!attr) {
         RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
@@ -981,6 +1023,9 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     T.u0 = unit0; T.u1 = unit1;
     T.sys_tier = sd.tier.p;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
+    static_assert(kTileRowWords == kStepWords, "one window bound for both plan builders");
+    T.max_words = w.knobs.window_words > 0 && w.knobs.window_words < kTileRowWords ? w.knobs.window_words
+                                                                                    : kTileRowWords;
     k_tile_rows<<<(nrow4 + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();
     scan_exclusive_i32(w.tile_cnt.p, w.tile_off.p, nrow4, w.scan32.p, st);

@@ -5,8 +5,18 @@
 
 namespace rdm {
 
+// Test settings of the tensor-core path (rdm_set_test_knobs); zeros keep the
+// production behaviour.
+struct TcKnobs {
+    long long wait_cycles = 0;  // bound of every mbarrier wait in SM clock cycles (0: ~2 s)
+    int hold = 0;               // 1: the producer first waits for a flag that nothing sets
+    int window_words = 0;       // bitmap window of the tile-plan builders in 32-column words
+                                // (0: 512, i.e. 16,384 columns; wider windows take the serial merge)
+};
+
 // work buffers of the tensor-core path (tile lists, per-tile K-step lists)
 struct TcWork {
+    TcKnobs knobs;
     DevBuf<uint16_t> zero;      // zero operand blocks: one per CTA and K-step slot
     DevBuf<int> tiles;          // per tile: job, I, -, nsteps, mask slot[4 x 8], column j[8]
     DevBuf<int> tile_cnt, tile_off;

@@ -41,6 +41,7 @@ EXPORTED = (
     "rdm_batch_create", "rdm_upload_h0", "rdm_upload_h1", "rdm_solve", "rdm_force_branches",
     "rdm_get_info", "rdm_get_p0_nnzb", "rdm_get_p1_nnzb", "rdm_get_p0", "rdm_get_p1",
     "rdm_get_alpha", "rdm_get_log", "rdm_block_product", "rdm_version", "rdm_bsr_dot_noalloc",
+    "rdm_set_test_knobs",
 )
 
 
@@ -74,6 +75,10 @@ class rdm_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("pad0", C.c_int32)]
+
+
+class rdm_test_knobs(C.Structure):
+    _fields_ = [("tc_wait_cycles", C.c_int64), ("tc_hold", C.c_int32), ("tc_window_cols", C.c_int32)]
 
 
 class rdm_iter_log(C.Structure):
@@ -111,6 +116,7 @@ def _load():
                                         C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
                                         C.POINTER(rdm_bsr_out), C.POINTER(C.c_int64)]),
         "rdm_version": (C.c_char_p, []),
+        "rdm_set_test_knobs": (C.c_int, [H, C.POINTER(rdm_test_knobs)]),
         "rdm_bsr_dot_noalloc": (C.c_int, [C.POINTER(rdm_bsr), C.POINTER(rdm_bsr), C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -348,6 +354,13 @@ def rdm_bsr_dot_noalloc(A, B, out_ptr: int, stream=None) -> None:
     if code != RDM_OK:
         raise RdmError(code, "rdm_bsr_dot_noalloc failed (device matrices with equal nb, b required; "
                              "nb <= 262144)")
+
+
+def rdm_set_test_knobs(h, tc_wait_cycles: int = 0, tc_hold: int = 0, tc_window_cols: int = 0) -> None:
+    """Test settings of the tensor-core path (see include/rdm.h); all zeros
+    restore production behaviour."""
+    k = rdm_test_knobs(tc_wait_cycles, tc_hold, tc_window_cols)
+    _check(h, _lib.rdm_set_test_knobs(h, C.byref(k)))
 
 
 # ---- convenience wrapper ---------------------------------------------------

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import exact_response, polarizability, tc2_response
 from oracle.dense import rel_frobenius
+from blockcheck import max_rel_err
 from oracle.tc2 import block_truncate
 from synth import Bsr, make_batch_config, make_chain, make_cluster, make_config
 
@@ -48,7 +49,9 @@ def test_cfg1_fp64_tau0_vs_exact(rdm):
     sol, code, info = gpu_solve(rdm, s, tau=0.0, tol=1e-12, mode="fp64", max_iter=100)
     assert code == rdm.RDM_OK and info.converged
     assert rel_frobenius(sol.p0().to_dense(), p0) <= 1e-10
+    assert max_rel_err(sol.p0().to_dense(), p0) <= 1e-10
     assert rel_frobenius(sol.p1(0, 0).to_dense(), p1s[0]) <= 1e-10
+    assert max_rel_err(sol.p1(0, 0).to_dense(), p1s[0]) <= 1e-10
     a = sol.alpha()[0, 0]
     assert a == pytest.approx(polarizability(p1s, h1s)[0, 0], rel=1e-10)
     # same iteration count and branch sequence as the step-by-step oracle
@@ -88,8 +91,10 @@ def test_cluster_fp64_tau_vs_stepwise_oracle(rdm, cluster150, oracle150):
     assert info.iterations == ob.iterations
     p0 = sol.p0().to_dense()
     assert rel_frobenius(p0, ob.p0) <= 1e-10
+    assert max_rel_err(p0, ob.p0) <= 1e-10
     for d in range(3):
         assert rel_frobenius(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-10
+        assert max_rel_err(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-10
     a = sol.alpha()
     h0, h1s = dense_list(s)
     ao = polarizability(ob.p1s, h1s)
@@ -107,8 +112,10 @@ def test_cluster_fp64_free_run_matches_oracle_limit(rdm, cluster150, oracle150):
     sol, code, info = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode="fp64")
     assert code == rdm.RDM_OK
     assert rel_frobenius(sol.p0().to_dense(), oracle150.p0) <= 1e-9
+    assert max_rel_err(sol.p0().to_dense(), oracle150.p0) <= 1e-9
     for d in range(3):
         assert rel_frobenius(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-8
+        assert max_rel_err(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-8
 
 
 def test_fp64_large_threshold_stays_bounded(rdm, cluster150):
@@ -179,8 +186,10 @@ def test_cluster_fp32_vs_oracle(rdm, cluster150, oracle150):
     sol, code, info = gpu_solve(rdm, s, tau=1e-6, tol=1e-9, mode="fp32")
     assert code in (rdm.RDM_OK, rdm.RDM_NOT_CONVERGED)
     assert rel_frobenius(sol.p0().to_dense(), oracle150.p0) <= 1e-5
+    assert max_rel_err(sol.p0().to_dense(), oracle150.p0) <= 1e-5
     for d in range(3):
         assert rel_frobenius(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-5
+        assert max_rel_err(sol.p1(0, d).to_dense(), oracle150.p1s[d]) <= 1e-5
 
 
 # ---------------------------------------------------------------------------
@@ -218,6 +227,7 @@ def test_block_product_fp32(rdm, b, terms):
                                         rdm.MODES["fp32"])
             got = res.to_dense()
             assert rel_frobenius(got, ref) <= 2e-6
+            assert max_rel_err(got, ref) <= 2e-6
             assert np.array_equal(got, got.T)
     finally:
         rdm.rdm_destroy(h)
@@ -240,6 +250,7 @@ def test_block_product_fp64(rdm, b, terms):
                                         rdm.MODE_FP64)
             got = res.to_dense()
             assert rel_frobenius(got, ref) <= 1e-13
+            assert max_rel_err(got, ref) <= 1e-13
             # kept blocks: exactly the blocks of ref with norm >= tau
             nb = -(-n // b)
             pad = np.zeros((nb * b, nb * b))
@@ -323,4 +334,5 @@ def test_no_perturbation_and_single_block(rdm):
     assert code == rdm.RDM_OK and s.h0.nb == 1
     p0, _, _, _ = exact_response(s.h0.to_dense(), [], s.n_occ)
     assert rel_frobenius(sol.p0().to_dense(), p0) <= 1e-10
+    assert max_rel_err(sol.p0().to_dense(), p0) <= 1e-10
     assert np.all(np.isnan(sol.alpha()))

@@ -15,6 +15,7 @@ import pytest
 
 from oracle import polarizability, tc2_response
 from oracle.dense import rel_frobenius
+from blockcheck import max_rel_err
 from oracle.tc2 import block_norms, block_truncate
 from synth import Bsr, make_chain, make_cluster
 
@@ -64,6 +65,7 @@ def test_tc_block_product(rdm, mode, terms, nblk):
                                         rdm.MODES[mode])
             got = res.to_dense()
             assert rel_frobenius(got, ref) <= 3e-5, mode
+            assert max_rel_err(got, ref) <= 3e-5, mode
             # blocks clearly above / below the threshold are kept / dropped
             nrm = block_norms(exact, b)
             nb = nrm.shape[0]
@@ -89,6 +91,7 @@ def test_tc_product_matches_fp64_kernel_closely(rdm):
         r64 = rdm.rdm_block_product(h, A, None, None, 0.0, 1.0, 1, 0.0, rdm.MODE_FP64).to_dense()
         rbf = rdm.rdm_block_product(h, A, None, None, 0.0, 1.0, 1, 0.0, rdm.MODE_MIXED_BF16).to_dense()
         assert rel_frobenius(r64, a @ a) <= 1e-13
+        assert max_rel_err(r64, a @ a) <= 1e-13
         assert 1e-9 < rel_frobenius(rbf, r64) <= 3e-5
     finally:
         rdm.rdm_destroy(h)
@@ -141,8 +144,10 @@ def test_mixed_solve_vs_oracle(rdm, cluster150, oracle150, mode):
     ao = polarizability(ob.p1s, h1s)
     assert np.max(np.abs(a - ao)) / np.max(np.abs(ao)) <= 1e-6
     assert rel_frobenius(sol.p0().to_dense(), ob.p0) <= 1e-5
+    assert max_rel_err(sol.p0().to_dense(), ob.p0) <= 1e-5
     for d in range(3):
         assert rel_frobenius(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-4
+        assert max_rel_err(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-4
     assert abs(info.idempotency) < 1e-8 and abs(info.trace_error) < 1e-8
 
 
@@ -182,6 +187,7 @@ def test_final_tier_double_fp32_purification(rdm, cluster150):
     assert iff.kernel_flops[3] > 0 and iff.kernel_flops[1] == 0.0
     assert iff.iterations == i64.iterations
     assert rel_frobenius(pff, p64) <= 1e-9
+    assert max_rel_err(pff, p64) <= 1e-9
     assert np.max(np.abs(aff - a64)) / np.max(np.abs(a64)) <= 1e-9
     assert abs(iff.idempotency) < 1e-8
 
@@ -193,7 +199,8 @@ def test_final_tier_fp32_purification(rdm, cluster150, oracle150):
     s = cluster150
     ob, h1s = oracle150
     sol = rdm.Solver(0)
-    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x0=3)
+    # final tier without FP64 products: X0^2 in FP32, the first-order products split
+    sol.set_params(tau=1e-6, tol=1e-9, mode=mode, max_iter=100, refine_x0=3, refine_x1=2)
     sol.load(s)
     code, info = sol.solve()
     assert code == rdm.RDM_OK and info.converged
@@ -235,3 +242,70 @@ def test_mixed_batch_with_converged_copies(rdm):
         one.solve()
         a1, a0 = sol.alpha(k), one.alpha()
         assert np.max(np.abs(a1 - a0)) / np.max(np.abs(a0)) <= 1e-6
+
+
+def test_expired_wait_returns_etimeout_and_the_handle_stays_usable(rdm, cluster150):
+    """The tensor-core kernel bounds every wait.  With a short bound and its
+    copy warp waiting for a flag that nothing sets, the wait runs out: the
+    kernel raises its abort flag, drains, frees its tensor memory and returns;
+    the solve reports RDM_ETIMEOUT, and the same handle then solves to the
+    same bits as before."""
+    s = cluster150
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100)
+    sol.load(s)
+    code, _ = sol.solve()
+    assert code == rdm.RDM_OK
+    a_ref, p0_ref = sol.alpha().copy(), sol.p0().vals.copy()
+    rdm.rdm_set_test_knobs(sol.h, tc_wait_cycles=2_000_000, tc_hold=1)     # ~1 ms
+    with pytest.raises(rdm.RdmError) as e:
+        sol.solve()
+    assert e.value.code == rdm.RDM_ETIMEOUT
+    rdm.rdm_set_test_knobs(sol.h)
+    code, _ = sol.solve()
+    assert code == rdm.RDM_OK
+    assert np.array_equal(sol.alpha(), a_ref) and np.array_equal(sol.p0().vals, p0_ref)
+
+
+def test_serial_plan_builders_give_the_same_tiles(rdm, cluster150):
+    """Tile rows and K-steps whose columns span more than the bitmap window
+    are built by serial merges; with a 32-column window most of them take
+    that path here.  The tiles, their K-steps and so every bit of the result
+    are the same as with the warp-parallel builders."""
+    s = cluster150
+    res = []
+    for window in (0, 32):
+        sol = rdm.Solver(0)
+        rdm.rdm_set_test_knobs(sol.h, tc_window_cols=window)
+        sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100)
+        sol.load(s)
+        code, _ = sol.solve()
+        assert code == rdm.RDM_OK
+        res.append((sol.alpha().copy(), sol.p0().vals.copy(), [sol.p1(0, d).vals.copy() for d in range(3)]))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    for d in range(3):
+        assert np.array_equal(res[0][2][d], res[1][2][d])
+
+
+def test_test_knobs_are_validated(rdm):
+    h = rdm.rdm_create(0)
+    try:
+        for bad in (dict(tc_window_cols=33), dict(tc_window_cols=16416), dict(tc_wait_cycles=-1), dict(tc_hold=2)):
+            with pytest.raises(rdm.RdmError):
+                rdm.rdm_set_test_knobs(h, **bad)
+    finally:
+        rdm.rdm_destroy(h)
+
+
+def test_mixed_modes_reject_unsupported_block_sizes_up_front(rdm):
+    s = make_chain(8, opa=4, b=4, spacing=2.8, cutoff=8.0, seed=0, dirs=("x",))
+    sol = rdm.Solver(0)
+    sol.set_params(mode="mixed_fp16")
+    with pytest.raises(rdm.RdmError) as e:
+        sol.load(s)
+    assert e.value.code == rdm.RDM_EINVAL
+    sol.set_params(mode="fp64")
+    sol.load(s)
+    with pytest.raises(rdm.RdmError) as e:
+        sol.set_params(mode="mixed_bf16")
+    assert e.value.code == rdm.RDM_EINVAL

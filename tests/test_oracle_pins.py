@@ -307,6 +307,31 @@ def test_tc2_large_threshold_stays_bounded():
     assert any(rec["idempotency"] < -1e-10 * s.n_occ for rec in r.log)
 
 
+def test_tc2_idempotency_stall_stop_iteration():
+    """The idempotency-stall stop (stall_tol > 0) fires when e = Tr X0 -
+    ||X0||_F^2 has not decreased over two iterations while below stall_tol.
+    Predicted by hand for H0 = diag(-1, 0, 1), N_occ = 1: the Gershgorin
+    bounds are -1 and 1, so X0_0 = diag(1, 1/2, 0); the trace never drops
+    below N_occ, every step squares, and the middle eigenvalue runs through
+    2^-1, 2^-2, 2^-4, ..., 2^-64.  Every value and every sum is exact in FP64
+    until Tr X0 = 1 + 2^-64 rounds to 1 at X0_6; so e_n = 1/4, 3/16, 15/256,
+    2^-8 - 2^-16, 2^-16 - 2^-32, 2^-32 (1 + 2^-64 rounds to 1 in ||X0||^2),
+    then 0, 0, 0.  The first n with e_{n+1} >= e_{n-1} is n = 7 (0 >= 0): the
+    loop stops after 8 updates.  With the stop disabled it runs to max_iter."""
+    h0 = np.diag([-1.0, 0.0, 1.0])
+    h1s = [np.diag([0.3, -0.2, 0.1])]
+    r = tc2_response(h0, h1s, 1, 1, tau=0.0, tol=0.0, max_iter=50, stall_tol=1e-3)
+    assert r.converged and r.iterations == 8
+    assert r.branches == [1] * 8
+    e = [rec["idempotency"] for rec in r.log]
+    assert e[:6] == [0.25, 0.1875, 0.05859375, 2.0 ** -8 - 2.0 ** -16, 2.0 ** -16 - 2.0 ** -32, 2.0 ** -32]
+    assert e[6:] == [0.0, 0.0]
+    # the level matters only as an upper bound; 0 disables the stop
+    assert tc2_response(h0, h1s, 1, 1, tau=0.0, tol=0.0, max_iter=50, stall_tol=1e-300).iterations == 8
+    off = tc2_response(h0, h1s, 1, 1, tau=0.0, tol=0.0, max_iter=50, stall_tol=0.0)
+    assert off.iterations == 50 and not off.converged
+
+
 def test_tc2_forced_branches_replay():
     s = chain_sys(12)
     h0 = s.h0.to_dense()
