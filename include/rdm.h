@@ -131,11 +131,20 @@ typedef struct {
                                one super-row per group).  0: automatic, from the free device
                                memory.  Results do not depend on the grouping. */
     int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT
-                               (RDM_REFINE_FP32X2 for RDM_MODE_MIXED_FP16, RDM_REFINE_FP64 for
-                               RDM_MODE_MIXED_BF16), RDM_REFINE_FP64, RDM_REFINE_FP32X2, or
-                               RDM_REFINE_FP32 (the final tier then ends on the FP32 idempotency
-                               stall) */
-    int32_t reserved[1];
+                               (RDM_REFINE_FP32X2 for RDM_MODE_MIXED_FP16 with 32 x 32 blocks,
+                               otherwise RDM_REFINE_FP64), RDM_REFINE_FP64, RDM_REFINE_FP32X2
+                               (32 x 32 blocks only), or RDM_REFINE_FP32 (the final tier then ends
+                               on the FP32 idempotency stall) */
+    int32_t stall_window;   /* mixed modes: the idempotency error e "stalls" when |e_n| >= |e_{n-w}| / 2
+                               with w = stall_window iterations (0: 2); a stall moves a system to the
+                               final tier, and in the final tier ends its iteration */
+    int32_t block_size;     /* block size of the solve's products: 0 = the uploaded b; 16, 32 or 64
+                               re-blocks every system (the same matrices in b' x b' blocks; the
+                               filter then acts on b' x b' blocks) and the getters return P0 and P1
+                               in the uploaded layout.  Ignored while autotune is on. */
+    int32_t autotune;       /* 1: the first solve after an upload times one probe solve at each block
+                               size in {16, 32, 64} and keeps the fastest for this and later solves
+                               (rdm_info.block_size, probe_ms); 0: off */
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -169,7 +178,9 @@ typedef struct {
     int64_t device_bytes_peak; /* largest device memory held by the library's buffers during
                                   the solve (all handles of the process) */
     int32_t product_groups;    /* most super-row groups a step of the solve was split into (chunk_mb) */
-    int32_t pad0;
+    int32_t block_size;        /* block size the products ran at (rdm_params.block_size / autotune) */
+    double  autotune_ms;       /* wall time of the autotuner's probe solves (0 when it did not run) */
+    double  probe_ms[3];       /* device time of the probe solve at b = 16, 32, 64 (0: not probed) */
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */
@@ -313,9 +324,10 @@ typedef struct {
                                 raise its abort flag, let its copies and MMAs in flight finish, free
                                 its tensor memory and return; the solve then fails with RDM_ETIMEOUT
                                 and the handle stays usable. */
-    int32_t tc_hold;         /* 1: the tensor-core kernel's copy warp first waits for a device flag that
-                                nothing sets, so that its wait runs out (with tc_wait_cycles) and the
-                                solve returns RDM_ETIMEOUT without a fault */
+    int32_t tc_hold;         /* 1: the tensor-core kernel's MMA thread first waits for a device flag that
+                                nothing sets, so that its wait runs out (with tc_wait_cycles), the copy
+                                warp's wait for a free stage runs out after it and drains its copies,
+                                and the solve returns RDM_ETIMEOUT without a fault */
     int32_t tc_window_cols;  /* column window (a multiple of 32, at most 16,384) of the warp-parallel
                                 builders of the tensor-core tile and K-step lists; rows whose columns
                                 span more take the serial merges.  0 = 16,384.  Results do not depend

@@ -18,6 +18,7 @@
 #include <memory>
 #include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "../../include/rdm.h"
@@ -30,6 +31,15 @@ long long rdm::g_kernel_launches = 0;
 
 namespace {
 
+// one system's matrices at one block size: host patterns, device values
+struct SysMats {
+    int b = 0, nb = 0;
+    std::vector<int> rp, col;          // H0
+    DevBuf<double> val;
+    std::vector<int> rp1[3], col1[3];  // H1_dir
+    DevBuf<double> val1[3];
+};
+
 struct HostSys {
     bool has_h0 = false;
     int nb = 0, n = 0;
@@ -39,6 +49,7 @@ struct HostSys {
     bool has_h1[3] = {false, false, false};
     std::vector<int> rp1[3], col1[3];
     DevBuf<double> val1[3];
+    SysMats rb;                        // the same matrices at the solve's block size (when it differs)
 };
 
 struct SysState {
@@ -62,7 +73,13 @@ struct rdm_handle {
     std::string err;
     rdm_params prm;
     int S = 1;
-    int b = 0;
+    int b = 0;                 // block size of the uploaded matrices
+    int bs = 0;                // block size of the current solve (b, or the re-blocked size)
+    int tuned_b = 0;           // autotuner's choice for the uploaded problem (0: not tuned)
+    double autotune_ms = 0, probe_ms[3] = {0, 0, 0};
+    std::thread worker;        // rdm_solve_async
+    bool pending = false;
+    int async_status = 0;
     std::vector<HostSys> hs;
     std::vector<uint8_t> forced;
 
@@ -105,6 +122,9 @@ struct rdm_handle {
     std::vector<rdm_iter_log> log;
     std::vector<double> alpha;
     std::vector<int> final_rp;     // host copy of X row_ptr after the solve
+    // results in the uploaded block size when the solve ran at another one:
+    // pattern (row_ptr, col) per (system, matrix), made on first request
+    std::vector<std::pair<std::vector<int>, std::vector<int>>> conv;
     int64_t pool_cap_hint = 0;
 };
 
@@ -239,18 +259,55 @@ void upload_matrix(rdm_handle *h, const rdm_bsr *A, std::vector<int> &rp, std::v
 // assembly of the batch into global block-diagonal sets
 // ---------------------------------------------------------------------------
 
+// The matrices of system s at block size bs (the uploaded ones, or a
+// re-blocked copy made once and kept until the next upload).
+void ensure_reblocked(rdm_handle *h, int s, int bs) {
+    HostSys &y = h->hs[s];
+    if (bs == h->b || y.rb.b == bs) return;
+    SysMats &r = y.rb;
+    r.b = 0;
+    auto one = [&](const std::vector<int> &rp, const std::vector<int> &col, const double *val,
+                   std::vector<int> &orp, std::vector<int> &ocol, DevBuf<double> &oval) {
+        reblock_pattern(rp, col, h->b, y.n, bs, orp, ocol);
+        const int64_t nout = (int64_t)ocol.size();
+        std::vector<int> orow(nout);
+        for (int i = 0; i + 1 < (int)orp.size(); ++i)
+            for (int p = orp[i]; p < orp[i + 1]; ++p) orow[p] = i;
+        DevBuf<int> drp, dcol, dorow, docol;
+        drp.ensure(rp.size());
+        dcol.ensure(std::max<size_t>(col.size(), 1));
+        dorow.ensure(std::max<int64_t>(nout, 1));
+        docol.ensure(std::max<int64_t>(nout, 1));
+        h2d(drp.p, rp.data(), rp.size(), h->stream);
+        h2d(dcol.p, col.data(), col.size(), h->stream);
+        h2d(dorow.p, orow.data(), (size_t)nout, h->stream);
+        h2d(docol.p, ocol.data(), (size_t)nout, h->stream);
+        oval.ensure(std::max<int64_t>(nout, 1) * bs * bs);
+        launch_reblock_vals(drp.p, dcol.p, val, (int)rp.size() - 1, h->b, dorow.p, docol.p, oval.p, nout, bs,
+                            h->stream);
+        sync(h);
+    };
+    one(y.rp, y.col, y.val.p, r.rp, r.col, r.val);
+    for (int d = 0; d < 3; ++d)
+        if (y.has_h1[d]) one(y.rp1[d], y.col1[d], y.val1[d].p, r.rp1[d], r.col1[d], r.val1[d]);
+    r.nb = (int)r.rp.size() - 1;
+    r.b = bs;
+}
+
 void assemble(rdm_handle *h) {
     const int S = h->S;
     h->row0.assign(S, 0);
     h->nbs.assign(S, 0);
     h->norb.assign(S, 0);
     int NB = 0;
+    const bool rb = h->bs != h->b;
     for (int s = 0; s < S; ++s) {
         if (!h->hs[s].has_h0) throw Error{RDM_ESTATE, "H0 of system " + std::to_string(s) + " not uploaded"};
+        if (rb) ensure_reblocked(h, s, h->bs);
         h->row0[s] = NB;
-        h->nbs[s] = h->hs[s].nb;
+        h->nbs[s] = rb ? h->hs[s].rb.nb : h->hs[s].nb;
         h->norb[s] = h->hs[s].n;
-        NB += h->hs[s].nb;
+        NB += h->nbs[s];
     }
     h->NB = NB;
     // directions: the set uploaded for system 0; every system must match
@@ -262,7 +319,7 @@ void assemble(rdm_handle *h) {
             if (h->hs[s].has_h1[d] != h->hs[0].has_h1[d])
                 throw Error{RDM_EINVAL, "every system of a batch needs the same H1 directions"};
     h->nd = nd;
-    const int b = h->b;
+    const int b = h->bs;
     const size_t bb = (size_t)b * b;
 
     auto build = [&](MatSet &M, int nmat, auto get_rp, auto get_col, auto get_val) {
@@ -303,13 +360,20 @@ void assemble(rdm_handle *h) {
                 off += n;
             }
     };
-    build(h->H0, 1, [&](int s, int) -> const std::vector<int> & { return h->hs[s].rp; },
-          [&](int s, int) -> const std::vector<int> & { return h->hs[s].col; },
-          [&](int s, int) { return (const double *)h->hs[s].val.p; });
+    build(h->H0, 1, [&](int s, int) -> const std::vector<int> & { return rb ? h->hs[s].rb.rp : h->hs[s].rp; },
+          [&](int s, int) -> const std::vector<int> & { return rb ? h->hs[s].rb.col : h->hs[s].col; },
+          [&](int s, int) { return (const double *)(rb ? h->hs[s].rb.val.p : h->hs[s].val.p); });
     if (nd) {
-        build(h->H1, nd, [&](int s, int m) -> const std::vector<int> & { return h->hs[s].rp1[h->dirs[m]]; },
-              [&](int s, int m) -> const std::vector<int> & { return h->hs[s].col1[h->dirs[m]]; },
-              [&](int s, int m) { return (const double *)h->hs[s].val1[h->dirs[m]].p; });
+        build(h->H1, nd,
+              [&](int s, int m) -> const std::vector<int> & {
+                  return rb ? h->hs[s].rb.rp1[h->dirs[m]] : h->hs[s].rp1[h->dirs[m]];
+              },
+              [&](int s, int m) -> const std::vector<int> & {
+                  return rb ? h->hs[s].rb.col1[h->dirs[m]] : h->hs[s].col1[h->dirs[m]];
+              },
+              [&](int s, int m) {
+                  return (const double *)(rb ? h->hs[s].rb.val1[h->dirs[m]].p : h->hs[s].val1[h->dirs[m]].p);
+              });
     }
     // X0 has the pattern of H0, X1_g that of H1_g
     MatSet &X = h->X[0];
@@ -380,7 +444,7 @@ bool is_tc(Arith a) { return a == AR_BF16X3 || a == AR_FP16X3; }
 
 // the mixed modes need a block size that the tensor-core kernel handles
 bool tc_block_ok(int mode, int b) {
-    return !(mode == RDM_MODE_MIXED_BF16 || mode == RDM_MODE_MIXED_FP16) || b == 0 || b == 32;
+    return !(mode == RDM_MODE_MIXED_BF16 || mode == RDM_MODE_MIXED_FP16) || b == 0 || tc_block_size_ok(b);
 }
 
 // Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
@@ -392,11 +456,13 @@ bool tc_block_ok(int mode, int b) {
 // on the tensor cores for the fp16 mode (with the segmented accumulation of
 // the tensor-core kernel they are as accurate as FP32 CUDA-core products
 // there) and FP64 for the bf16 mode.
-void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0) {
+// The double-FP32 kernel takes 32 x 32 blocks only: with other block sizes the
+// fp16 mode's default X0^2 refinement is FP64.
+void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0, int b = 32) {
     if (refine_x1 == RDM_REFINE_DEFAULT)
         refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_SPLIT : RDM_REFINE_FP64;
     if (refine_x0 == RDM_REFINE_DEFAULT)
-        refine_x0 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_FP32X2 : RDM_REFINE_FP64;
+        refine_x0 = mode == RDM_MODE_MIXED_FP16 && b == 32 ? RDM_REFINE_FP32X2 : RDM_REFINE_FP64;
     for (int p = 0; p < njob; ++p) {
         Arith split = mode == RDM_MODE_MIXED_BF16 ? AR_BF16X3 : AR_FP16X3;
         switch (mode) {
@@ -568,7 +634,8 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     const int64_t nupper = hq[1];
 
     // Numeric phase, fused truncation and compaction, one group of
-    // consecutive super-rows (4 block rows of a job) at a time: the buffer of
+    // consecutive super-rows (the block rows of a tensor-core tile, 128 / b of
+    // them, of one job) at a time: the buffer of
     // untruncated blocks holds one group's upper slots.  A lower block's
     // upper partner lies in an earlier row, so it is in the same group or
     // already compacted; the result does not depend on the grouping.
@@ -591,10 +658,10 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         const size_t cap = std::min(avail, std::max(totm / 16, size_t(4) << 30));
         budget = std::max<int64_t>(1, (int64_t)(cap / slot_bytes));
     }
-    const int NB4 = (NB + 3) / 4, nunit = njob * NB4;
+    const int TR = tc_tile_rows(b), NBT = (NB + TR - 1) / TR, nunit = njob * NBT;
     auto unit_row = [&](int u) {   // first flat row of super-row unit u (u = nunit: nrows)
         if (u >= nunit) return nrows;
-        return (u / NB4) * NB + 4 * (u % NB4);
+        return (u / NBT) * NB + TR * (u % NBT);
     };
     std::vector<int> gunit{0};          // first unit of every group
     std::vector<int> hrp, hurp;         // host out_rp and upper ranks at row starts (several groups)
@@ -757,7 +824,7 @@ std::vector<double> stats(rdm_handle *h, MatSet &X) {
     const int nq = 3 + h->nd;
     h->row_part.ensure((size_t)nq * h->NB);
     h->sys_q.ensure((size_t)nq * h->S);
-    launch_row_stats(X.row_ptr.p, X.col.p, X.val.p, X.nmat, h->NB, h->b, h->H0.row_ptr.p,
+    launch_row_stats(X.row_ptr.p, X.col.p, X.val.p, X.nmat, h->NB, h->bs, h->H0.row_ptr.p,
                      h->H0.col.p, h->H0.val.p, h->row_part.p, h->stream);
     launch_sys_sum(h->row_part.p, nq, h->NB, h->sd.row0.p, h->sd.nbs.p, h->S, h->sys_q.p, h->stream);
     std::vector<double> q((size_t)nq * h->S);
@@ -769,12 +836,12 @@ std::vector<double> stats(rdm_handle *h, MatSet &X) {
 int run_solve(rdm_handle *h, rdm_info *info_out) {
     DeviceGuard dg(h->device);
     if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
-    if (!tc_block_ok(h->prm.mode, h->b))
-        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 blocks");
+    if (!tc_block_ok(h->prm.mode, h->bs))
+        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, 32 x 32 or 64 x 64 blocks");
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_kernel_launches;
     assemble(h);
-    const int S = h->S, NB = h->NB, nd = h->nd, b = h->b;
+    const int S = h->S, NB = h->NB, nd = h->nd, b = h->bs;
     const rdm_params &P = h->prm;
     cudaStream_t st = h->stream;
     const bool mixed = P.mode == RDM_MODE_MIXED_BF16 || P.mode == RDM_MODE_MIXED_FP16;
@@ -864,11 +931,14 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             const double stall_tol = P.stall_tol;
             y.e_hist.push_back(e);
             const size_t E = y.e_hist.size();
+            // stall window of the precision ladder (R10): |e_n| >= |e_{n-W}| / 2
+            const int W = P.stall_window > 0 ? P.stall_window : 2;
+            const bool stalled = (int)E >= W + 1 && fabs(e) >= 0.5 * fabs(y.e_hist[E - 1 - W]) &&
+                                 fabs(e) < 1e-2 * nocc[s];
             if (!stop && n >= std::max(3, P.min_iter) && E >= 3) {
+                // FP64: the oracle's stall stop (e not decreased over two iterations, below stall_tol)
                 if (!lowprec && stall_tol > 0 && e >= y.e_hist[E - 3] && e < stall_tol) stop = true;
-                if (lowprec && y.tier == final_tier && n - y.tier_start >= 2 &&
-                    fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) && fabs(e) < 1e-2 * nocc[s])
-                    stop = true;
+                if (lowprec && y.tier == final_tier && n - y.tier_start >= 2 && stalled) stop = true;
                 // mixed modes: X0 refined in FP64 is idempotent to 1e-10 per
                 // occupied state (four orders below the truncation error of any
                 // useful tau; the FP64 rounding floor is ~1e-12 per state)
@@ -889,8 +959,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                 continue;
             }
             // tier switch on idempotency stall (mixed modes)
-            if (mixed && y.tier < final_tier && E >= 3 && fabs(e) >= 0.5 * fabs(y.e_hist[E - 3]) &&
-                fabs(e) < 1e-2 * nocc[s]) {
+            if (mixed && y.tier < final_tier && stalled) {
                 y.tier++;
                 y.tier_start = n;
             }
@@ -936,7 +1005,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         Arith tab[kMaxTiers][kMaxJobs];
         unsigned tiers_present = 0;
         std::vector<int> tier_of(S, 0);
-        for (int t = 0; t <= final_tier; ++t) tier_arith(P.mode, t, jt.njob, tab[t], P.refine_x1, P.refine_x0);
+        for (int t = 0; t <= final_tier; ++t) tier_arith(P.mode, t, jt.njob, tab[t], P.refine_x1, P.refine_x0, b);
         for (int s = 0; s < S; ++s) {
             tier_of[s] = ss[s].tier;
             if (act[s]) tiers_present |= 1u << ss[s].tier;
@@ -1064,9 +1133,106 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         h->info[s].trace_error = q[(size_t)s * nq] - nocc[s];
         h->info[s].idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
     }
+    h->conv.assign((size_t)S * 4, {});
+    for (int s = 0; s < S; ++s) h->info[s].block_size = b;
     h->solved = true;
     if (info_out) *info_out = h->info[0];
     return all_conv ? RDM_OK : RDM_NOT_CONVERGED;
+}
+
+// The solve at the chosen block size: the uploaded b, rdm_params.block_size,
+// or (autotune) the fastest of one probe solve at each of 16, 32 and 64,
+// remembered until the next upload or parameter change.  A probe that runs
+// out of memory or pool capacity is skipped; any other error ends the call.
+int solve_entry(rdm_handle *h, rdm_info *info_out) {
+    DeviceGuard dg(h->device);
+    const rdm_params &P = h->prm;
+    if (h->hs.empty() || !h->b) return fail(h, RDM_ESTATE, "no system uploaded");
+    bool have_result = false;
+    int status = RDM_OK;
+    if (P.autotune && !h->tuned_b) {
+        const int cand[3] = {16, 32, 64};
+        const auto t0 = std::chrono::steady_clock::now();
+        double best = 0;
+        int best_b = 0, last_b = 0;
+        for (int k = 0; k < 3; ++k) {
+            h->probe_ms[k] = 0;
+            h->bs = cand[k];
+            int st;
+            try {
+                for (int sy = 0; sy < h->S; ++sy)
+                    if (h->hs[sy].has_h0) ensure_reblocked(h, sy, cand[k]);   // outside the timed solve
+                st = run_solve(h, nullptr);
+            } catch (const Error &e) {
+                st = e.code;
+                h->err = e.msg;
+            }
+            last_b = 0;
+            if (st == RDM_ENOMEM || st == RDM_ECAPACITY) continue;
+            if (st < 0) return st;
+            h->probe_ms[k] = h->info[0].time_ms;
+            last_b = cand[k];
+            status = st;
+            if (!best_b || h->probe_ms[k] < best) {
+                best = h->probe_ms[k];
+                best_b = cand[k];
+            }
+        }
+        h->autotune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (!best_b) return fail(h, RDM_ENOMEM, "autotune: no block size in {16, 32, 64} fits the device");
+        h->tuned_b = best_b;
+        have_result = last_b == best_b;   // the last probe already is the solve at the chosen size
+    } else if (!P.autotune) {
+        h->autotune_ms = 0;
+        for (double &x : h->probe_ms) x = 0;
+    }
+    if (!have_result) {
+        h->bs = P.autotune ? h->tuned_b : P.block_size > 0 ? P.block_size : h->b;
+        status = run_solve(h, nullptr);
+        if (status < 0) return status;
+    }
+    for (auto &I : h->info) {
+        I.autotune_ms = h->autotune_ms;
+        for (int k = 0; k < 3; ++k) I.probe_ms[k] = h->probe_ms[k];
+    }
+    if (info_out) *info_out = h->info[0];
+    return status;
+}
+
+// Wait for a solve started by rdm_solve_async (every call but rdm_sync,
+// rdm_last_error and the parameter-free queries does this first).
+void join_pending(rdm_handle *h) {
+    if (h && h->pending) {
+        if (h->worker.joinable()) h->worker.join();
+        h->pending = false;
+    }
+}
+
+// Pattern of matrix `mat` of system `sys` in the uploaded block size when the
+// solve ran at another one (cached until the next solve): host copies of the
+// solve's pattern, re-blocked.
+const std::pair<std::vector<int>, std::vector<int>> &uploaded_pattern(rdm_handle *h, int sys, int mat) {
+    auto &slot = h->conv[(size_t)sys * 4 + mat];
+    if (slot.first.empty()) {
+        const int NB = h->NB, r0 = h->row0[sys], nbs = h->nbs[sys];
+        const int *rp = h->final_rp.data() + (size_t)mat * NB;
+        const int64_t first = rp[r0], n = rp[r0 + nbs] - first;
+        std::vector<int> lrp(nbs + 1), lcol(n);
+        for (int i = 0; i <= nbs; ++i) lrp[i] = (int)(rp[r0 + i] - first);
+        d2h(lcol.data(), h->X[h->cur].col.p + first, (size_t)n, h->stream);
+        sync(h);
+        for (auto &c : lcol) c -= r0;
+        reblock_pattern(lrp, lcol, h->bs, h->norb[sys], h->b, slot.first, slot.second);
+    }
+    return slot;
+}
+
+int64_t result_nnzb(rdm_handle *h, int sys, int mat) {
+    if (h->bs == h->b) {
+        const int *rp = h->final_rp.data() + (size_t)mat * h->NB;
+        return rp[h->row0[sys] + h->nbs[sys]] - rp[h->row0[sys]];
+    }
+    return (int64_t)uploaded_pattern(h, sys, mat).second.size();
 }
 
 int get_matrix(rdm_handle *h, int sys, int mat, rdm_bsr_out *out) {
@@ -1075,13 +1241,14 @@ int get_matrix(rdm_handle *h, int sys, int mat, rdm_bsr_out *out) {
     if (!out) return fail(h, RDM_EINVAL, "null output");
     DeviceGuard dg(h->device);
     MatSet &X = h->X[h->cur];
-    const int NB = h->NB, r0 = h->row0[sys], nbs = h->nbs[sys], b = h->b;
-    const size_t bb = (size_t)b * b;
+    const int NB = h->NB, r0 = h->row0[sys], nbs = h->nbs[sys], bs = h->bs;
+    const size_t bbs = (size_t)bs * bs;
     const int *rp = h->final_rp.data() + (size_t)mat * NB;
-    int64_t first = rp[r0], last = rp[r0 + nbs];
-    int64_t n = last - first;
-    out->nb = nbs;
-    out->b = b;
+    const int64_t first = rp[r0], last = rp[r0 + nbs];
+    const bool conv = bs != h->b;
+    const int64_t n = conv ? result_nnzb(h, sys, mat) : last - first;
+    out->nb = conv ? h->hs[sys].nb : nbs;
+    out->b = h->b;
     out->n = h->norb[sys];
     if (!out->row_ptr) {   // size query
         out->nnzb = n;
@@ -1091,11 +1258,43 @@ int get_matrix(rdm_handle *h, int sys, int mat, rdm_bsr_out *out) {
         out->nnzb = n;
         return fail(h, RDM_EINVAL, "output capacity too small (need " + std::to_string(n) + " blocks)");
     }
-    for (int i = 0; i <= nbs; ++i) out->row_ptr[i] = (int)(rp[r0 + i] - first);
-    d2h(out->col_idx, X.col.p + first, (size_t)n, h->stream);
-    d2h(out->vals, X.val.p + first * bb, (size_t)n * bb, h->stream);
+    if (!conv) {
+        for (int i = 0; i <= nbs; ++i) out->row_ptr[i] = (int)(rp[r0 + i] - first);
+        d2h(out->col_idx, X.col.p + first, (size_t)n, h->stream);
+        d2h(out->vals, X.val.p + first * bbs, (size_t)n * bbs, h->stream);
+        sync(h);
+        for (int64_t p = 0; p < n; ++p) out->col_idx[p] -= r0;
+        out->nnzb = n;
+        return RDM_OK;
+    }
+    // the solve ran at block size bs: the matrix goes back to the uploaded b
+    const auto &pat = uploaded_pattern(h, sys, mat);
+    const int b = h->b, nbu = (int)pat.first.size() - 1;
+    std::vector<int> lrp(nbs + 1), orow(n);
+    for (int i = 0; i <= nbs; ++i) lrp[i] = (int)(rp[r0 + i] - first);
+    for (int i = 0; i < nbu; ++i)
+        for (int p = pat.first[i]; p < pat.first[i + 1]; ++p) orow[p] = i;
+    DevBuf<int> drp, dcol, dorow, docol;
+    DevBuf<double> dval;
+    drp.ensure(nbs + 1);
+    dcol.ensure(std::max<int64_t>(last - first, 1));
+    dorow.ensure(std::max<int64_t>(n, 1));
+    docol.ensure(std::max<int64_t>(n, 1));
+    dval.ensure(std::max<int64_t>(n, 1) * b * b);
+    h2d(drp.p, lrp.data(), lrp.size(), h->stream);
+    // the solve's columns are global (row0 offset): local copies for the kernel
+    std::vector<int> lcol(last - first);
+    d2h(lcol.data(), X.col.p + first, lcol.size(), h->stream);
     sync(h);
-    for (int64_t p = 0; p < n; ++p) out->col_idx[p] -= r0;
+    for (auto &c : lcol) c -= r0;
+    h2d(dcol.p, lcol.data(), lcol.size(), h->stream);
+    h2d(dorow.p, orow.data(), (size_t)n, h->stream);
+    h2d(docol.p, pat.second.data(), (size_t)n, h->stream);
+    launch_reblock_vals(drp.p, dcol.p, X.val.p + first * bbs, nbs, bs, dorow.p, docol.p, dval.p, n, b, h->stream);
+    d2h(out->vals, dval.p, (size_t)n * b * b, h->stream);
+    sync(h);
+    for (int i = 0; i <= nbu; ++i) out->row_ptr[i] = pat.first[i];
+    std::copy(pat.second.begin(), pat.second.end(), out->col_idx);
     out->nnzb = n;
     return RDM_OK;
 }
@@ -1123,6 +1322,7 @@ int rdm_default_params(rdm_params *p) {
     p->min_iter = 1;
     p->use_graphs = 0;
     p->verbose = 0;
+    p->stall_window = 2;
     return RDM_OK;
 }
 
@@ -1155,6 +1355,7 @@ int rdm_create(rdm_handle **out, int device, void *cuda_stream) {
 
 int rdm_destroy(rdm_handle *h) {
     if (!h) return RDM_OK;
+    join_pending(h);
     {
         int prev = -1;
         cudaGetDevice(&prev);
@@ -1173,22 +1374,28 @@ const char *rdm_last_error(const rdm_handle *h) {
 
 int rdm_set_params(rdm_handle *h, const rdm_params *p) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!p) return fail(h, RDM_EINVAL, "null params");
     if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 3 ||
         !(p->spin_factor > 0) || p->min_iter < 0 || p->refine_x1 < 0 || p->refine_x1 > 4 ||
         p->refine_x0 < 0 || p->refine_x0 > 4 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
-        p->use_graphs != 0)
+        p->use_graphs != 0 || p->stall_window < 0 || p->block_size < 0 || p->block_size > 64 ||
+        (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1)
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
-                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0, use_graphs 0)");
-    if (!tc_block_ok(p->mode, h->b))
-        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 "
-                                   "blocks (the uploaded matrices have b = " + std::to_string(h->b) + ")");
+                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0, use_graphs 0, "
+                                   "stall_window >= 0, block_size 0 or a power of two <= 64, autotune 0 or 1)");
+    if (!tc_block_ok(p->mode, p->autotune ? 32 : p->block_size > 0 ? p->block_size : h->b))
+        return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, "
+                                   "32 x 32 or 64 x 64 blocks (the uploaded matrices have b = " + std::to_string(h->b) +
+                                   "; rdm_params.block_size or autotune can re-block them)");
     h->prm = *p;
+    h->tuned_b = 0;
     return RDM_OK;
 }
 
 int rdm_batch_create(rdm_handle *h, int n_systems) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (n_systems < 1 || n_systems > 65536) return fail(h, RDM_EINVAL, "n_systems out of range");
     return guarded(h, [&] {
         DeviceGuard dg(h->device);
@@ -1196,6 +1403,7 @@ int rdm_batch_create(rdm_handle *h, int n_systems) {
         h->hs.resize(n_systems);
         h->S = n_systems;
         h->b = 0;
+        h->tuned_b = 0;
         h->solved = false;
         return RDM_OK;
     });
@@ -1203,15 +1411,16 @@ int rdm_batch_create(rdm_handle *h, int n_systems) {
 
 int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
     return guarded(h, [&] {
         DeviceGuard dg(h->device);
         if (!H0) return fail(h, RDM_EINVAL, "null matrix");
         if (n_electrons <= 0 || (n_electrons & 1) || n_electrons / 2 >= H0->n)
             return fail(h, RDM_EINVAL, "electron count must be even with 0 < N_e/2 < n");
-        if (!tc_block_ok(h->prm.mode, H0->b))
-            return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 32 x 32 "
-                                       "blocks; set another mode first to upload b = " + std::to_string(H0->b));
+        if (!h->prm.autotune && !h->prm.block_size && !tc_block_ok(h->prm.mode, H0->b))
+            return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, "
+                                       "32 x 32 or 64 x 64 blocks; set another mode first to upload b = " + std::to_string(H0->b));
         HostSys &y = h->hs[sys];
         int saved_b = h->b;
         if (h->S == 1) h->b = 0;
@@ -1222,6 +1431,8 @@ int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons
             throw;
         }
         y.has_h0 = true;
+        y.rb = SysMats{};
+        h->tuned_b = 0;
         y.nb = H0->nb;
         y.n = H0->n;
         y.n_elec = n_electrons;
@@ -1235,6 +1446,7 @@ int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons
 
 int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
     if (dir < 0 || dir > 2) return fail(h, RDM_EINVAL, "direction must be 0, 1 or 2");
     return guarded(h, [&] {
@@ -1246,6 +1458,8 @@ int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1) {
             return fail(h, RDM_EINVAL, "H1 must have the same nb, b and n as H0");
         upload_matrix(h, H1, y.rp1[dir], y.col1[dir], y.val1[dir], false);
         y.has_h1[dir] = true;
+        y.rb = SysMats{};
+        h->tuned_b = 0;
         h->solved = false;
         return RDM_OK;
     });
@@ -1253,6 +1467,7 @@ int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1) {
 
 int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (len < 0 || (len > 0 && !seq)) return fail(h, RDM_EINVAL, "bad branch sequence");
     for (int i = 0; i < len; ++i)
         if (seq[i] != 1 && seq[i] != 2) return fail(h, RDM_EINVAL, "branches must be 1 or 2");
@@ -1262,11 +1477,35 @@ int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len) {
 
 int rdm_solve(rdm_handle *h, rdm_info *info) {
     if (!h) return RDM_EINVAL;
-    return guarded(h, [&] { return run_solve(h, info); });
+    join_pending(h);
+    return guarded(h, [&] { return solve_entry(h, info); });
+}
+
+int rdm_solve_async(rdm_handle *h) {
+    if (!h) return RDM_EINVAL;
+    join_pending(h);
+    if (h->hs.empty() || !h->b) return fail(h, RDM_ESTATE, "no system uploaded");
+    h->async_status = RDM_OK;
+    try {
+        h->worker = std::thread([h] { h->async_status = guarded(h, [&] { return solve_entry(h, nullptr); }); });
+    } catch (const std::exception &e) {
+        return fail(h, RDM_EINVAL, std::string("cannot start the solve thread: ") + e.what());
+    }
+    h->pending = true;
+    return RDM_OK;
+}
+
+int rdm_sync(rdm_handle *h, rdm_info *info) {
+    if (!h) return RDM_EINVAL;
+    if (!h->pending) return fail(h, RDM_ESTATE, "no solve in flight");
+    join_pending(h);
+    if (info && h->solved && h->async_status >= 0) *info = h->info[0];
+    return h->async_status;
 }
 
 int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     rdm_test_knobs z{};
     if (!k) k = &z;
     if (k->tc_wait_cycles < 0 || k->tc_hold < 0 || k->tc_hold > 1 || k->tc_window_cols < 0 ||
@@ -1280,6 +1519,7 @@ int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k) {
 
 int rdm_get_info(rdm_handle *h, int sys, rdm_info *info) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
     if (sys < 0 || sys >= h->S || !info) return fail(h, RDM_EINVAL, "bad system index or null output");
     *info = h->info[sys];
@@ -1288,31 +1528,40 @@ int rdm_get_info(rdm_handle *h, int sys, rdm_info *info) {
 
 int rdm_get_p0_nnzb(rdm_handle *h, int sys, int64_t *nnzb) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
     if (sys < 0 || sys >= h->S || !nnzb) return fail(h, RDM_EINVAL, "bad system index or null output");
-    *nnzb = h->info[sys].nnzb_p0;
-    return RDM_OK;
+    return guarded(h, [&] {
+        DeviceGuard dg(h->device);
+        *nnzb = result_nnzb(h, sys, 0);
+        return RDM_OK;
+    });
 }
 
 int rdm_get_p1_nnzb(rdm_handle *h, int sys, int dir, int64_t *nnzb) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
     if (sys < 0 || sys >= h->S || !nnzb || dir < 0 || dir > 2) return fail(h, RDM_EINVAL, "bad index or null output");
     for (int d = 0; d < h->nd; ++d)
-        if (h->dirs[d] == dir) {
-            *nnzb = h->info[sys].nnzb_p1[dir];
-            return RDM_OK;
-        }
+        if (h->dirs[d] == dir)
+            return guarded(h, [&] {
+                DeviceGuard dg(h->device);
+                *nnzb = result_nnzb(h, sys, 1 + d);
+                return RDM_OK;
+            });
     return fail(h, RDM_EINVAL, "direction was not uploaded");
 }
 
 int rdm_get_p0(rdm_handle *h, int sys, rdm_bsr_out *out) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     return guarded(h, [&] { return get_matrix(h, sys, 0, out); });
 }
 
 int rdm_get_p1(rdm_handle *h, int sys, int dir, rdm_bsr_out *out) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     return guarded(h, [&] {
         for (int d = 0; d < h->nd; ++d)
             if (h->dirs[d] == dir) return get_matrix(h, sys, 1 + d, out);
@@ -1322,6 +1571,7 @@ int rdm_get_p1(rdm_handle *h, int sys, int dir, rdm_bsr_out *out) {
 
 int rdm_get_alpha(rdm_handle *h, int sys, double alpha[9]) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!h->solved) return fail(h, RDM_ESTATE, "no solve result");
     if (sys < 0 || sys >= h->S || !alpha) return fail(h, RDM_EINVAL, "bad system index or null output");
     for (int k = 0; k < 9; ++k) alpha[k] = h->alpha[(size_t)sys * 9 + k];
@@ -1330,6 +1580,7 @@ int rdm_get_alpha(rdm_handle *h, int sys, double alpha[9]) {
 
 int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     if (!n || (cap > 0 && !out)) return fail(h, RDM_EINVAL, "null output");
     int m = std::min<int>(cap, (int)h->log.size());
     for (int k = 0; k < m; ++k) out[k] = h->log[k];
@@ -1341,6 +1592,7 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
                       double c_lin, double c_sq, int terms, double tau, int mode,
                       rdm_bsr_out *out, int64_t *needed) {
     if (!h) return RDM_EINVAL;
+    join_pending(h);
     return guarded(h, [&]() -> int {
         DeviceGuard dg(h->device);
         if (!A || (terms == 2 && !B)) return fail(h, RDM_EINVAL, "null operand");

@@ -1,55 +1,59 @@
-// Tensor-core numeric phase (tcgen05 + TMEM, sm_103a) for 32 x 32 blocks.
+// Tensor-core numeric phase (tcgen05 + TMEM, sm_103a) for b x b blocks,
+// b = 16, 32 or 64.
 //
 // Work decomposition.  Output blocks are grouped in 128 x 256 super-tiles:
-// block rows 4I..4I+3 times 8 block columns taken, in increasing order, from
-// the columns that these rows need (upper triangle of the mask), so that every
-// tile column is needed by at least one tile row.  A super-tile is
-// one MMA accumulator: D[128 x 256] = sum over K-steps of A[128 x 32] B[256 x 32]^T
-// where a K-step is one block index k at which some row of the tile's A rows
-// and some row of its B rows have a stored block (Gustavson's row merge,
-// Algorithm 1, lifted to a 4 x 8 block tile).  Missing blocks are zero.  The
-// X1 products (X0 X1 + X1 X0) simply concatenate the K-steps of both terms.
-// The tile is as wide as one MMA allows because operand bytes bound the
-// kernel: a K-step brings 12 blocks (48 KB) for 128 x 256 x 32 of MMA work,
-// against 8 blocks (32 KB) for 128 x 128 x 32 with 4 x 4 tiles; on the masks
-// of the 2,000-atom cluster the 4 x 8 tiles copied ~20% fewer bytes per
-// product and ran the products 29% faster than 4 x 4 tiles.
+// TBM = 128/b block rows times TBN = 256/b block columns taken, in increasing
+// order, from the columns that these rows need (upper triangle of the mask),
+// so that every tile column is needed by at least one tile row.  A super-tile
+// is one MMA accumulator: D[128 x 256] = sum over K-steps of A[128 x b]
+// B[256 x b]^T where a K-step is one block index k at which some row of the
+// tile's A rows and some row of its B rows have a stored block (Gustavson's
+// row merge, Algorithm 1, lifted to a TBM x TBN block tile).  Missing blocks
+// are zero.  The X1 products (X0 X1 + X1 X0) simply concatenate the K-steps
+// of both terms.  The tile is as wide as one MMA allows because operand bytes
+// bound the kernel: a K-step brings (128 + 256) x b operand elements for
+// 128 x 256 x b of MMA work whatever b is; at b = 32 on the masks of the
+// 2,000-atom cluster the 4 x 8 tiles copied ~20% fewer bytes per product and
+// ran the products 29% faster than 4 x 4 tiles.
 //
 // Split precision.  Every operand block is stored as a hi and a lo plane
-// (bf16 or fp16, hi = rn(x), lo = rn(x - hi)); one K-step issues the products
-// hi*hi + hi*lo + lo*hi (2 MMAs of K = 16 each), all accumulated in FP32 in
+// (bf16 or fp16, hi = rn(x), lo = rn(x - hi)); every K = 16 slice of a K-step
+// issues the products hi*hi + hi*lo + lo*hi, all accumulated in FP32 in
 // tensor memory.  The operand planes are laid out in global memory in the
 // canonical K-major core-matrix order of the MMA (8 rows x 16 bytes per core
 // matrix, core matrices adjacent along K 128 bytes apart), with the 8-row
-// groups of a block's hi and lo planes alternating (512 bytes each, 1 KB
-// between the groups of one plane): one 4 KB bulk copy per block lands both
-// planes ready for the MMA; interleaving halved the copies.  A streaming
-// probe (one CTA per SM, no MMA) moves at most ~6.5 TB/s over the GPU in
-// 4 KB bulk copies, from L2 as from DRAM, and ~7.4-8.9 TB/s in 16-32 KB
-// copies: the rate of such copies into each SM bounds this kernel.
+// groups of a block's hi and lo planes alternating (16 b bytes each, 32 b
+// bytes between the groups of one plane): one bulk copy of 4 b^2 bytes per
+// block lands both planes ready for the MMA, and blocks stacked in a stage
+// continue the same stride, so that a side of a K-step is one operand.  A
+// streaming probe (one CTA per SM, no MMA) moves at most ~6.5 TB/s over the
+// GPU in 4 KB bulk copies, from L2 as from DRAM, and ~7.4-8.9 TB/s in
+// 16-32 KB copies: the rate of such copies into each SM bounds this kernel.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over a static tile
-// schedule): warp 0 issues the bulk copies into a 4-stage ring of 48 KB
-// stages, warp 1 owns the tensor-memory allocation and one thread issues the
-// MMAs, warps 2-9 (two per TMEM lane quarter = block row of the tile, four
-// block columns each) run the epilogue.  Ten warps put three on some SM
-// sub-partitions, which caps a thread at 168 registers: the epilogue keeps
-// its 128 accumulators in registers and parks the tile metadata in shared
-// memory.  An L2 prefetch of the blocks eight K-steps ahead (one extra bulk
-// request per block) made the kernel 13% slower: bulk requests are scarce.
+// schedule): warp 0 issues the bulk copies into a ring of stages, warp 1
+// owns the tensor-memory allocation and one thread issues the MMAs, warps
+// 2-9 (two per TMEM lane quarter, 128 accumulator columns each) run the
+// epilogue.  Ten warps put three on some SM sub-partitions, which caps a
+// thread at 168 registers: the epilogue keeps its 128 accumulators in
+// registers and parks the tile metadata in shared memory.  At b = 64 an
+// output block spans two lane quarters, so the two warps that share its
+// columns combine their halves (norm, transpose of diagonal blocks) through
+// shared memory, synchronised by a bounded mbarrier handshake.
 //
 // Accumulation in segments.  The tensor cores' FP32 accumulation truncates
 // (it is not round-to-nearest), so a long accumulation chain drifts towards
-// zero: measured on positive data, -2e-7 relative per K-step, -2e-5 after 96
-// K-steps.  The K-steps of a tile are therefore accumulated in segments of
-// kSegSteps in fresh TMEM accumulators (2 rotating buffers of 256 columns);
-// the epilogue warps add every finished segment to registers with
-// round-to-nearest FP32 adds and release the buffer.  The drift is then that
-// of one segment (-7e-7 relative), independent of the tile's length.  After
-// the last segment: C = c_lin X + c_sq D, diagonal blocks symmetrised, block
-// Frobenius norm, truncation flag, FP64 store of the (upper-triangle) block.
-// Every mbarrier wait is bounded: on timeout the kernel raises an error flag,
-// drains what it issued and frees its tensor memory.
+// zero: measured on positive data, -2e-7 relative per 32-deep K-step, -2e-5
+// after 96 of them.  The K-steps of a tile are therefore accumulated in
+// segments of 128 K (kSegSteps K-steps) in fresh TMEM accumulators (2
+// rotating buffers of 256 columns); the epilogue warps add every finished
+// segment to registers with round-to-nearest FP32 adds and release the
+// buffer.  The drift is then that of one segment (-7e-7 relative),
+// independent of the tile's length.  After the last segment:
+// C = c_lin X + c_sq D, diagonal blocks symmetrised, block Frobenius norm,
+// truncation flag, FP64 store of the (upper-triangle) block.  Every wait is
+// bounded: on timeout the kernel raises an error flag, drains what it issued
+// and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -60,30 +64,57 @@
 namespace rdm {
 namespace {
 
-constexpr int TB = 32;                       // block size handled here
-constexpr int TBM = 4;                       // block rows per super-tile (MMA M = 128)
-constexpr int TBN = 8;                       // block columns per super-tile
-constexpr int kTileN = TBN * TB;             // MMA N = accumulator columns in tensor memory
-constexpr int kSlots = TBM + TBN;            // operand blocks per K-step: A rows, then B rows
-constexpr int kStages = TBN == 8 ? 4 : 7;    // ring stages: 4 x 48 KB beside the epilogue staging (fit checked below)
-constexpr int kPlaneElems = TB * TB;         // 1024 bf16 per block plane
-constexpr int kPlaneBytes = kPlaneElems * 2; // 2048
-constexpr int kPairBytes = 2 * kPlaneBytes;  // hi and lo planes of one block, interleaved: 4 KB
-constexpr int kSideABytes = TBM * kPairBytes;    // A side: TBM blocks stacked
-constexpr int kStageBytes = kSlots * kPairBytes; // A side, then the TBN blocks of the B side
+// geometry of the tiles for block size B
+template <int B>
+struct Geo {
+    static constexpr int TBM = 128 / B;                 // block rows per super-tile (MMA M = 128)
+    static constexpr int TBN = 256 / B;                 // block columns per super-tile (MMA N = 256)
+    static constexpr int kSlots = TBM + TBN;            // operand blocks per K-step: A rows, then B rows
+    static constexpr int kPlaneElems = B * B;           // elements of one plane of a block
+    static constexpr int kPairBytes = 4 * B * B;        // hi and lo planes of one block, interleaved
+    static constexpr int kSideABytes = TBM * kPairBytes;    // A side of a stage: TBM blocks stacked
+    static constexpr int kStageBytes = kSlots * kPairBytes; // A side, then the TBN blocks of the B side
+    static constexpr int kStages = B == 16 ? 7 : B == 32 ? 4 : 2;   // fit checked below
+    static constexpr int kColOff = 4 + TBM * TBN;       // tile record: job, super-row, -, nsteps,
+    static constexpr int kTileInts = kColOff + TBN;     //   mask slot[TBM x TBN], column j of each tile column
+    static constexpr int kSegSteps = 128 / B;           // K-steps per accumulation segment (128 K)
+    static constexpr int kSub = B / 16;                 // MMAs of K = 16 per K-step and product
+    static constexpr uint32_t kSBO = 32 * B;            // bytes between the 8-row groups of one plane
+    static constexpr uint32_t kLoOff = 16 * B;          // bytes from a group's hi part to its lo part
+    static_assert(kSlots <= 32, "one producer lane per slot");
+};
+
+constexpr int kTileN = 256;                  // MMA N = accumulator columns in tensor memory
 constexpr int kEpiWarps = 8;                 // epilogue warps: 2 per TMEM lane quarter
-constexpr int kColBlocks = TBN / 2;          // block columns per epilogue warp
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kColOff = 4 + TBM * TBN;       // tile record: job, super-row, -, nsteps, mask slot[TBM x TBN],
-constexpr int kTileInts = kColOff + TBN;     //   then column j of each tile column
-constexpr int kSegSteps = 4;                 // K-steps accumulated in tensor memory per segment
 constexpr int kSegBufs = 512 / kTileN;       // segment accumulators: the 512 TMEM columns
-static_assert(kSlots <= 32 && kSegBufs >= 2 && (kSegBufs & (kSegBufs - 1)) == 0, "tile shape");
+// epilogue metadata per warp (8 words per output block): at b = 32 and 64
+// (4 and 2 blocks per warp) it is parked in the padding column of the warp's
+// 32 x 33 staging tile; at b = 16 (16 blocks per warp) in a region of its own
+template <int B>
+constexpr int meta_words() { return B == 16 ? 16 * 8 : 0; }
+template <int B>
+constexpr int meta_stride() { return B == 16 ? 1 : 33; }
+static_assert(kSegBufs >= 2 && (kSegBufs & (kSegBufs - 1)) == 0, "tile shape");
 constexpr long long kWaitCycles = 4000000000LL;   // default bound of a wait: ~2 s at 2 GHz
 
 // Stays 0 for the life of the program: the test setting `hold` makes the
 // producer wait for it, so that every wait of the kernel runs out.
 __device__ int g_never_set = 0;
+
+// Test setting `hold`: the MMA thread first waits (bounded) for g_never_set;
+// the wait runs out and raises the abort flag before any MMA is issued, so
+// the copy warp's wait for a free stage runs out too and it drains the copies
+// it has in flight.  Kept out of line: inlined ahead of the loops it slowed
+// the kernel down twofold.
+__device__ __noinline__ void hold_until_timeout(volatile int *abort_flag, long long limit) {
+    const long long t0 = clock64();
+    while (*(volatile int *)&g_never_set == 0)
+        if (clock64() - t0 > limit) {
+            *abort_flag = 1;
+            return;
+        }
+}
 
 // ---------------------------------------------------------------------------
 // PTX helpers
@@ -176,12 +207,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // ---------------------------------------------------------------------------
 // operand planes: hi/lo split in the K-major core-matrix layout
 // ---------------------------------------------------------------------------
+template <int B>
 __device__ __forceinline__ int pair_offset(int r, int c, int plane) {
-    // element (r, c) of plane `plane` (0 hi, 1 lo) of a 32 x 32 block: the two
-    // planes' 8-row groups alternate (512 bytes each), so that one 4 KB copy
-    // brings both and both are K-major core-matrix operands with a 1 KB stride
-    // between 8-row groups; inside a group, core matrix (c/8) at 64 elements
-    return ((r >> 3) << 9) + (plane << 8) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7);
+    // element (r, c) of plane `plane` (0 hi, 1 lo) of a B x B block: the two
+    // planes' 8-row groups alternate (8 B elements each), so that one copy
+    // brings both and both are K-major core-matrix operands with a 32 B-byte
+    // stride between 8-row groups; inside a group, core matrix (c/8) at 64
+    // elements
+    return (r >> 3) * (16 * B) + plane * (8 * B) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7);
 }
 
 // per matrix m: scale[m] = 2^floor(log2(2^14 / max block norm)) for fp16 (the
@@ -212,19 +245,20 @@ __global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__rest
 
 // one thread per 8 consecutive elements of a block row (one core-matrix row):
 // 64 bytes of FP64 in, 16 bytes of hi and 16 bytes of lo out
-template <bool BF16>
+template <bool BF16, int B>
 __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
                                const float *__restrict__ scale,
                                const int *__restrict__ mat_first, int nmat) {
+    constexpr int kPE = B * B;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nblk * (kPlaneElems / 8)) return;
-    const int64_t p = g / (kPlaneElems / 8);
-    const int rc0 = (int)(g % (kPlaneElems / 8)) * 8;     // first element (row r, columns c0..c0+7)
-    const int r = rc0 >> 5, c0 = rc0 & 31;
+    if (g >= nblk * (kPE / 8)) return;
+    const int64_t p = g / (kPE / 8);
+    const int rc0 = (int)(g % (kPE / 8)) * 8;     // first element (row r, columns c0..c0+7)
+    const int r = rc0 / B, c0 = rc0 % B;
     int m = 0;
     while (m + 1 < nmat && p >= mat_first[m + 1]) ++m;
     const float sc = scale[m];
-    const double2 *v2 = reinterpret_cast<const double2 *>(val + p * kPlaneElems + rc0);
+    const double2 *v2 = reinterpret_cast<const double2 *>(val + p * kPE + rc0);
     uint16_t h[8], l[8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -252,9 +286,9 @@ __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uin
     lv.x = l[0] | ((uint32_t)l[1] << 16); lv.y = l[2] | ((uint32_t)l[3] << 16);
     lv.z = l[4] | ((uint32_t)l[5] << 16); lv.w = l[6] | ((uint32_t)l[7] << 16);
     // columns c0..c0+7 of row r are 8 consecutive elements of one core matrix
-    uint16_t *o = hi + p * (2 * kPlaneElems);
-    *reinterpret_cast<uint4 *>(o + pair_offset(r, c0, 0)) = hv;
-    *reinterpret_cast<uint4 *>(o + pair_offset(r, c0, 1)) = lv;
+    uint16_t *o = hi + p * (2 * kPE);
+    *reinterpret_cast<uint4 *>(o + pair_offset<B>(r, c0, 0)) = hv;
+    *reinterpret_cast<uint4 *>(o + pair_offset<B>(r, c0, 1)) = lv;
 }
 
 // ---------------------------------------------------------------------------
@@ -263,13 +297,13 @@ __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uin
 struct TileBuild {
     const int *rp;       // input set row_ptr (flat)
     const int *col;
-    int NB, NB4;
+    int NB, NBT;         // block rows, super-rows (ceil(NB / TBM))
     JobTable jt;
     const int *out_rp;   // mask row_ptr (flat, njob*NB+1)
     const int *mcol;     // mask columns
     const int *sys_of_row, *active, *sys_tier;
     JobMask job_mask;    // jobs computed on the tensor cores, per tier
-    int u0, u1;          // super-row units (job * NB4 + I) of this plan
+    int u0, u1;          // super-row units (job * NBT + I) of this plan
     int *tile_cnt;       // [u1 - u0]
     const int *tile_off; // scanned
     int *tiles;          // [ntile * kTileInts]
@@ -280,10 +314,11 @@ struct TileBuild {
     int max_words;       // bitmap window in 32-column words (<= 512); wider windows: serial merge
 };
 
-// upper mask range [cur, end) of block row 4I + m of job p, empty for rows
+// upper mask range [cur, end) of block row TBM I + m of job p, empty for rows
 // whose system is converged or whose job is not computed on the tensor cores
+template <int B>
 __device__ __forceinline__ void tile_row_range(const TileBuild &T, int p, int I, int m, int &cur, int &end) {
-    const int i = TBM * I + m;
+    const int i = Geo<B>::TBM * I + m;
     cur = end = 0;
     if (i >= T.NB) return;
     int lo = T.out_rp[p * T.NB + i], hi = T.out_rp[p * T.NB + i + 1];
@@ -302,28 +337,31 @@ __device__ __forceinline__ void tile_row_range(const TileBuild &T, int p, int I,
 }
 
 // Tiles of one (job, super-row), warp-parallel: the upper mask columns of
-// block rows 4I..4I+3 are marked in a shared-memory bitmap over their column
+// the TBM block rows are marked in a shared-memory bitmap over their column
 // window; the rank of a column among the distinct ones (prefix popcounts)
 // gives its tile (rank / TBN) and tile column (rank % TBN).  Windows wider
-// than the bitmap fall back to a serial 4-way merge by lane 0 (count or fill).
+// than the bitmap fall back to a serial merge by lane 0 (count or fill).
 constexpr int kTileRowWarps = 8, kTileRowWords = 512;   // 16,384 columns per window
+template <int B>
 __device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
                                  int fill);
+template <int B>
 __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, int fill) {
+    using G = Geo<B>;
     __shared__ unsigned bits_s[kTileRowWarps][kTileRowWords];
     __shared__ int rank_s[kTileRowWarps][kTileRowWords];
     const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = T.u0 + blockIdx.x * kTileRowWarps + wq;
     if (t >= T.u1) return;
-    const int p = t / T.NB4, I = t % T.NB4;
+    const int p = t / T.NBT, I = t % T.NBT;
     unsigned *bm = bits_s[wq];
     int *wr = rank_s[wq];
     int c0 = 0, e0 = 0;
-    if (lane < TBM) tile_row_range(T, p, I, lane, c0, e0);
-    int cur[TBM], end[TBM];
+    if (lane < G::TBM) tile_row_range<B>(T, p, I, lane, c0, e0);
+    int cur[G::TBM], end[G::TBM];
     int lo = 0x7fffffff, hi = -1;
 #pragma unroll
-    for (int m = 0; m < TBM; ++m) {
+    for (int m = 0; m < G::TBM; ++m) {
         cur[m] = __shfl_sync(0xffffffffu, c0, m);
         end[m] = __shfl_sync(0xffffffffu, e0, m);
         if (cur[m] < end[m]) {
@@ -338,13 +376,13 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
     }
     const int nw = ((hi - lo) >> 5) + 1;
     if (nw > T.max_words) {
-        if (lane == 0) tile_rows_serial(T, t, p, I, cur, end, fill);
+        if (lane == 0) tile_rows_serial<B>(T, t, p, I, cur, end, fill);
         return;
     }
     for (int w = lane; w < nw; w += 32) bm[w] = 0u;
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < TBM; ++m)
+    for (int m = 0; m < G::TBM; ++m)
         for (int e = cur[m] + lane; e < end[m]; e += 32) {
             const int j = T.mcol[e] - lo;
             atomicOr(&bm[j >> 5], 1u << (j & 31));
@@ -365,62 +403,65 @@ __global__ void __launch_bounds__(32 * kTileRowWarps) k_tile_rows(TileBuild T, i
         carry += __shfl_sync(0xffffffffu, x, 31);
     }
     __syncwarp();
-    const int ndist = carry, ntile = (ndist + TBN - 1) / TBN;
+    const int ndist = carry, ntile = (ndist + G::TBN - 1) / G::TBN;
     if (!fill) {
         if (lane == 0) T.tile_cnt[t - T.u0] = ntile;
         return;
     }
     for (int q = lane; q < ntile; q += 32) {
-        int *d = T.tiles + (size_t)(base + q) * kTileInts;
+        int *d = T.tiles + (size_t)(base + q) * G::kTileInts;
         d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
-        for (int k = 4; k < kTileInts; ++k) d[k] = -1;
+        for (int k = 4; k < G::kTileInts; ++k) d[k] = -1;
     }
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < TBM; ++m)
+    for (int m = 0; m < G::TBM; ++m)
         for (int e = cur[m] + lane; e < end[m]; e += 32) {
             const int jc = T.mcol[e];
             const int j = jc - lo;
             const int r = wr[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
-            int *d = T.tiles + (size_t)(base + r / TBN) * kTileInts;
-            d[4 + m * TBN + r % TBN] = e;
-            d[kColOff + r % TBN] = jc;
+            int *d = T.tiles + (size_t)(base + r / G::TBN) * G::kTileInts;
+            d[4 + m * G::TBN + r % G::TBN] = e;
+            d[G::kColOff + r % G::TBN] = jc;
         }
 }
 
-// the serial 4-way merge (same tile order as the bitmap path)
+// the serial TBM-way merge (same tile order as the bitmap path)
+template <int B>
 __device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const int *cur0, const int *end0,
                                  int fill) {
-    int cur[TBM], end[TBM];
-    for (int m = 0; m < TBM; ++m) { cur[m] = cur0[m]; end[m] = end0[m]; }
-    // the distinct columns needed by the 4 rows, in increasing order, are packed
-    // 4 at a time into tiles: every tile column is needed by at least one row
+    using G = Geo<B>;
+    int cur[G::TBM], end[G::TBM];
+    for (int m = 0; m < G::TBM; ++m) { cur[m] = cur0[m]; end[m] = end0[m]; }
+    // the distinct columns needed by the TBM rows, in increasing order, are
+    // packed TBN at a time into tiles: every tile column is needed by at least
+    // one row
     int ncol = 0, n = 0;
     const int base = fill ? T.tile_off[t - T.u0] : 0;
     int *d = nullptr;
     // list heads kept in registers: one load per advance
-    int head[TBM];
+    int head[G::TBM];
 #pragma unroll
-    for (int m = 0; m < TBM; ++m) head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
+    for (int m = 0; m < G::TBM; ++m) head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
     while (true) {
         int jmin = 0x7fffffff;
 #pragma unroll
-        for (int m = 0; m < TBM; ++m) jmin = min(jmin, head[m]);
+        for (int m = 0; m < G::TBM; ++m) jmin = min(jmin, head[m]);
         if (jmin == 0x7fffffff) break;
-        const int c = ncol % TBN;
+        const int c = ncol % G::TBN;
         if (c == 0) {
             if (fill) {
-                d = T.tiles + (size_t)(base + n) * kTileInts;
+                d = T.tiles + (size_t)(base + n) * G::kTileInts;
                 d[0] = p; d[1] = I; d[2] = -1; d[3] = 0;
-                for (int q = 4; q < kTileInts; ++q) d[q] = -1;
+                for (int q = 4; q < G::kTileInts; ++q) d[q] = -1;
             }
             ++n;
         }
-        if (fill) d[kColOff + c] = jmin;
+        if (fill) d[G::kColOff + c] = jmin;
 #pragma unroll
-        for (int m = 0; m < TBM; ++m)
+        for (int m = 0; m < G::TBM; ++m)
             if (head[m] == jmin) {
-                if (fill) d[4 + m * TBN + c] = cur[m];
+                if (fill) d[4 + m * G::TBN + c] = cur[m];
                 ++cur[m];
                 head[m] = cur[m] < end[m] ? T.mcol[cur[m]] : 0x7fffffff;
             }
@@ -431,68 +472,72 @@ __device__ void tile_rows_serial(const TileBuild &T, int t, int p, int I, const 
 
 // one thread per tile: K-steps = union over the tile's A rows intersected with
 // the union over its B rows, for each term (count or fill)
+template <int B>
 __device__ void tile_steps_serial(const TileBuild &T, int t, int fill) {
-    const int *d = T.tiles + (size_t)t * kTileInts;
+    using G = Geo<B>;
+    const int *d = T.tiles + (size_t)t * G::kTileInts;
     const int p = d[0], I = d[1];
     const Job &job = T.jt.job[p];
     int64_t w = fill ? T.step_off[t] : 0;
     int n = 0;
     for (int term = 0; term < job.nterm; ++term) {
         const int am = job.a[term], bm = job.b[term];
-        int cur[kSlots], end[kSlots];
-        for (int q = 0; q < TBM; ++q) {
-            const int i = TBM * I + q;
+        int cur[G::kSlots], end[G::kSlots];
+        for (int q = 0; q < G::TBM; ++q) {
+            const int i = G::TBM * I + q;
             cur[q] = end[q] = 0;
             if (i < T.NB) { cur[q] = T.rp[am * T.NB + i]; end[q] = T.rp[am * T.NB + i + 1]; }
         }
-        for (int q = 0; q < TBN; ++q) {
-            const int j = d[kColOff + q];
-            cur[TBM + q] = end[TBM + q] = 0;
-            if (j >= 0) { cur[TBM + q] = T.rp[bm * T.NB + j]; end[TBM + q] = T.rp[bm * T.NB + j + 1]; }
+        for (int q = 0; q < G::TBN; ++q) {
+            const int j = d[G::kColOff + q];
+            cur[G::TBM + q] = end[G::TBM + q] = 0;
+            if (j >= 0) { cur[G::TBM + q] = T.rp[bm * T.NB + j]; end[G::TBM + q] = T.rp[bm * T.NB + j + 1]; }
         }
         // list heads kept in registers: one load per advance
-        int head[kSlots];
+        int head[G::kSlots];
 #pragma unroll
-        for (int q = 0; q < kSlots; ++q) head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
+        for (int q = 0; q < G::kSlots; ++q) head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
         while (true) {
             int kmin = 0x7fffffff;
 #pragma unroll
-            for (int q = 0; q < kSlots; ++q) kmin = min(kmin, head[q]);
+            for (int q = 0; q < G::kSlots; ++q) kmin = min(kmin, head[q]);
             if (kmin == 0x7fffffff) break;
             bool anyA = false, anyB = false;
-            int idx[kSlots];
+            int idx[G::kSlots];
 #pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
+            for (int q = 0; q < G::kSlots; ++q) {
                 idx[q] = -1;
                 if (head[q] == kmin) {
                     idx[q] = cur[q];
                     ++cur[q];
                     head[q] = cur[q] < end[q] ? T.col[cur[q]] : 0x7fffffff;
-                    if (q < TBM) anyA = true; else anyB = true;
+                    if (q < G::TBM) anyA = true; else anyB = true;
                 }
             }
             if (anyA && anyB) {
                 if (fill && w + n < T.step_off[t + 1]) {
-                    int *s = T.steps + (size_t)(w + n) * kSlots;
-                    for (int q = 0; q < kSlots; ++q) s[q] = idx[q];
+                    int *s = T.steps + (size_t)(w + n) * G::kSlots;
+                    for (int q = 0; q < G::kSlots; ++q) s[q] = idx[q];
                 }
                 ++n;
             }
         }
     }
     if (!fill) T.step_cnt[t] = n;
-    else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
+    else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * G::kTileInts + 3] = -1;
 }
 
 // K-steps of one tile, warp-parallel: per term, the columns k of the tile's
-// TBM A rows and of its TBN B rows are marked in two shared-memory bitmaps over
-// the window where both can have columns; a K-step is a k marked in both, its
-// index the rank of k among those (prefix popcounts).  Each list entry at
-// such a k writes its block index into its slot of the step; the other
-// slots stay -1 (zero block).  Same steps, same order as the serial merge,
-// which lane 0 runs for windows wider than the bitmaps.
+// TBM A rows and of its TBN B rows are marked in two shared-memory bitmaps
+// over the window where both can have columns; a K-step is a k marked in
+// both, its index the rank of k among those (prefix popcounts).  Each list
+// entry at such a k writes its block index into its slot of the step; the
+// other slots stay -1 (zero block).  Same steps, same order as the serial
+// merge, which lane 0 runs for windows wider than the bitmaps.
 constexpr int kStepWarps = 4, kStepWords = 512;    // 16,384 columns per window
+template <int B>
 __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int fill) {
+    using G = Geo<B>;
     __shared__ unsigned ba_s[kStepWarps][kStepWords], bb_s[kStepWarps][kStepWords];
     __shared__ int rank_s[kStepWarps][kStepWords];
     const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -500,17 +545,17 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
     if (t >= T.ntile) return;
     unsigned *ba = ba_s[wq], *bb = bb_s[wq];
     int *wr = rank_s[wq];
-    const int *d = T.tiles + (size_t)t * kTileInts;
+    const int *d = T.tiles + (size_t)t * G::kTileInts;
     const int p = d[0], I = d[1];
     const Job &job = T.jt.job[p];
     // the window of every term must fit the bitmaps, else the serial merge
-    int lo_t[2], hi_t[2], cur[2][kSlots], end[2][kSlots];
+    int lo_t[2], hi_t[2], cur[2][G::kSlots], end[2][G::kSlots];
     bool fits = true;
     for (int term = 0; term < job.nterm; ++term) {
         const int am = job.a[term], bm = job.b[term];
         int loA = 0x7fffffff, hiA = -1, loB = 0x7fffffff, hiB = -1;
-        for (int q = 0; q < TBM; ++q) {
-            const int i = TBM * I + q;
+        for (int q = 0; q < G::TBM; ++q) {
+            const int i = G::TBM * I + q;
             cur[term][q] = end[term][q] = 0;
             if (i < T.NB) { cur[term][q] = T.rp[am * T.NB + i]; end[term][q] = T.rp[am * T.NB + i + 1]; }
             if (cur[term][q] < end[term][q]) {
@@ -518,13 +563,16 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
                 hiA = max(hiA, T.col[end[term][q] - 1]);
             }
         }
-        for (int q = 0; q < TBN; ++q) {
-            const int j = d[kColOff + q];
-            cur[term][TBM + q] = end[term][TBM + q] = 0;
-            if (j >= 0) { cur[term][TBM + q] = T.rp[bm * T.NB + j]; end[term][TBM + q] = T.rp[bm * T.NB + j + 1]; }
-            if (cur[term][TBM + q] < end[term][TBM + q]) {
-                loB = min(loB, T.col[cur[term][TBM + q]]);
-                hiB = max(hiB, T.col[end[term][TBM + q] - 1]);
+        for (int q = 0; q < G::TBN; ++q) {
+            const int j = d[G::kColOff + q];
+            cur[term][G::TBM + q] = end[term][G::TBM + q] = 0;
+            if (j >= 0) {
+                cur[term][G::TBM + q] = T.rp[bm * T.NB + j];
+                end[term][G::TBM + q] = T.rp[bm * T.NB + j + 1];
+            }
+            if (cur[term][G::TBM + q] < end[term][G::TBM + q]) {
+                loB = min(loB, T.col[cur[term][G::TBM + q]]);
+                hiB = max(hiB, T.col[end[term][G::TBM + q] - 1]);
             }
         }
         lo_t[term] = max(loA, loB);
@@ -532,7 +580,7 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         if (hi_t[term] >= lo_t[term] && ((hi_t[term] - lo_t[term]) >> 5) + 1 > T.max_words) fits = false;
     }
     if (!fits) {
-        if (lane == 0) tile_steps_serial(T, t, fill);
+        if (lane == 0) tile_steps_serial<B>(T, t, fill);
         return;
     }
     int64_t w = fill ? T.step_off[t] : 0;
@@ -543,8 +591,8 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         const int nw = ((hi - lo) >> 5) + 1;
         for (int x = lane; x < nw; x += 32) { ba[x] = 0u; bb[x] = 0u; }
         __syncwarp();
-        for (int q = 0; q < kSlots; ++q) {
-            unsigned *bmap = q < TBM ? ba : bb;
+        for (int q = 0; q < G::kSlots; ++q) {
+            unsigned *bmap = q < G::TBM ? ba : bb;
             for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
                 const int k = T.col[e];
                 if (k < lo || k > hi) continue;
@@ -574,11 +622,11 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
         if (fill) {
             const int64_t wend = T.step_off[t + 1];
             for (int64_t q = w + n + lane; q < min(w + n + carry, wend); q += 32) {
-                int *st = T.steps + (size_t)q * kSlots;
-                for (int k = 0; k < kSlots; ++k) st[k] = -1;
+                int *st = T.steps + (size_t)q * G::kSlots;
+                for (int k = 0; k < G::kSlots; ++k) st[k] = -1;
             }
             __syncwarp();
-            for (int q = 0; q < kSlots; ++q)
+            for (int q = 0; q < G::kSlots; ++q)
                 for (int e = cur[term][q] + lane; e < end[term][q]; e += 32) {
                     const int k = T.col[e];
                     if (k < lo || k > hi) continue;
@@ -586,7 +634,7 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
                     const unsigned word = ba[kk >> 5];
                     if (!((word >> (kk & 31)) & 1u)) continue;
                     const int r = wr[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
-                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * kSlots + q] = e;
+                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * G::kSlots + q] = e;
                 }
             __syncwarp();
         }
@@ -594,21 +642,22 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
     }
     if (lane == 0) {
         if (!fill) T.step_cnt[t] = n;
-        else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * kTileInts + 3] = -1;
+        else if (n != (int)(T.step_off[t + 1] - T.step_off[t])) T.tiles[(size_t)t * G::kTileInts + 3] = -1;
     }
 }
 
+template <int B>
 __global__ void k_set_nsteps(int *tiles, const int *step_cnt, int ntile) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < ntile) tiles[(size_t)t * kTileInts + 3] = step_cnt[t];
+    if (t < ntile) tiles[(size_t)t * Geo<B>::kTileInts + 3] = step_cnt[t];
 }
 
 // ---------------------------------------------------------------------------
 // the tensor-core product kernel
 // ---------------------------------------------------------------------------
 struct TcArgs {
-    const uint16_t *planes;       // operand planes of the input set (hi and lo interleaved, 4 KB per block)
-    const uint16_t *zero;         // zero blocks (8 per CTA)
+    const uint16_t *planes;       // operand planes of the input set (hi and lo interleaved per block)
+    const uint16_t *zero;         // zero blocks (kSlots per CTA)
     const int *tiles;
     const int64_t *step_off;
     const int *steps;
@@ -629,30 +678,91 @@ struct TcArgs {
     int64_t u0;
     int *err;
     long long wait_cycles;        // bound of every mbarrier wait
-    int hold;                     // test setting: the producer waits for g_never_set first
+    int hold;                     // test setting: the MMA thread waits for g_never_set first
 };
 
 struct __align__(8) SmemCtl {
-    uint64_t full[kStages], empty[kStages];
+    uint64_t full[8], empty[8];
     uint64_t seg_full[kSegBufs], seg_empty[kSegBufs];
     uint64_t drain;
+    uint64_t pair[4];             // b = 64: handshake of the two epilogue warps of a column range
+    float pair_ss[kEpiWarps];     // b = 64: partial squared norms exchanged within a pair
     uint32_t tmem_base;
     int abort_flag;
 };
 
+// Epilogue metadata of one output block, gathered by one lane while the
+// tile's MMAs run and parked in shared memory (8 words per block: slot, old
+// slot, diagonal, output index, c_lin, c_sq, tau lo, tau hi); the old X
+// block of the linear term is prefetched into L2.
+template <int B>
+__device__ __forceinline__ void gather_meta(const TcArgs &A, int s, float *q) {
+    constexpr int W = meta_stride<B>();
+    int m_sx = -1, m_diag = 0, m_keepidx = 0;
+    float m_cl = 0.f, m_cq = 0.f;
+    double m_tau = 0.0;
+    if (s >= 0) {
+        const int i = A.slot_row[s];
+        const int sys = A.sys_of_row[i];
+        const int job = A.slot_job[s];
+        m_cl = (float)A.c_lin[sys];
+        // undo the operand scaling: every term of a job has the same scale product
+        m_cq = (float)A.c_sq[sys] / (A.scale[A.job_a[job]] * A.scale[A.job_b[job]]);
+        m_tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
+        m_sx = A.slot_x[s];
+        m_diag = A.slot_t[s] == s;
+        m_keepidx = A.uidx[s] - (int)A.u0;
+        if (m_sx >= 0 && m_cl != 0.f) {
+            const double *px = A.in_val + (size_t)m_sx * (B * B);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8 * B * B) : "memory");
+        }
+    }
+    q[0] = __int_as_float(s);
+    q[W] = __int_as_float(m_sx);
+    q[2 * W] = __int_as_float(m_diag);
+    q[3 * W] = __int_as_float(m_keepidx);
+    q[4 * W] = m_cl;
+    q[5 * W] = m_cq;
+    q[6 * W] = __int_as_float(__double2loint(m_tau));
+    q[7 * W] = __int_as_float(__double2hiint(m_tau));
+}
+
+// b = 64: one step of the handshake of the two epilogue warps that share a
+// block column range (their lane quarters hold the two row halves of the same
+// blocks): both arrive on the pair's mbarrier (count 2) and wait, bounded like
+// every wait of the kernel, for the phase to complete.
+__device__ __forceinline__ bool pair_sync(SmemCtl *ctl, int pair, uint32_t &round, int lane,
+                                          volatile int *abort_flag, long long limit) {
+    __threadfence_block();     // this lane's shared-memory writes before the arrival
+    __syncwarp();
+    int ok = 1;
+    if (lane == 0) {
+        mbar_arrive(&ctl->pair[pair]);
+        ok = mbar_wait(&ctl->pair[pair], round & 1, abort_flag, limit) ? 1 : 0;
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __threadfence_block();     // the partner's writes before this lane's reads
+    ++round;
+    return ok != 0;
+}
+
+template <int B>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
+    using G = Geo<B>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *stages = smem_raw;                                       // kStages * 32 KB
-    float *stage_ep = reinterpret_cast<float *>(smem_raw + kStages * kStageBytes);   // kEpiWarps x 32 x 33
-    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(stage_ep + kEpiWarps * 32 * 33);
+    uint8_t *stages = smem_raw;                                                    // kStages stages
+    float *stage_ep = reinterpret_cast<float *>(smem_raw + G::kStages * G::kStageBytes);   // kEpiWarps x 32 x 33
+    float *meta_all = stage_ep + kEpiWarps * 32 * 33;                              // kEpiWarps x meta_words
+    SmemCtl *ctl = reinterpret_cast<SmemCtl *>(meta_all + kEpiWarps * meta_words<B>());
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
+        for (int s = 0; s < G::kStages; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
         for (int b = 0; b < kSegBufs; ++b) { mbar_init(&ctl->seg_full[b], 1); mbar_init(&ctl->seg_empty[b], kEpiWarps); }
         mbar_init(&ctl->drain, 1);
+        for (int q = 0; q < 4; ++q) mbar_init(&ctl->pair[q], 2);
         ctl->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -672,63 +782,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     if (warp == 0) {
         // ---------------- producer: bulk copies of the operand blocks ----------------
         // Lane m < kSlots owns slot m of every stage (slot m < TBM: A block row
-        // m, else B block row m - TBM; slot m at m * 4 KB): it loads the block
-        // index of the next K-step while the current step's copies, one 4 KB
+        // m, else B block row m - TBM; slot m at m * kPairBytes): it loads the
+        // block index of the next K-step while the current step's copies, one
         // copy per slot (hi and lo planes), are issued by all lanes at once.
         // A slot whose block is missing needs zeros; a stage slot that already
         // holds zeros from its previous use is not copied again (zmask).
         uint32_t it = 0;
         bool ok = true;
-        if (A.hold) {
-            // test setting: wait (bounded) for a flag that nothing sets; the
-            // wait runs out, raises the abort flag and nothing is issued
-            int held = 1;
-            if (lane == 0) {
-                const long long t0 = clock64();
-                while (*(volatile int *)&g_never_set == 0) {
-                    if (clock64() - t0 > A.wait_cycles) {
-                        *abort_flag = 1;
-                        held = 0;
-                        break;
-                    }
-                }
-            }
-            ok = __shfl_sync(0xffffffffu, held, 0) != 0;
-        }
-        uint32_t zmask[kStages];
+        uint32_t zmask[G::kStages];
 #pragma unroll
-        for (int k = 0; k < kStages; ++k) zmask[k] = 0u;
+        for (int k = 0; k < G::kStages; ++k) zmask[k] = 0u;
         for (int t = blockIdx.x; t < A.ntile && ok; t += gridDim.x) {
             const int64_t s0 = A.step_off[t], s1 = A.step_off[t + 1];
-            int nxt = (s0 < s1 && lane < kSlots) ? A.steps[s0 * kSlots + lane] : -1;
+            int nxt = (s0 < s1 && lane < G::kSlots) ? A.steps[s0 * G::kSlots + lane] : -1;
             for (int64_t q = s0; q < s1; ++q, ++it) {
                 const int cur = nxt;
-                if (q + 1 < s1 && lane < kSlots) nxt = A.steps[(q + 1) * kSlots + lane];
-                const int st = it % kStages;
-                const uint32_t ph = (it / kStages) & 1;
-                const uint32_t zbits = __ballot_sync(0xffffffffu, lane < kSlots && cur < 0);
+                if (q + 1 < s1 && lane < G::kSlots) nxt = A.steps[(q + 1) * G::kSlots + lane];
+                const int st = it % G::kStages;
+                const uint32_t ph = (it / G::kStages) & 1;
+                const uint32_t zbits = __ballot_sync(0xffffffffu, lane < G::kSlots && cur < 0);
                 uint32_t zprev = 0u;
 #pragma unroll
-                for (int k = 0; k < kStages; ++k)
+                for (int k = 0; k < G::kStages; ++k)
                     if (k == st) zprev = zmask[k];
-                const bool skip = lane >= kSlots || (cur < 0 && ((zprev >> lane) & 1u));
+                const bool skip = lane >= G::kSlots || (cur < 0 && ((zprev >> lane) & 1u));
                 const uint32_t need = __ballot_sync(0xffffffffu, !skip);
                 int waited = 1;
                 if (lane == 0) {
                     waited = mbar_wait(&ctl->empty[st], ph ^ 1, abort_flag, A.wait_cycles) ? 1 : 0;
-                    if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * kPairBytes);
+                    if (waited) mbar_expect_tx(&ctl->full[st], (uint32_t)__popc(need) * G::kPairBytes);
                 }
                 waited = __shfl_sync(0xffffffffu, waited, 0);
                 if (!waited) { ok = false; break; }
 #pragma unroll
-                for (int k = 0; k < kStages; ++k)
+                for (int k = 0; k < G::kStages; ++k)
                     if (k == st) zmask[k] = zbits;
                 if (!skip) {
                     // zero blocks: one per CTA and slot, so that the CTAs do not all
                     // read the same few L2 sectors
-                    const uint16_t *src = cur >= 0 ? A.planes + (size_t)cur * (2 * kPlaneElems)
-                                                   : A.zero + ((size_t)blockIdx.x * kSlots + lane) * (2 * kPlaneElems);
-                    bulk_g2s(stages + st * kStageBytes + lane * kPairBytes, src, kPairBytes, &ctl->full[st]);
+                    const uint16_t *src = cur >= 0 ? A.planes + (size_t)cur * (2 * G::kPlaneElems)
+                                                   : A.zero + ((size_t)blockIdx.x * G::kSlots + lane) * (2 * G::kPlaneElems);
+                    bulk_g2s(stages + st * G::kStageBytes + lane * G::kPairBytes, src, G::kPairBytes, &ctl->full[st]);
                 }
             }
         }
@@ -736,14 +830,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             // after an abort, wait (bounded) until the copies of the stages
             // still in flight have landed before the CTA leaves: the last
             // min(it, kStages) issued stages, each at the phase of its last use
-            const uint32_t n = it < (uint32_t)kStages ? it : (uint32_t)kStages;
+            const uint32_t n = it < (uint32_t)G::kStages ? it : (uint32_t)G::kStages;
             for (uint32_t q = it - n; q < it; ++q)
-                mbar_wait_drain(&ctl->full[q % kStages], (q / kStages) & 1, A.wait_cycles);
+                mbar_wait_drain(&ctl->full[q % G::kStages], (q / G::kStages) & 1, A.wait_cycles);
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
+            if (A.hold) hold_until_timeout(abort_flag, A.wait_cycles);
             uint32_t it = 0, seg = 0;
             bool issued = false;
             for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
@@ -756,23 +851,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                     if (!mbar_wait(&ctl->seg_empty[buf], (use & 1) ^ 1, abort_flag, A.wait_cycles)) { ok = false; break; }
                     fence_after();
                     const uint32_t d_tmem = tmem + buf * kTileN;
-                    const int64_t qe = q + kSegSteps < s1 ? q + kSegSteps : s1;
+                    const int64_t qe = q + G::kSegSteps < s1 ? q + G::kSegSteps : s1;
                     const int64_t qs = q;
                     for (; q < qe; ++q, ++it) {
-                        const int st = it % kStages;
-                        const uint32_t ph = (it / kStages) & 1;
+                        const int st = it % G::kStages;
+                        const uint32_t ph = (it / G::kStages) & 1;
                         if (!mbar_wait(&ctl->full[st], ph, abort_flag, A.wait_cycles)) { ok = false; break; }
                         fence_after();
-                        const uint32_t base = smem_u32(stages + st * kStageBytes);
-                        const uint32_t a_hi = base, a_lo = base + 512;
-                        const uint32_t b_hi = base + kSideABytes, b_lo = base + kSideABytes + 512;
+                        const uint32_t base = smem_u32(stages + st * G::kStageBytes);
+                        const uint32_t a_hi = base, a_lo = base + G::kLoOff;
+                        const uint32_t b_hi = base + G::kSideABytes, b_lo = base + G::kSideABytes + G::kLoOff;
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
+                        for (int kk = 0; kk < G::kSub; ++kk) {
                             const uint32_t ko = kk * 256;
                             const uint32_t first = (q == qs && kk == 0) ? 0u : 1u;
-                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 1024), smem_desc(b_hi + ko, 128, 1024), A.idesc, first);
-                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, 1024), smem_desc(b_lo + ko, 128, 1024), A.idesc, 1u);
-                            mma_f16(d_tmem, smem_desc(a_lo + ko, 128, 1024), smem_desc(b_hi + ko, 128, 1024), A.idesc, 1u);
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, G::kSBO), smem_desc(b_hi + ko, 128, G::kSBO), A.idesc, first);
+                            mma_f16(d_tmem, smem_desc(a_hi + ko, 128, G::kSBO), smem_desc(b_lo + ko, 128, G::kSBO), A.idesc, 1u);
+                            mma_f16(d_tmem, smem_desc(a_lo + ko, 128, G::kSBO), smem_desc(b_hi + ko, 128, G::kSBO), A.idesc, 1u);
                         }
                         issued = true;
                         mma_commit(&ctl->empty[st]);
@@ -790,71 +885,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..9, TMEM lane quarter = block row ----------------
-        const int eq = warp & 3;                       // lanes 32*eq .. 32*eq+31
-        const int n0 = ((warp - 2) >> 2) * kColBlocks;  // this warp's column blocks n0 .. n0 + kColBlocks - 1
-        float *S = stage_ep + (warp - 2) * 32 * 33;     // one block, transposed through shared memory
-        uint32_t seg = 0;
+        // ---------------- epilogue: warps 2..9 ----------------
+        const int eq = warp & 3;                        // TMEM lanes 32*eq .. 32*eq+31
+        const int colhalf = (warp - 2) >> 2;            // accumulator columns 128*colhalf .. +127
+        float *S = stage_ep + (warp - 2) * 32 * 33;     // one 32 x 32 tile, transposed through shared memory
+        // metadata of block n, word w at meta[(8 n + w) * MW]
+        constexpr int MW = meta_stride<B>();
+        float *meta = B == 16 ? meta_all + (warp - 2) * meta_words<B>() : S + 32;
+        uint32_t seg = 0, pround = 0;
         for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
-            // metadata of this warp's output blocks, one lane each, gathered
-            // while the tile's MMAs run and parked in the padding column of S
-            // (8 words per block: slot, old slot, diagonal, output index,
-            // c_lin, c_sq, tau lo, tau hi) to keep registers for the
-            // accumulators; the old X blocks of the linear term are
-            // prefetched into L2
-            const int *d = A.tiles + (size_t)t * kTileInts;
-            float *meta = S + 32;                      // S[r * 33 + 32], r = 0..31
-            if (lane < kColBlocks) {
-                int m_s = -1, m_sx = -1, m_diag = 0, m_keepidx = 0;
-                float m_cl = 0.f, m_cq = 0.f;
-                double m_tau = 0.0;
-                m_s = d[4 + eq * TBN + n0 + lane];
-                if (m_s >= 0) {
-                    const int i = A.slot_row[m_s];
-                    const int sys = A.sys_of_row[i];
-                    const int job = A.slot_job[m_s];
-                    m_cl = (float)A.c_lin[sys];
-                    // undo the operand scaling: every term of a job has the same scale product
-                    m_cq = (float)A.c_sq[sys] / (A.scale[A.job_a[job]] * A.scale[A.job_b[job]]);
-                    m_tau = A.job_tau_sel[job] ? A.tau1[sys] : A.tau0[sys];
-                    m_sx = A.slot_x[m_s];
-                    m_diag = A.slot_t[m_s] == m_s;
-                    m_keepidx = A.uidx[m_s] - (int)A.u0;
-                    if (m_sx >= 0 && m_cl != 0.f) {
-                        const double *px = A.in_val + (size_t)m_sx * kPlaneElems;
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8192) : "memory");
-                    }
-                }
-                float *q = meta + lane * 8 * 33;
-                q[0] = __int_as_float(m_s);
-                q[33] = __int_as_float(m_sx);
-                q[2 * 33] = __int_as_float(m_diag);
-                q[3 * 33] = __int_as_float(m_keepidx);
-                q[4 * 33] = m_cl;
-                q[5 * 33] = m_cq;
-                q[6 * 33] = __int_as_float(__double2loint(m_tau));
-                q[7 * 33] = __int_as_float(__double2hiint(m_tau));
+            const int *d = A.tiles + (size_t)t * G::kTileInts;
+            // metadata of this warp's output blocks, one lane each
+            if constexpr (B == 32) {
+                // block row eq of the tile, block columns 4 colhalf .. 4 colhalf + 3
+                if (lane < 4) gather_meta<B>(A, d[4 + eq * G::TBN + 4 * colhalf + lane], meta + lane * 8 * MW);
+            } else if constexpr (B == 16) {
+                // block rows 2 eq (lanes 0-7) and 2 eq + 1 (lanes 8-15), block columns 8 colhalf .. + 7
+                if (lane < 16)
+                    gather_meta<B>(A, d[4 + (2 * eq + (lane >> 3)) * G::TBN + 8 * colhalf + (lane & 7)], meta + lane * 8 * MW);
+            } else {
+                // block row eq / 2 (row half eq & 1), block columns 2 colhalf, 2 colhalf + 1
+                if (lane < 2) gather_meta<B>(A, d[4 + (eq >> 1) * G::TBN + 2 * colhalf + lane], meta + lane * 8 * MW);
             }
             __syncwarp();
             const int nst = d[3];
             if (nst < 0 && lane == 0) atomicOr(A.err, 4);
             // the tile's accumulator: sum of its segments, added with
-            // round-to-nearest in registers (row 32*eq + lane, this warp's 32 * kColBlocks columns)
-            float racc[32 * kColBlocks];
+            // round-to-nearest in registers (row 32*eq + lane, this warp's 128 columns)
+            float racc[128];
 #pragma unroll
-            for (int c = 0; c < 32 * kColBlocks; ++c) racc[c] = 0.f;
-            const int nseg = nst > 0 ? (nst + kSegSteps - 1) / kSegSteps : 0;
+            for (int c = 0; c < 128; ++c) racc[c] = 0.f;
+            const int nseg = nst > 0 ? (nst + G::kSegSteps - 1) / G::kSegSteps : 0;
             bool ok = true;
             for (int g = 0; g < nseg; ++g, ++seg) {
                 const int buf = seg & (kSegBufs - 1);
                 const uint32_t use = seg / kSegBufs;
                 if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag, A.wait_cycles)) { ok = false; break; }
                 fence_after();
-                const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * kTileN;
+                const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * kTileN + 128 * colhalf;
 #pragma unroll
-                for (int h = 0; h < 2 * kColBlocks; ++h) {
+                for (int h = 0; h < 8; ++h) {
                     float part[16];
-                    tmem_ld16(ta + n0 * 32 + h * 16, part);
+                    tmem_ld16(ta + h * 16, part);
 #pragma unroll
                     for (int c = 0; c < 16; ++c) racc[h * 16 + c] += part[c];
                 }
@@ -863,62 +935,226 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
                 if (lane == 0) mbar_arrive(&ctl->seg_empty[buf]);
             }
             if (!ok) break;
+
+            if constexpr (B == 32) {
+                // lane l holds row l of 4 blocks of 32 columns
 #pragma unroll
-            for (int n = 0; n < kColBlocks; ++n) {
-                const float *q = meta + n * 8 * 33;
-                const int s = __float_as_int(q[0]);
-                if (s < 0) continue;
-                float acc[32];
+                for (int n = 0; n < 4; ++n) {
+                    const float *q = meta + n * 8 * MW;
+                    const int s = __float_as_int(q[0]);
+                    if (s < 0) continue;
+                    float acc[32];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] = racc[n * 32 + c];
-                const float cl = q[4 * 33];
-                const float cq = q[5 * 33];
-                const double tau = __hiloint2double(__float_as_int(q[7 * 33]), __float_as_int(q[6 * 33]));
-                const int sx = __float_as_int(q[33]);
-                const bool diag = __float_as_int(q[2 * 33]) != 0;
-                const int oidx = __float_as_int(q[3 * 33]);
-                __syncwarp();
-                // linear term: the old block is staged in S (coalesced row reads,
-                // rounded to FP32), then each lane takes its own row
-                if (sx >= 0 && cl != 0.f) {
-                    const double *gx = A.in_val + (size_t)sx * kPlaneElems;
+                    for (int c = 0; c < 32; ++c) acc[c] = racc[n * 32 + c];
+                    const float cl = q[4 * MW];
+                    const float cq = q[5 * MW];
+                    const double tau = __hiloint2double(__float_as_int(q[7 * MW]), __float_as_int(q[6 * MW]));
+                    const int sx = __float_as_int(q[1 * MW]);
+                    const bool diag = __float_as_int(q[2 * MW]) != 0;
+                    const int oidx = __float_as_int(q[3 * MW]);
+                    __syncwarp();
+                    // linear term: the old block is staged in S (coalesced row reads,
+                    // rounded to FP32), then each lane takes its own row
+                    if (sx >= 0 && cl != 0.f) {
+                        const double *gx = A.in_val + (size_t)sx * G::kPlaneElems;
 #pragma unroll 8
-                    for (int r = 0; r < 32; ++r) S[r * 33 + lane] = (float)gx[r * 32 + lane];
-                    __syncwarp();
+                        for (int r = 0; r < 32; ++r) S[r * 33 + lane] = (float)gx[r * 32 + lane];
+                        __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[c] = fmaf(cl, S[lane * 33 + c], cq * acc[c]);
-                    __syncwarp();
-                } else {
+                        for (int c = 0; c < 32; ++c) acc[c] = fmaf(cl, S[lane * 33 + c], cq * acc[c]);
+                        __syncwarp();
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[c] = cq * acc[c];
-                }
-                // lane l holds row l of the block; a diagonal block is
-                // symmetrised as (X + X^T) / 2
-#pragma unroll
-                for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
-                __syncwarp();
-                if (diag) {
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[c] = 0.5f * (S[lane * 33 + c] + S[c * 33 + lane]);
-                    __syncwarp();
+                        for (int c = 0; c < 32; ++c) acc[c] = cq * acc[c];
+                    }
+                    // a diagonal block is symmetrised as (X + X^T) / 2
 #pragma unroll
                     for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
                     __syncwarp();
-                }
-                float ss = 0.f;
+                    if (diag) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) ss = fmaf(acc[c], acc[c], ss);
+                        for (int c = 0; c < 32; ++c) acc[c] = 0.5f * (S[lane * 33 + c] + S[c * 33 + lane]);
+                        __syncwarp();
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-                const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
-                const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
-                double *o = A.out_val + (size_t)oidx * kPlaneElems;
-                for (int r = 0; r < 32; ++r) o[r * 32 + lane] = (double)S[r * 33 + lane];
-                if (lane == 0) {
-                    A.out_nrm[s] = nrm;
-                    A.keep[s] = kp;
+                        for (int c = 0; c < 32; ++c) S[lane * 33 + c] = acc[c];
+                        __syncwarp();
+                    }
+                    float ss = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) ss = fmaf(acc[c], acc[c], ss);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
+                    const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
+                    double *o = A.out_val + (size_t)oidx * G::kPlaneElems;
+                    for (int r = 0; r < 32; ++r) o[r * 32 + lane] = (double)S[r * 33 + lane];
+                    if (lane == 0) {
+                        A.out_nrm[s] = nrm;
+                        A.keep[s] = kp;
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
+            } else if constexpr (B == 16) {
+                // half-warp h = lane / 16 holds rows of block row 2 eq + h: lane l
+                // is row l & 15 of that block row, over 8 blocks of 16 columns
+                const int h = lane >> 4, c16 = lane & 15;
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                    const float *q = meta + (h * 8 + n) * 8 * MW;
+                    const int s = __float_as_int(q[0]);
+                    const float cl = q[4 * MW];
+                    const float cq = q[5 * MW];
+                    const double tau = __hiloint2double(__float_as_int(q[7 * MW]), __float_as_int(q[6 * MW]));
+                    const int sx = __float_as_int(q[1 * MW]);
+                    const bool diag = s >= 0 && __float_as_int(q[2 * MW]) != 0;
+                    const int oidx = __float_as_int(q[3 * MW]);
+                    const bool lin = s >= 0 && sx >= 0 && cl != 0.f;
+                    float acc[16];
+                    __syncwarp();
+                    if (lin) {
+                        const double *gx = A.in_val + (size_t)sx * G::kPlaneElems;
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) S[(16 * h + r) * 33 + c16] = (float)gx[r * 16 + c16];
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        acc[c] = lin ? fmaf(cl, S[lane * 33 + c], cq * racc[n * 16 + c]) : cq * racc[n * 16 + c];
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) S[lane * 33 + c] = acc[c];
+                    __syncwarp();
+                    // a diagonal block is symmetrised as (X + X^T) / 2
+                    if (diag) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[c] = 0.5f * (S[lane * 33 + c] + S[(16 * h + c) * 33 + c16]);
+                    }
+                    __syncwarp();
+                    if (diag) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) S[lane * 33 + c] = acc[c];
+                    }
+                    __syncwarp();
+                    float ss = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) ss = fmaf(acc[c], acc[c], ss);
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    const float nrm = sqrtf(ss) * (1.0f + 1e-6f);
+                    const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
+                    if (s >= 0) {
+                        double *o = A.out_val + (size_t)oidx * G::kPlaneElems;
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) o[r * 16 + c16] = (double)S[(16 * h + r) * 33 + c16];
+                        if (c16 == 0) {
+                            A.out_nrm[s] = nrm;
+                            A.keep[s] = kp;
+                        }
+                    }
+                    __syncwarp();
+                }
+            } else {
+                // b = 64: lane l holds row 32 rh + l of 2 blocks of 64 columns; the
+                // partner warp (warp ^ 1) holds the other 32 rows of the same blocks
+                // (both see the same slots, so both take the same branches and
+                // handshakes; after an abort both skip the rest)
+                const int rh = eq & 1, pr = (warp - 2) >> 1;
+                const float *Sp = stage_ep + ((warp ^ 1) - 2) * 32 * 33;   // the partner's staging tile
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    const float *q = meta + n * 8 * MW;
+                    const int s = __float_as_int(q[0]);
+                    if (s < 0 || !ok) continue;
+                    const float cl = q[4 * MW];
+                    const float cq = q[5 * MW];
+                    const double tau = __hiloint2double(__float_as_int(q[7 * MW]), __float_as_int(q[6 * MW]));
+                    const int sx = __float_as_int(q[1 * MW]);
+                    const bool diag = __float_as_int(q[2 * MW]) != 0;
+                    const int oidx = __float_as_int(q[3 * MW]);
+                    // linear term, one 32-column half of the old rows at a time
+#pragma unroll
+                    for (int ch = 0; ch < 2; ++ch) {
+                        __syncwarp();
+                        if (sx >= 0 && cl != 0.f) {
+                            const double *gx = A.in_val + (size_t)sx * G::kPlaneElems + (size_t)(32 * rh) * 64 + 32 * ch;
+#pragma unroll 8
+                            for (int r = 0; r < 32; ++r) S[r * 33 + lane] = (float)gx[r * 64 + lane];
+                            __syncwarp();
+#pragma unroll
+                            for (int c = 0; c < 32; ++c)
+                                racc[n * 64 + 32 * ch + c] = fmaf(cl, S[lane * 33 + c], cq * racc[n * 64 + 32 * ch + c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) racc[n * 64 + 32 * ch + c] = cq * racc[n * 64 + 32 * ch + c];
+                        }
+                    }
+                    if (diag) {
+                        // (X + X^T) / 2: the off-diagonal quarter (rh, 1 - rh) pairs with
+                        // the partner's quarter (1 - rh, rh), exchanged through S
+                        __syncwarp();
+                        if (rh == 0) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) S[lane * 33 + c] = racc[n * 64 + 32 + c];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) S[lane * 33 + c] = racc[n * 64 + c];
+                        }
+                        ok = pair_sync(ctl, pr, pround, lane, abort_flag, A.wait_cycles);
+                        if (rh == 0) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) racc[n * 64 + 32 + c] = 0.5f * (racc[n * 64 + 32 + c] + Sp[c * 33 + lane]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) racc[n * 64 + c] = 0.5f * (racc[n * 64 + c] + Sp[c * 33 + lane]);
+                        }
+                        ok = pair_sync(ctl, pr, pround, lane, abort_flag, A.wait_cycles) && ok;
+                        // the diagonal quarter (rh, rh) with its own transpose
+                        if (rh == 0) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) S[lane * 33 + c] = racc[n * 64 + c];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) S[lane * 33 + c] = racc[n * 64 + 32 + c];
+                        }
+                        __syncwarp();
+                        if (rh == 0) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) racc[n * 64 + c] = 0.5f * (racc[n * 64 + c] + S[c * 33 + lane]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) racc[n * 64 + 32 + c] = 0.5f * (racc[n * 64 + 32 + c] + S[c * 33 + lane]);
+                        }
+                    }
+                    // Frobenius norm over both row halves
+                    float ss = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 64; ++c) ss = fmaf(racc[n * 64 + c], racc[n * 64 + c], ss);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                    if (lane == 0) ctl->pair_ss[warp - 2] = ss;
+                    ok = pair_sync(ctl, pr, pround, lane, abort_flag, A.wait_cycles) && ok;
+                    const float other = *(volatile float *)&ctl->pair_ss[(warp ^ 1) - 2];
+                    const float tot = rh == 0 ? ss + other : other + ss;
+                    const float nrm = sqrtf(tot) * (1.0f + 1e-6f);
+                    const bool kp = ((double)nrm >= tau) && (nrm > 0.f);
+                    // store this warp's 32 rows, one 32-column half at a time
+                    double *o = A.out_val + (size_t)oidx * G::kPlaneElems + (size_t)(32 * rh) * 64;
+#pragma unroll
+                    for (int ch = 0; ch < 2; ++ch) {
+                        __syncwarp();
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) S[lane * 33 + c] = racc[n * 64 + 32 * ch + c];
+                        __syncwarp();
+                        for (int r = 0; r < 32; ++r) o[r * 64 + 32 * ch + lane] = (double)S[r * 33 + lane];
+                    }
+                    if (lane == 0 && rh == 0) {
+                        A.out_nrm[s] = nrm;
+                        A.keep[s] = kp;
+                    }
+                    // the partner reuses pair_ss and its S only after this point
+                    ok = pair_sync(ctl, pr, pround, lane, abort_flag, A.wait_cycles) && ok;
+                }
+                if (!ok) break;
             }
         }
     }
@@ -933,43 +1169,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     }
 }
 
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + kEpiWarps * 32 * 33 * sizeof(float) + sizeof(SmemCtl) + 1024;
-static_assert(kSmemBytes <= 227 * 1024, "shared memory of the tensor-core kernel exceeds 227 KB");
+template <int B>
+constexpr size_t smem_bytes() {
+    return (size_t)Geo<B>::kStages * Geo<B>::kStageBytes + kEpiWarps * 32 * 33 * sizeof(float) +
+           kEpiWarps * meta_words<B>() * sizeof(float) + sizeof(SmemCtl) + 1024;
+}
+static_assert(smem_bytes<16>() <= 227 * 1024 && smem_bytes<32>() <= 227 * 1024 && smem_bytes<64>() <= 227 * 1024,
+              "shared memory of the tensor-core kernel exceeds 227 KB");
+static_assert(Geo<16>::kStages <= 8 && Geo<32>::kStages <= 8 && Geo<64>::kStages <= 8, "mbarrier arrays");
 
-}  // namespace
-
-void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
-    if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
-    if (ar != AR_BF16X3 && ar != AR_FP16X3) throw Error{-1, "tensor-core arithmetic not available"};
-    const int nmat = in.nmat;
-    std::vector<int> first(nmat + 1, 0);
-    for (int m = 0; m < nmat; ++m) first[m + 1] = first[m] + (int)in.nnzb[m];
-    w.mat_first.ensure(nmat + 1);
-    w.scale.ensure(std::max(nmat, 1));
-    RDM_CUDA_TRY(cudaMemcpyAsync(w.mat_first.p, first.data(), (nmat + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_matrix_scales<<<nmat, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
-    RDM_LAUNCH_CHECK();
-    const int64_t n = in.total * kPlaneElems;
-    in.ophi.ensure(std::max<int64_t>(2 * n, 1));   // hi and lo, interleaved per block
-    if (n == 0) return;
+template <int B>
+void split_planes(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
+    const int64_t n = in.total * (int64_t)(B * B);
     const int64_t grid = (n / 8 + 255) / 256;
     if (ar == AR_BF16X3)
-        k_split_planes<true><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
-                                                             w.mat_first.p, nmat);
+        k_split_planes<true, B><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
+                                                                w.mat_first.p, in.nmat);
     else
-        k_split_planes<false><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
-                                                              w.mat_first.p, nmat);
+        k_split_planes<false, B><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
+                                                                 w.mat_first.p, in.nmat);
     RDM_LAUNCH_CHECK();
 }
 
-double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
-                         int NB, const TcPlan &plan, cudaStream_t st) {
-    if (in.b != TB) throw Error{-1, "the tensor-core path handles 32 x 32 blocks"};
-    if (plan.ntile == 0) return 0.0;
+template <int B>
+double launch_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
+                 const TcPlan &plan, cudaStream_t st) {
+    using G = Geo<B>;
     int dev = 0, nsm = 0;
     RDM_CUDA_TRY(cudaGetDevice(&dev));
     RDM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t zero_elems = (size_t)nsm * kSlots * 2 * kPlaneElems;   // a zero block (hi and lo) per CTA and slot
+    const size_t zero_elems = (size_t)nsm * G::kSlots * 2 * G::kPlaneElems;   // a zero block per CTA and slot
     if (!w.zero.p || w.zero.cap < zero_elems) {
         w.zero.ensure(zero_elems);
         RDM_CUDA_TRY(cudaMemsetAsync(w.zero.p, 0, w.zero.cap * sizeof(uint16_t), st));
@@ -995,29 +1224,31 @@ double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt,
     A.hold = w.knobs.hold;
     static bool attr = false;
     if (!attr) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+        RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_bytes<B>()));
         attr = true;
     }
     const int grid = plan.ntile < nsm ? plan.ntile : nsm;
-    k_tc_bf16x3<<<grid, kThreads, kSmemBytes, st>>>(A);
+    k_tc_bf16x3<B><<<grid, kThreads, smem_bytes<B>(), st>>>(A);
     RDM_LAUNCH_CHECK();
-    (void)NB;
-    return (double)plan.nsteps * 3.0 * 2.0 * 128.0 * kTileN * 32.0;
+    return (double)plan.nsteps * 3.0 * 2.0 * 128.0 * kTileN * B;
 }
 
-TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
-                     const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st) {
+template <int B>
+TcPlan build_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp, const int *mcol,
+                  TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st) {
+    using G = Geo<B>;
     TcPlan plan{};
-    const int NB = in.NB, NB4 = (NB + TBM - 1) / TBM;
-    const int nrow4 = unit1 - unit0;
-    if (nrow4 <= 0) return plan;
+    const int NB = in.NB, NBT = (NB + G::TBM - 1) / G::TBM;
+    const int nrowt = unit1 - unit0;
+    if (nrowt <= 0) return plan;
     w.counters.ensure(8);
     RDM_CUDA_TRY(cudaMemsetAsync(w.counters.p, 0, 8 * sizeof(int), st));
-    w.tile_cnt.ensure(nrow4 + 1);
-    w.tile_off.ensure(nrow4 + 1);
-    w.scan32.ensure(scan_tmp_elems(nrow4 + 1));
+    w.tile_cnt.ensure(nrowt + 1);
+    w.tile_off.ensure(nrowt + 1);
+    w.scan32.ensure(scan_tmp_elems(nrowt + 1));
     TileBuild T{};
-    T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NB4 = NB4; T.jt = jt;
+    T.rp = in.row_ptr.p; T.col = in.col.p; T.NB = NB; T.NBT = NBT; T.jt = jt;
     T.out_rp = out_rp; T.mcol = mcol; T.sys_of_row = sd.sys_of_row.p; T.active = sd.active.p;
     T.job_mask = job_mask;
     T.u0 = unit0; T.u1 = unit1;
@@ -1026,38 +1257,87 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
     static_assert(kTileRowWords == kStepWords, "one window bound for both plan builders");
     T.max_words = w.knobs.window_words > 0 && w.knobs.window_words < kTileRowWords ? w.knobs.window_words
                                                                                     : kTileRowWords;
-    k_tile_rows<<<(nrow4 + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 0);
+    k_tile_rows<B><<<(nrowt + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();
-    scan_exclusive_i32(w.tile_cnt.p, w.tile_off.p, nrow4, w.scan32.p, st);
+    scan_exclusive_i32(w.tile_cnt.p, w.tile_off.p, nrowt, w.scan32.p, st);
     int ntile = 0;
-    RDM_CUDA_TRY(cudaMemcpyAsync(&ntile, w.tile_off.p + nrow4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RDM_CUDA_TRY(cudaMemcpyAsync(&ntile, w.tile_off.p + nrowt, sizeof(int), cudaMemcpyDeviceToHost, st));
     RDM_CUDA_TRY(cudaStreamSynchronize(st));
     plan.ntile = ntile;
     if (ntile == 0) return plan;
-    w.tiles.ensure((size_t)ntile * kTileInts);
+    w.tiles.ensure((size_t)ntile * G::kTileInts);
     T.tiles = w.tiles.p;
-    k_tile_rows<<<(nrow4 + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 1);
+    k_tile_rows<B><<<(nrowt + kTileRowWarps - 1) / kTileRowWarps, 32 * kTileRowWarps, 0, st>>>(T, 1);
     RDM_LAUNCH_CHECK();
     w.step_cnt.ensure(ntile + 1);
     w.step_off.ensure(ntile + 1);
     w.scan64.ensure(scan_tmp_elems(ntile + 1));
     T.ntile = ntile;
     T.step_cnt = w.step_cnt.p;
-    k_tile_steps<<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 0);
+    k_tile_steps<B><<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 0);
     RDM_LAUNCH_CHECK();
     scan_exclusive_i64(w.step_cnt.p, w.step_off.p, ntile, w.scan64.p, st);
     int64_t nsteps = 0;
     RDM_CUDA_TRY(cudaMemcpyAsync(&nsteps, w.step_off.p + ntile, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     RDM_CUDA_TRY(cudaStreamSynchronize(st));
     plan.nsteps = nsteps;
-    w.steps.ensure(std::max<int64_t>(nsteps, 1) * kSlots);
+    w.steps.ensure(std::max<int64_t>(nsteps, 1) * G::kSlots);
     T.step_off = w.step_off.p;
     T.steps = w.steps.p;
-    k_set_nsteps<<<(ntile + 127) / 128, 128, 0, st>>>(w.tiles.p, w.step_cnt.p, ntile);
+    k_set_nsteps<B><<<(ntile + 127) / 128, 128, 0, st>>>(w.tiles.p, w.step_cnt.p, ntile);
     RDM_LAUNCH_CHECK();
-    k_tile_steps<<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 1);
+    k_tile_steps<B><<<(ntile + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, 0, st>>>(T, 1);
     RDM_LAUNCH_CHECK();
     return plan;
+}
+
+}  // namespace
+
+bool tc_block_size_ok(int b) { return b == 16 || b == 32 || b == 64; }
+
+int tc_tile_rows(int b) { return tc_block_size_ok(b) ? 128 / b : 4; }
+
+void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
+    if (!tc_block_size_ok(in.b)) throw Error{-1, "the tensor-core path handles 16 x 16, 32 x 32 and 64 x 64 blocks"};
+    if (ar != AR_BF16X3 && ar != AR_FP16X3) throw Error{-1, "tensor-core arithmetic not available"};
+    const int nmat = in.nmat;
+    std::vector<int> first(nmat + 1, 0);
+    for (int m = 0; m < nmat; ++m) first[m + 1] = first[m] + (int)in.nnzb[m];
+    w.mat_first.ensure(nmat + 1);
+    w.scale.ensure(std::max(nmat, 1));
+    RDM_CUDA_TRY(cudaMemcpyAsync(w.mat_first.p, first.data(), (nmat + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_matrix_scales<<<nmat, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
+    RDM_LAUNCH_CHECK();
+    const int64_t n = in.total * (int64_t)in.b * in.b;
+    in.ophi.ensure(std::max<int64_t>(2 * n, 1));   // hi and lo, interleaved per block
+    if (n == 0) return;
+    switch (in.b) {
+        case 16: split_planes<16>(in, ar, w, st); break;
+        case 32: split_planes<32>(in, ar, w, st); break;
+        default: split_planes<64>(in, ar, w, st); break;
+    }
+}
+
+double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
+                         int NB, const TcPlan &plan, cudaStream_t st) {
+    (void)NB;
+    if (!tc_block_size_ok(in.b)) throw Error{-1, "the tensor-core path handles 16 x 16, 32 x 32 and 64 x 64 blocks"};
+    if (plan.ntile == 0) return 0.0;
+    switch (in.b) {
+        case 16: return launch_tc<16>(a, in, jt, ar, w, plan, st);
+        case 32: return launch_tc<32>(a, in, jt, ar, w, plan, st);
+        default: return launch_tc<64>(a, in, jt, ar, w, plan, st);
+    }
+}
+
+TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
+                     const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st) {
+    switch (in.b) {
+        case 16: return build_plan<16>(in, jt, sd, out_rp, mcol, w, job_mask, unit0, unit1, st);
+        case 32: return build_plan<32>(in, jt, sd, out_rp, mcol, w, job_mask, unit0, unit1, st);
+        case 64: return build_plan<64>(in, jt, sd, out_rp, mcol, w, job_mask, unit0, unit1, st);
+        default: throw Error{-1, "the tensor-core path handles 16 x 16, 32 x 32 and 64 x 64 blocks"};
+    }
 }
 
 }  // namespace rdm

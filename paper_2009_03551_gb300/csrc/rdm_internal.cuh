@@ -328,4 +328,15 @@ void launch_compact_count(const CompactArgs &c, int *cnt, cudaStream_t st);
 // output blocks [d0, d1) of the group
 void launch_compact_copy(const CompactArgs &c, int d1, cudaStream_t st);
 
+// k_reblock.cu: the same matrix in b_out x b_out instead of b_in x b_in blocks.
+// Host pattern (rp/col of one matrix, local block indices; n orbitals): an
+// output block exists where a stored input block overlaps it.
+void reblock_pattern(const std::vector<int> &rp, const std::vector<int> &col, int b_in, int n, int b_out,
+                     std::vector<int> &rp_out, std::vector<int> &col_out);
+// Values of the nout output blocks (out_row/out_col: block row and column of
+// each, device) from the input matrix (device row_ptr/col/val, nb_in rows).
+void launch_reblock_vals(const int *in_rp, const int *in_col, const double *in_val, int nb_in, int b_in,
+                         const int *out_row, const int *out_col, double *out_val, int64_t nout, int b_out,
+                         cudaStream_t st);
+
 }  // namespace rdm

@@ -9,7 +9,7 @@ namespace rdm {
 // production behaviour.
 struct TcKnobs {
     long long wait_cycles = 0;  // bound of every mbarrier wait in SM clock cycles (0: ~2 s)
-    int hold = 0;               // 1: the producer first waits for a flag that nothing sets
+    int hold = 0;               // 1: the MMA thread first waits for a flag that nothing sets
     int window_words = 0;       // bitmap window of the tile-plan builders in 32-column words
                                 // (0: 512, i.e. 16,384 columns; wider windows take the serial merge)
 };
@@ -18,11 +18,11 @@ struct TcKnobs {
 struct TcWork {
     TcKnobs knobs;
     DevBuf<uint16_t> zero;      // zero operand blocks: one per CTA and K-step slot
-    DevBuf<int> tiles;          // per tile: job, I, -, nsteps, mask slot[4 x 8], column j[8]
+    DevBuf<int> tiles;          // per tile: job, I, -, nsteps, mask slot[TBM x TBN], column j[TBN]
     DevBuf<int> tile_cnt, tile_off;
     DevBuf<int> step_cnt;
     DevBuf<int64_t> step_off;
-    DevBuf<int> steps;          // per K-step: 4 A block indices, 8 B block indices (-1 = zero)
+    DevBuf<int> steps;          // per K-step: TBM A block indices, TBN B block indices (-1 = zero)
     DevBuf<int> counters;       // [0]: error bits of the product kernel
     DevBuf<int> scan32;
     DevBuf<int64_t> scan64;
@@ -35,6 +35,12 @@ struct TcPlan {
     int64_t nsteps;
 };
 
+// Block sizes the tensor-core kernel handles (16, 32, 64), and the block rows
+// of its 128 x 256 tiles for block size b (128 / b; 4 for other sizes, the
+// super-row of the CUDA-core path).
+bool tc_block_size_ok(int b);
+int tc_tile_rows(int b);
+
 // Convert the FP64 master values of `in` into hi/lo operand planes of
 // arithmetic `ar` in the K-major core-matrix layout of the MMA.  For fp16
 // every matrix is first scaled by a power of two (from its largest block
@@ -44,8 +50,8 @@ void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st);
 
 // Tile lists of one multiplication step from the output mask, for the jobs
 // selected by job_mask (per system tier) and the super-row units
-// [unit0, unit1) (unit = job * ceil(NB/4) + I covers block rows 4I..4I+3 of
-// the job).
+// [unit0, unit1) (unit = job * ceil(NB/TR) + I covers block rows
+// TR I .. TR I + TR - 1 of the job, TR = tc_tile_rows(b)).
 TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp,
                      const int *mcol, TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st);
 

@@ -41,7 +41,7 @@ EXPORTED = (
     "rdm_batch_create", "rdm_upload_h0", "rdm_upload_h1", "rdm_solve", "rdm_force_branches",
     "rdm_get_info", "rdm_get_p0_nnzb", "rdm_get_p1_nnzb", "rdm_get_p0", "rdm_get_p1",
     "rdm_get_alpha", "rdm_get_log", "rdm_block_product", "rdm_version", "rdm_bsr_dot_noalloc",
-    "rdm_set_test_knobs",
+    "rdm_set_test_knobs", "rdm_solve_async", "rdm_sync",
 )
 
 
@@ -62,7 +62,7 @@ class rdm_params(C.Structure):
                 ("max_iter", C.c_int32), ("mode", C.c_int32), ("min_iter", C.c_int32),
                 ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
                 ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("refine_x0", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("stall_window", C.c_int32), ("block_size", C.c_int32), ("autotune", C.c_int32)]
 
 
 class rdm_info(C.Structure):
@@ -74,7 +74,8 @@ class rdm_info(C.Structure):
                 ("kernel_ms", C.c_double * 7), ("kernel_flops", C.c_double * 4),
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
-                ("product_groups", C.c_int32), ("pad0", C.c_int32)]
+                ("product_groups", C.c_int32), ("block_size", C.c_int32), ("autotune_ms", C.c_double),
+                ("probe_ms", C.c_double * 3)]
 
 
 class rdm_test_knobs(C.Structure):
@@ -104,6 +105,8 @@ def _load():
         "rdm_upload_h0": (C.c_int, [H, C.c_int, C.POINTER(rdm_bsr), C.c_int64]),
         "rdm_upload_h1": (C.c_int, [H, C.c_int, C.c_int, C.POINTER(rdm_bsr)]),
         "rdm_solve": (C.c_int, [H, C.POINTER(rdm_info)]),
+        "rdm_solve_async": (C.c_int, [H]),
+        "rdm_sync": (C.c_int, [H, C.POINTER(rdm_info)]),
         "rdm_force_branches": (C.c_int, [H, C.POINTER(C.c_uint8), C.c_int]),
         "rdm_get_info": (C.c_int, [H, C.c_int, C.POINTER(rdm_info)]),
         "rdm_get_p0_nnzb": (C.c_int, [H, C.c_int, C.POINTER(C.c_int64)]),
@@ -227,6 +230,19 @@ def rdm_force_branches(h, seq) -> None:
 def rdm_solve(h) -> tuple:
     info = rdm_info()
     code = _check(h, _lib.rdm_solve(h, C.byref(info)), allow_warn=True)
+    return code, info
+
+
+def rdm_solve_async(h) -> None:
+    """Start the solve; it runs while the caller continues (rdm_sync waits)."""
+    _check(h, _lib.rdm_solve_async(h))
+
+
+def rdm_sync(h) -> tuple:
+    """Wait for the solve started by rdm_solve_async: (status, rdm_info)."""
+    info = rdm_info()
+    code = _lib.rdm_sync(h, C.byref(info))
+    _check(h, code, allow_warn=True)
     return code, info
 
 
@@ -415,6 +431,12 @@ class Solver:
     def solve(self):
         code, info = rdm_solve(self.h)
         return code, info
+
+    def solve_async(self):
+        rdm_solve_async(self.h)
+
+    def sync(self):
+        return rdm_sync(self.h)
 
     def p0(self, sys: int = 0, out=None) -> BsrResult:
         return rdm_get_p0(self.h, sys, out=out)

@@ -45,12 +45,16 @@ def _sym_bsr(rng, n, b, density, scale=1.0, decay=None):
     return a, Bsr.from_dense(a, b, drop_zero_blocks=False, keep_diagonal=True)
 
 
+@pytest.mark.parametrize("b", [16, 32, 64])
 @pytest.mark.parametrize("mode", ["mixed_bf16", "mixed_fp16"])
 @pytest.mark.parametrize("terms", [1, 2])
 @pytest.mark.parametrize("nblk", [3, 9, 13])
-def test_tc_block_product(rdm, mode, terms, nblk):
-    b = 32
-    rng = np.random.default_rng(7 * nblk + terms)
+def test_tc_block_product(rdm, b, mode, terms, nblk):
+    """Split products on the tensor cores for every block size they take
+    (16 x 16 blocks: 8 x 16-block tiles; 32: 4 x 8; 64: 2 x 4, each output
+    block spread over two TMEM lane quarters), ragged last block, with and
+    without the linear term and truncation."""
+    rng = np.random.default_rng(7 * nblk + terms + b)
     n = nblk * b - 5                                  # ragged last block
     a, A = _sym_bsr(rng, n, b, 0.35)
     bd, B = _sym_bsr(rng, n, b, 0.35, 0.5)
@@ -199,8 +203,7 @@ def test_final_tier_fp32_purification(rdm, cluster150, oracle150):
     s = cluster150
     ob, h1s = oracle150
     sol = rdm.Solver(0)
-    # final tier without FP64 products: X0^2 in FP32, the first-order products split
-    sol.set_params(tau=1e-6, tol=1e-9, mode=mode, max_iter=100, refine_x0=3, refine_x1=2)
+    sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x0=3)
     sol.load(s)
     code, info = sol.solve()
     assert code == rdm.RDM_OK and info.converged
@@ -242,6 +245,31 @@ def test_mixed_batch_with_converged_copies(rdm):
         one.solve()
         a1, a0 = sol.alpha(k), one.alpha()
         assert np.max(np.abs(a1 - a0)) / np.max(np.abs(a0)) <= 1e-6
+
+
+@pytest.mark.parametrize("b", [16, 64])
+@pytest.mark.parametrize("mode", ["mixed_bf16", "mixed_fp16"])
+def test_mixed_solve_other_block_sizes_vs_oracle(rdm, b, mode):
+    """The whole mixed ladder with 16 x 16 and 64 x 64 blocks (ragged last
+    block at 64) against oracle B at the same block partition."""
+    s = make_cluster(150, opa=8, b=b, cutoff=10.0, seed=11, dirs=("x", "y", "z"))
+    h0 = s.h0.to_dense()
+    h1s = [m.to_dense() for m in s.h1]
+    ob = tc2_response(h0, h1s, s.n_occ, s.b, tau=1e-6, tol=1e-9)
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, mode=mode, max_iter=100, refine_x0=3, refine_x1=2)
+    sol.load(s)
+    code, info = sol.solve()
+    assert code == rdm.RDM_OK and info.converged
+    assert info.tc_launches > 0 and info.kernel_flops[1] == 0.0
+    a = sol.alpha()
+    ao = polarizability(ob.p1s, h1s)
+    assert np.max(np.abs(a - ao)) / np.max(np.abs(ao)) <= 1e-6
+    assert rel_frobenius(sol.p0().to_dense(), ob.p0) <= 1e-5
+    assert max_rel_err(sol.p0().to_dense(), ob.p0) <= 1e-5
+    for d in range(3):
+        assert rel_frobenius(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-4
+        assert max_rel_err(sol.p1(0, d).to_dense(), ob.p1s[d]) <= 1e-4
 
 
 def test_expired_wait_returns_etimeout_and_the_handle_stays_usable(rdm, cluster150):
@@ -298,7 +326,7 @@ def test_test_knobs_are_validated(rdm):
 
 
 def test_mixed_modes_reject_unsupported_block_sizes_up_front(rdm):
-    s = make_chain(8, opa=4, b=4, spacing=2.8, cutoff=8.0, seed=0, dirs=("x",))
+    s = make_chain(8, opa=4, b=4, spacing=2.8, cutoff=8.0, seed=0, dirs=("x",))   # b = 4: below 16
     sol = rdm.Solver(0)
     sol.set_params(mode="mixed_fp16")
     with pytest.raises(rdm.RdmError) as e:
