@@ -44,8 +44,10 @@ FP64_PEAK_NOTE = ("GB300 FP64: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz =
 FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.5 TFLOP/s"
 DENSE_MAX_N = 16000       # largest system the dense CPU oracle may be given (N x N FP64: 2 GB)
 SAMPLE_ATOMS = 250        # atoms of the carve-out the CPU oracle solves (N = 2,000)
-# MMA work of one K-step of the tensor-core kernel: 3 products of 128 x 256 x 32
-TC_FLOPS_PER_KSTEP = 3 * 2 * 128 * 256 * 32
+# MMA work of one K-step of the tensor-core kernel at block size b: 3 products of 128 x 256 x b
+def tc_flops_per_kstep(b):
+    return 3 * 2 * 128 * 256 * b
+
 
 # DRAM traffic of the product kernels, from one ncu capture each (profiles/):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, divided by the work
@@ -56,8 +58,9 @@ TC_FLOPS_PER_KSTEP = 3 * 2 * 128 * 256 * 32
 # the capture (SHA-256 of the file with comments and whitespace removed).
 PROFILED_TRAFFIC = {
     "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
-           "sha256": "6a82385f0d0a5f5e14c70eba34567217d1377dd7c2340b3f90a7116d34ac1682",
-           "bytes_per_unit": None, "unit": "K-step"},
+           "sha256": "020e38747ccced213c166392d11fe045129567ac410f23f663b3573644e9f3ae",
+           "bytes_per_unit": 16045.0, "unit": "K-step", "b": 32,
+           "capture": "profiles/k_tc_bf16x3_dram_cluster1000.md"},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
            "sha256": "1c9d3e76e36659e5d06b0d237474522761ebecc2732c37eb20f037dc4adcb12e",
            "bytes_per_unit": None, "unit": "block triple"},
@@ -83,18 +86,23 @@ def parse():
     ap.add_argument("--tau-refine", type=float, default=-1.0,
                     help="threshold of the final (FP64/FP32) tier of the mixed modes (< 0: --tau); the "
                          "FP64 comparison solve runs at this threshold throughout")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1 (default): the library picks the block size of the products in {16, 32, 64} by timed "
+                         "probe solves during the warm-up; 0: the uploaded 32 x 32 blocks")
+    ap.add_argument("--block-size", type=int, default=0, help="block size of the products (0: uploaded; "
+                                                                "ignored with --autotune 1)")
     ap.add_argument("--sweep", default="",
                     help="tau or tol: instead of the timed solve, sweep the truncation threshold (or the "
                          "band-energy tolerance) on --workload and print one JSON line per point")
     return ap.parse_args()
 
 
-def profiled_traffic(cls, units_per_launch):
+def profiled_traffic(cls, units_per_launch, b=32):
     """DRAM bytes per launch of the class's kernel, scaled from the committed
     capture by the units the launch processes; None if there is no capture of
-    the current code."""
+    the current code at this block size."""
     rec = PROFILED_TRAFFIC.get(cls)
-    if rec is None or rec["bytes_per_unit"] is None or not units_per_launch:
+    if rec is None or rec["bytes_per_unit"] is None or not units_per_launch or rec.get("b", 32) != b:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["file"])
     try:
@@ -385,7 +393,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     torch.cuda.synchronize()
 
     sol = rdm.Solver(dev.index, stream.cuda_stream)
-    params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100)
+    params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100,
+                  autotune=args.autotune, block_size=args.block_size)
     tau64 = args.tau_refine if args.tau_refine > 0 else args.tau
     sol.set_params(**params)
     if nsys:
@@ -507,7 +516,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     # tensor-core split products, FP64, FP32 and double-FP32 CUDA-core products
     tc_ms, f64_ms, f32_ms, ff_ms = kms[1], kms[2], kms[3], kms[6]
     issued_tc = max(0.0, issued - (kfl[1] + kfl[2] + kfl[3]))
-    ksteps_per_launch = issued_tc / TC_FLOPS_PER_KSTEP / tc_launches if tc_launches else 0.0
+    bsz = int(last.block_size) or sys_.b
+    ksteps_per_launch = issued_tc / tc_flops_per_kstep(bsz) / tc_launches if tc_launches else 0.0
     classes = {
         "tc": ("k_tc_bf16x3 (tcgen05 split-precision block SpGEMM + fused truncation)", tc_ms, kfl[0],
                peaks["bf16_tflops"] * 1e12 / 3.0, "tensor",
@@ -524,7 +534,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     dom = max(classes, key=lambda k: classes[k][1])
     kname, k_ms, k_fl, peak, bound, peak_note = classes[dom]
     achieved = k_fl / (k_ms / 1e3) if k_ms > 0 else 0.0
-    traffic = profiled_traffic("tc", ksteps_per_launch) if dom == "tc" else None
+    traffic = profiled_traffic("tc", ksteps_per_launch, bsz) if dom == "tc" else None
     roofline = {"kernel": kname, "bound": bound, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
                 "ms_per_solve": k_ms, "peak_source": peak_note, "share_of_solve": k_ms / (s_per_solve * 1e3),
@@ -559,6 +569,9 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
                                     "reductions_setup_host": kms[5], "double_fp32_products": kms[6]},
+            "block_size": {"products": int(last.block_size), "uploaded": sys_.b,
+                           "autotune": {"on": bool(args.autotune), "probe_ms_b16_b32_b64": list(last.probe_ms),
+                                        "probe_total_ms": last.autotune_ms} if args.autotune else None},
             "tier_iterations": list(last.tier_iters)[:3],
             "device_gb_peak": last.device_bytes_peak / 1e9, "product_groups": int(last.product_groups),
             "clocks": clocks}

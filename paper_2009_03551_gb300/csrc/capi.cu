@@ -1140,6 +1140,35 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     return all_conv ? RDM_OK : RDM_NOT_CONVERGED;
 }
 
+// Free the solve's work buffers and matrix sets (the uploaded matrices stay):
+// between autotuning probes at different block sizes, whose grow-only buffers
+// would otherwise add up.
+void release_work(rdm_handle *h) {
+    for (auto *b : {&h->row_cnt, &h->row_off, &h->pool_col, &h->pool_npair, &h->mask_col, &h->out_rp, &h->slot_row,
+                    &h->slot_job, &h->slot_npair, &h->slot_x, &h->slot_t, &h->work, &h->work2, &h->work3,
+                    &h->scan_tmp32, &h->pair_a, &h->pair_b, &h->cnt_rows, &h->uidx, &h->scan_tmp_s, &h->urp,
+                    &h->dest, &h->cpsrc})
+        b->release();
+    h->pair_off.release();
+    h->scan_tmp64.release();
+    h->out_val.release();
+    h->out_nrm.release();
+    h->keep.release();
+    h->X[0].release();
+    h->X[1].release();
+    h->H0.release();
+    h->H1.release();
+    h->tcw.tiles.release();
+    h->tcw.steps.release();
+    h->tcw.step_cnt.release();
+    h->tcw.step_off.release();
+    h->tcw.tile_cnt.release();
+    h->tcw.tile_off.release();
+    h->tcw.zero.release();
+    h->pool_cap_hint = 0;
+    h->solved = false;
+}
+
 // The solve at the chosen block size: the uploaded b, rdm_params.block_size,
 // or (autotune) the fastest of one probe solve at each of 16, 32 and 64,
 // remembered until the next upload or parameter change.  A probe that runs
@@ -1157,6 +1186,7 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
         int best_b = 0, last_b = 0;
         for (int k = 0; k < 3; ++k) {
             h->probe_ms[k] = 0;
+            if (k > 0) release_work(h);
             h->bs = cand[k];
             int st;
             try {
@@ -1187,7 +1217,9 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
         for (double &x : h->probe_ms) x = 0;
     }
     if (!have_result) {
-        h->bs = P.autotune ? h->tuned_b : P.block_size > 0 ? P.block_size : h->b;
+        const int want = P.autotune ? h->tuned_b : P.block_size > 0 ? P.block_size : h->b;
+        if (P.autotune && h->bs != want) release_work(h);
+        h->bs = want;
         status = run_solve(h, nullptr);
         if (status < 0) return status;
     }

@@ -284,6 +284,29 @@ def test_batch_matches_individual_solves(rdm):
         assert np.max(np.abs(sol.alpha(k) - ae)) <= 1e-6 * np.max(np.abs(ae))
 
 
+def test_partitioned_batch_matches_the_whole_batch(rdm):
+    """The multi-GPU path partitions a batch over ranks (bench.partition) and
+    each rank solves its share as a batch of its own.  On one GPU: the two
+    shares of a 2-rank partition, solved one after the other, give every
+    system's P0 bit for bit, and alpha to rounding (the per-system sum of the
+    row partials may group differently), as the whole batch does (FP64)."""
+    import bench
+    systems = [make_chain(30, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=5, dirs=("x", "y", "z")),
+               make_cluster(60, opa=8, b=32, cutoff=10.0, seed=6, dirs=("x", "y", "z")),
+               make_cluster(23, opa=8, b=32, cutoff=10.0, seed=7, dirs=("x", "y", "z")),
+               make_chain(44, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=8, dirs=("x", "y", "z"))]
+    whole, code, _ = gpu_solve(rdm, systems, tau=1e-7, tol=1e-9, mode="fp64")
+    assert code == rdm.RDM_OK
+    shares = bench.partition([bench.work_estimate(s) for s in systems], 2)
+    assert sorted(shares[0] + shares[1]) == [0, 1, 2, 3] and shares[0] and shares[1]
+    for share in shares:
+        part, code, _ = gpu_solve(rdm, [systems[k] for k in share], tau=1e-7, tol=1e-9, mode="fp64")
+        assert code == rdm.RDM_OK
+        for q, k in enumerate(share):
+            assert np.array_equal(part.p0(q).vals, whole.p0(k).vals)
+            assert np.allclose(part.alpha(q), whole.alpha(k), rtol=1e-13, atol=0)
+
+
 def test_bad_inputs_are_rejected(rdm):
     s = make_config(1, n_atoms=8)
     h = rdm.rdm_create(0)
