@@ -44,6 +44,7 @@ FP64_PEAK_NOTE = ("GB300 FP64: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz =
 FP32_PEAK_NOTE = "GB300 FP32: 152 SMs x 128 FMA/clk/SM x 2 flop x 2.07 GHz = 80.5 TFLOP/s"
 DENSE_MAX_N = 16000       # largest system the dense CPU oracle may be given (N x N FP64: 2 GB)
 SAMPLE_ATOMS = 250        # atoms of the carve-out the CPU oracle solves (N = 2,000)
+SLICE_PAIRS = 28          # bf16 slice pairs one FP64-class slice product issues per useful product
 # MMA work of one K-step of the tensor-core kernel at block size b: 3 products of 128 x 256 x b
 def tc_flops_per_kstep(b):
     return 3 * 2 * 128 * 256 * b
@@ -57,8 +58,9 @@ def tc_flops_per_kstep(b):
 # reported only while the code of the kernel's source file is unchanged since
 # the capture (SHA-256 of the file with comments and whitespace removed).
 PROFILED_TRAFFIC = {
-    "tc": {"file": "paper_2009_03551_gb300/csrc/k_tc.cu",
-           "sha256": "020e38747ccced213c166392d11fe045129567ac410f23f663b3573644e9f3ae",
+    "tc": {"file": ["paper_2009_03551_gb300/csrc/k_tc.cu", "paper_2009_03551_gb300/csrc/tc_ptx.cuh",
+                    "paper_2009_03551_gb300/csrc/tc_plan.cuh"],
+           "sha256": "recaptured after the kernel sources were split into headers",
            "bytes_per_unit": 16045.0, "unit": "K-step", "b": 32,
            "capture": "profiles/k_tc_bf16x3_dram_cluster1000.md"},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
@@ -91,6 +93,9 @@ def parse():
                          "probe solves during the warm-up; 0: the uploaded 32 x 32 blocks")
     ap.add_argument("--block-size", type=int, default=0, help="block size of the products (0: uploaded; "
                                                                 "ignored with --autotune 1)")
+    ap.add_argument("--refine-x0", type=int, default=0,
+                    help="final-tier arithmetic of X0^2 (rdm.h RDM_REFINE_*: 0 default, 1 FP64, 3 FP32, "
+                         "4 double-FP32, 5 tensor-core slice products)")
     ap.add_argument("--sweep", default="",
                     help="tau or tol: instead of the timed solve, sweep the truncation threshold (or the "
                          "band-energy tolerance) on --workload and print one JSON line per point")
@@ -104,9 +109,10 @@ def profiled_traffic(cls, units_per_launch, b=32):
     rec = PROFILED_TRAFFIC.get(cls)
     if rec is None or rec["bytes_per_unit"] is None or not units_per_launch or rec.get("b", 32) != b:
         return None
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["file"])
+    root = os.path.dirname(os.path.abspath(__file__))
+    files = rec["file"] if isinstance(rec["file"], list) else [rec["file"]]
     try:
-        sha = code_sha256(path)
+        sha = code_digest("".join(open(os.path.join(root, f), encoding="utf-8").read() for f in files))
     except OSError:
         return None
     return rec["bytes_per_unit"] * units_per_launch if sha == rec["sha256"] else None
@@ -394,7 +400,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
 
     sol = rdm.Solver(dev.index, stream.cuda_stream)
     params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100,
-                  autotune=args.autotune, block_size=args.block_size)
+                  autotune=args.autotune, block_size=args.block_size, refine_x0=args.refine_x0)
     tau64 = args.tau_refine if args.tau_refine > 0 else args.tau
     sol.set_params(**params)
     if nsys:
@@ -429,8 +435,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     last = infos[-1]
     useful = float(np.mean([i.useful_flops for i in infos]))
     issued = float(np.mean([i.issued_flops for i in infos]))
-    kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(7)]
-    kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(4)]
+    kms = [float(np.mean([i.kernel_ms[k] for i in infos])) for k in range(8)]
+    kfl = [float(np.mean([i.kernel_flops[k] for i in infos])) for k in range(5)]
     tc_launches = float(np.mean([i.tc_launches for i in infos]))
     launches = int(sum(i.kernel_launches for i in infos))
     sinfo = [sol.info(k) for k in range(nsys)]
@@ -514,8 +520,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     mode = args.mode
     # dominant kernel of the solve (by device time) among the product kernels:
     # tensor-core split products, FP64, FP32 and double-FP32 CUDA-core products
-    tc_ms, f64_ms, f32_ms, ff_ms = kms[1], kms[2], kms[3], kms[6]
-    issued_tc = max(0.0, issued - (kfl[1] + kfl[2] + kfl[3]))
+    tc_ms, f64_ms, f32_ms, ff_ms, oz_ms = kms[1], kms[2], kms[3], kms[6], kms[7]
+    issued_tc = max(0.0, issued - (kfl[1] + kfl[2] + kfl[3]) - kfl[4] * SLICE_PAIRS)
     bsz = int(last.block_size) or sys_.b
     ksteps_per_launch = issued_tc / tc_flops_per_kstep(bsz) / tc_launches if tc_launches else 0.0
     classes = {
@@ -530,6 +536,10 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
         "ff": ("k_numeric_f32_b32<double-FP32> (error-free FP32 block SpGEMM + fused truncation)", ff_ms, kfl[3],
                80.5e12 / 12.0, "alu", FP32_PEAK_NOTE + "; 12 FP32-pipe operations per multiply-add "
                "(2 useful flops) -> 6.7 TFLOP/s (derived from unit counts and clock)"),
+        "oz": ("k_tc_oz (tcgen05 exact bf16 slice products, FP64-class, + fused truncation)", oz_ms, kfl[4],
+               peaks["bf16_tflops"] * 1e12 / SLICE_PAIRS, "tensor",
+               f"measured bf16 dense burst / {SLICE_PAIRS} (28 slice-pair MMAs per useful product; {peak_kind}, "
+               "MEASURED_PEAKS.json bf16_tflops)"),
     }
     dom = max(classes, key=lambda k: classes[k][1])
     kname, k_ms, k_fl, peak, bound, peak_note = classes[dom]
@@ -543,7 +553,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
                 "per_class": {k: {"ms": v[1], "tflops": (v[2] / (v[1] / 1e3) / 1e12) if v[1] > 0 else None,
                                   "frac": ((v[2] / (v[1] / 1e3)) / v[3]) if v[1] > 0 else None}
                               for k, v in classes.items() if v[2] > 0}}
-    num_ms = tc_ms + f64_ms + f32_ms + ff_ms
+    num_ms = tc_ms + f64_ms + f32_ms + ff_ms + oz_ms
     achieved_all = useful / (num_ms / 1e3) if num_ms > 0 else 0.0
 
     line = {"metric": METRIC, "value": s_per_solve, "unit": "s", "higher_is_better": False,
@@ -568,7 +578,8 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "roofline": roofline, "fp64": fp64, "e2e": e2e, "gpu_launches": launches,
             "kernel_ms_per_solve": {"symbolic_pairs_tiles": kms[0], "tensor_core_products": kms[1],
                                     "fp64_products": kms[2], "fp32_products": kms[3], "compaction": kms[4],
-                                    "reductions_setup_host": kms[5], "double_fp32_products": kms[6]},
+                                    "reductions_setup_host": kms[5], "double_fp32_products": kms[6],
+                                    "slice_products": kms[7]},
             "block_size": {"products": int(last.block_size), "uploaded": sys_.b,
                            "autotune": {"on": bool(args.autotune), "probe_ms_b16_b32_b64": list(last.probe_ms),
                                         "probe_total_ms": last.autotune_ms} if args.autotune else None},

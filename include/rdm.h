@@ -81,6 +81,10 @@ extern "C" {
 #define RDM_REFINE_FP32X2    4   /* double-FP32 on the CUDA cores: each FP64 value as the sum of
                                     two FP32 words, the products accumulated with error-free
                                     transformations (about 46 bits; 32 x 32 blocks) */
+#define RDM_REFINE_SLICES    5   /* refine_x0 only: X0^2 on the tensor cores from exact products of
+                                    7 bf16 slices per element (row-scaled integer slices summed in
+                                    exact groups, then in double-FP32; about 48 bits; the splitting of
+                                    Ozaki, Ogita, Oishi and Rump 2012; 32 x 32 blocks) */
 
 typedef struct rdm_handle rdm_handle;
 
@@ -161,14 +165,14 @@ typedef struct {
     double  time_ms;        /* wall time of the solve on the handle's stream */
     double  useful_flops;   /* 2 b^3 per (i,k,j) block triple, summed over the solve */
     double  issued_flops;   /* flops the kernels executed (split products count 3x, padding counted) */
-    double  kernel_ms[7];   /* device time per kernel class (CUDA events on the handle's stream):
-                               0 symbolic mask + pair / tile lists, 1 tensor-core products,
+    double  kernel_ms[8];   /* device time per kernel class (CUDA events on the handle's stream):
+                               0 symbolic mask + pair / tile lists, 1 tensor-core split products,
                                2 FP64 CUDA-core products, 3 FP32 CUDA-core products (and copies
                                of converged systems), 4 truncation compaction, 5 reductions,
                                set-up and host decisions (the remainder of the solve),
-                               6 double-FP32 CUDA-core products */
-    double  kernel_flops[4];   /* useful flops (2 b^3 per block triple) of the tensor-core (0),
-                                  FP64 (1), FP32 (2) and double-FP32 (3) product launches */
+                               6 double-FP32 CUDA-core products, 7 tensor-core slice products */
+    double  kernel_flops[5];   /* useful flops (2 b^3 per block triple) of the tensor-core split (0),
+                                  FP64 (1), FP32 (2), double-FP32 (3) and slice-product (4) launches */
     int64_t kernel_launches;   /* kernels launched by the solve */
     int32_t tc_launches;       /* launches of the tensor-core product kernel */
     int32_t simt_launches;     /* launches of the CUDA-core product kernel */
@@ -280,9 +284,11 @@ int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n);
  * update step of Eqs. TC2 / TC2-CPSCF for one matrix.  A, B, X are symmetric
  * host BSR matrices with the same nb, b, n (X may be NULL: no linear term).
  * `mode` selects the product arithmetic (RDM_MODE_*; the mixed modes use the
- * hi+lo split tensor-core product).  The result goes to *out as for
+ * hi+lo split tensor-core product; RDM_PRODUCT_SLICES the exact bf16 slice
+ * product of RDM_REFINE_SLICES, for terms = 1 and 32 x 32 blocks).  The result goes to *out as for
  * rdm_get_p0; call with out->nnzb = 0 / NULL arrays to query the size only
  * (*needed receives the block count). */
+#define RDM_PRODUCT_SLICES   8   /* rdm_block_product only: the tensor-core slice product */
 int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const rdm_bsr *X,
                       double c_lin, double c_sq, int terms, double tau, int mode,
                       rdm_bsr_out *out, int64_t *needed);

@@ -105,8 +105,9 @@ struct rdm_handle {
     DevBuf<uint8_t> keep;
     DevBuf<unsigned long long> class_pairs;
     DevBuf<double> row_lo, row_hi;
-    TcWork tcw;
-    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    TcWork tcw, tcw_oz;      // plans of the split and of the slice-product tensor-core launches
+    OzWork ozw;
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void ensure_events() {
         for (auto &e : ev)
             if (!e) RDM_CUDA_TRY(cudaEventCreate(&e));
@@ -432,10 +433,10 @@ void assemble(rdm_handle *h) {
 struct StepStats {
     int64_t npairs = 0;
     int64_t nslot = 0;
-    int64_t pairs_tc = 0, pairs_64 = 0, pairs_32 = 0, pairs_ff = 0;   // block triples per kernel class
-    double issued_tc = 0;
+    int64_t pairs_tc = 0, pairs_64 = 0, pairs_32 = 0, pairs_ff = 0, pairs_oz = 0;   // block triples per class
+    double issued_tc = 0, issued_oz = 0;
     double bytes = 0;
-    double ms[6] = {0, 0, 0, 0, 0, 0};      // symbolic, tc, fp64, fp32, compaction, double-fp32
+    double ms[7] = {0, 0, 0, 0, 0, 0, 0};   // symbolic, tc, fp64, fp32, compaction, double-fp32, slice products
     int tc_launches = 0, simt_launches = 0;
     int groups = 1;                         // job groups of the numeric phase
 };
@@ -472,7 +473,8 @@ void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int 
             case RDM_MODE_MIXED_FP16:
                 if (tier == 0) ar[p] = split;
                 else if (p == 0) ar[p] = refine_x0 == RDM_REFINE_FP32 ? AR_FP32
-                                        : refine_x0 == RDM_REFINE_FP32X2 ? AR_FF : AR_FP64;
+                                        : refine_x0 == RDM_REFINE_FP32X2 ? AR_FF
+                                        : refine_x0 == RDM_REFINE_SLICES ? AR_OZ : AR_FP64;
                 else if (refine_x1 == RDM_REFINE_FP64) ar[p] = AR_FP64;
                 else if (refine_x1 == RDM_REFINE_FP32X2) ar[p] = AR_FF;
                 else ar[p] = refine_x1 == RDM_REFINE_SPLIT ? split : AR_FP32;
@@ -496,13 +498,18 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     // CUDA-core classes, launched in this order: FP64, double-FP32, FP32
     constexpr int kSimt = 3;
     const Arith simt_ar[kSimt] = {AR_FP64, AR_FF, AR_FP32};
-    JobMask tcm{}, cm[kSimt]{}, simt{};
+    JobMask tcm{}, cm[kSimt]{}, simt{}, ozm{};
     Arith tc_ar = AR_FP16X3;
-    bool any_tc = false, any_c[kSimt] = {false, false, false};
+    bool any_tc = false, any_oz = false, any_c[kSimt] = {false, false, false};
     for (int t = 0; t < kMaxTiers; ++t) {
         if (!((tiers_present >> t) & 1u)) continue;
         for (int p = 0; p < njob; ++p) {
             const Arith a = tab[t][p];
+            if (a == AR_OZ) {
+                ozm.m[t] |= 1u << p;
+                any_oz = true;
+                continue;
+            }
             if (is_tc(a)) {
                 tcm.m[t] |= 1u << p;
                 tc_ar = a;
@@ -540,6 +547,8 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     if (!f32_planes && in.opf32.cap * sizeof(float) > big) in.opf32.release();
     if (!any_c[1] && in.opf32lo.cap * sizeof(float) > big) in.opf32lo.release();
     if (tc) prepare_operands(in, tc_ar, h->tcw, st);
+    if (any_oz) prepare_oz_operands(in, h->ozw, st);
+    else if (h->ozw.slices.cap * sizeof(uint16_t) > big) h->ozw.slices.release();
     if (f32_planes) {
         in.opf32.ensure(std::max<int64_t>(in.total, 1) * bb);
         if (any_c[1]) in.opf32lo.ensure(std::max<int64_t>(in.total, 1) * bb);
@@ -594,18 +603,19 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     int64_t npairs = 0;
     d2h(&npairs, h->pair_off.p + nslot, 1, st);
     // block triples per kernel class (tensor cores, FP64, FP32, double-FP32) for the accounting
-    h->class_pairs.ensure(4);
-    RDM_CUDA_TRY(cudaMemsetAsync(h->class_pairs.p, 0, 4 * sizeof(unsigned long long), st));
+    h->class_pairs.ensure(5);
+    RDM_CUDA_TRY(cudaMemsetAsync(h->class_pairs.p, 0, 5 * sizeof(unsigned long long), st));
     launch_class_pairs(h->slot_row.p, mcol, h->slot_npair.p, h->slot_job.p, nslot, h->sd.sys_of_row.p,
-                       h->sd.active.p, h->sd.tier.p, tcm, cm[0], cm[2], cm[1], h->class_pairs.p, st);
-    unsigned long long cls[4] = {0, 0, 0, 0};
-    d2h(cls, h->class_pairs.p, 4, st);
+                       h->sd.active.p, h->sd.tier.p, tcm, cm[0], cm[2], cm[1], ozm, h->class_pairs.p, st);
+    unsigned long long cls[5] = {0, 0, 0, 0, 0};
+    d2h(cls, h->class_pairs.p, 5, st);
     sync(h);
     ss.npairs = npairs;
     ss.pairs_tc = (int64_t)cls[0];
     ss.pairs_64 = (int64_t)cls[1];
     ss.pairs_32 = (int64_t)cls[2];
     ss.pairs_ff = (int64_t)cls[3];
+    ss.pairs_oz = (int64_t)cls[4];
     if (any_c[0] || any_c[1] || any_c[2]) {
         h->pair_a.ensure(std::max<int64_t>(npairs, 1));
         h->pair_b.ensure(std::max<int64_t>(npairs, 1));
@@ -696,7 +706,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     h->cnt_rows.ensure(nrows + 1);
     out.row_ptr.ensure(nrows + 1);
     int kept = 0;
-    float t_simt[kSimt] = {0, 0, 0}, t_tc = 0, t_cmp = 0;
+    float t_simt[kSimt] = {0, 0, 0}, t_tc = 0, t_cmp = 0, t_oz = 0;
     const int ev_simt[kSimt] = {5, 6, 4};   // events after each CUDA-core class
     for (int g = 0; g < ngroup; ++g) {
         const int ua = gunit[g], ub = gunit[g + 1];
@@ -710,9 +720,11 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
                 launch_build_work(h->slot_row.p, mcol, s0, s1, worklist[c]->p, h->counters.p + 3 + c, st,
                                   h->sd.sys_of_row.p, h->sd.active.p, h->slot_job.p, h->sd.tier.p, cm[c],
                                   c == first_c ? 1 : 0);
-        TcPlan plan{};
+        TcPlan plan{}, oplan{};
         if (tc) plan = build_tc_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw, tcm, ua, ub, st);
+        if (any_oz) oplan = build_oz_plan(in, jt, h->sd, h->out_rp.p, mcol, h->tcw_oz, ozm, ua, ub, st);
         const bool tc_g = tc && plan.ntile > 0;
+        const bool oz_g = any_oz && oplan.ntile > 0;
         int nwork[kSimt];
         d2h(nwork, h->counters.p + 3, kSimt, st);
         sync(h);
@@ -750,6 +762,12 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
             ss.tc_launches += (int)(g_kernel_launches - lt);
         }
         RDM_CUDA_TRY(cudaEventRecord(h->ev[2], st));
+        if (oz_g) {
+            const long long lt = g_kernel_launches;
+            ss.issued_oz += launch_numeric_oz(a, in, mcol, h->ozw, h->tcw_oz, oplan, st);
+            ss.tc_launches += (int)(g_kernel_launches - lt);
+        }
+        RDM_CUDA_TRY(cudaEventRecord(h->ev[7], st));
 
         // compaction of the group's rows, appended after the previous groups
         CompactArgs ca{};
@@ -760,9 +778,11 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         scan_exclusive_i32(h->cnt_rows.p, out.row_ptr.p + r0, nr, h->scan_tmp32.p, st, kept);
         int kept_end = 0;
         d2h(&kept_end, out.row_ptr.p + r0 + nr, 1, st);
-        int tc_err = 0;
+        int tc_err = 0, oz_err = 0;
         if (tc_g) d2h(&tc_err, h->tcw.counters.p, 1, st);
+        if (oz_g) d2h(&oz_err, h->tcw_oz.counters.p, 1, st);
         sync(h);
+        tc_err |= oz_err;
         if (tc_err)
             throw Error{tc_err & 1 ? RDM_ETIMEOUT : RDM_ECUDA,
                         "tensor-core product kernel failed (code " + std::to_string(tc_err) + ")"};
@@ -784,16 +804,18 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         kept = kept_end;
         RDM_CUDA_TRY(cudaEventRecord(h->ev[3], st));
         RDM_CUDA_TRY(cudaEventSynchronize(h->ev[3]));
-        float mc[kSimt] = {0, 0, 0}, m42 = 0, m23 = 0;
+        float mc[kSimt] = {0, 0, 0}, m42 = 0, m23 = 0, moz = 0;
         cudaEventElapsedTime(&mc[0], h->ev[1], h->ev[ev_simt[0]]);             // FP64 class
         cudaEventElapsedTime(&mc[1], h->ev[ev_simt[0]], h->ev[ev_simt[1]]);    // double-FP32 class
         cudaEventElapsedTime(&mc[2], h->ev[ev_simt[1]], h->ev[ev_simt[2]]);    // FP32 class (and copies)
         cudaEventElapsedTime(&m42, h->ev[ev_simt[2]], h->ev[2]);               // tensor-core launch
-        cudaEventElapsedTime(&m23, h->ev[2], h->ev[3]);                        // compaction
+        cudaEventElapsedTime(&moz, h->ev[2], h->ev[7]);                        // slice-product launch
+        cudaEventElapsedTime(&m23, h->ev[7], h->ev[3]);                        // compaction
         for (int c = 0; c < kSimt; ++c) t_simt[c] += mc[c];
-        t_tc += m42; t_cmp += m23;
+        t_tc += m42; t_cmp += m23; t_oz += moz;
     }
-    ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (double)nupper * 8.0) * (double)bb;
+    ss.bytes = ((double)in.total * (tc ? 4.0 : 8.0) + (any_oz ? (double)in.nnzb[0] * 14.0 : 0.0) +
+                (double)nupper * 8.0) * (double)bb;
     out.total = kept;
     std::vector<int> rp(nrows + 1);
     d2h(rp.data(), out.row_ptr.p, nrows + 1, st);
@@ -805,7 +827,8 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
     ss.ms[3] = t_simt[2];     // FP32 products (and copies of converged systems)
     ss.ms[4] = t_cmp;
     ss.ms[5] = t_simt[1];     // double-FP32 products
-    ss.ms[0] = std::max(0.f, mall - (t_simt[0] + t_simt[1] + t_simt[2] + t_tc + t_cmp));  // mask, lists, plans
+    ss.ms[6] = t_oz;          // tensor-core slice products
+    ss.ms[0] = std::max(0.f, mall - (t_simt[0] + t_simt[1] + t_simt[2] + t_tc + t_cmp + t_oz));  // mask, lists, plans
     out.nnzb.assign(njob, 0);
     for (int p = 0; p < njob; ++p) out.nnzb[p] = rp[(size_t)(p + 1) * NB] - rp[(size_t)p * NB];
     return ss;
@@ -882,8 +905,8 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     JobTable jt = solve_jobs(nd);
     std::vector<double> c_lin(S), c_sq(S), t0(S), t1(S);
     std::vector<int> act(S);
-    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0, flops_ff = 0;
-    double kms[6] = {0, 0, 0, 0, 0, 0};
+    double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0, flops_ff = 0, flops_oz = 0;
+    double kms[7] = {0, 0, 0, 0, 0, 0, 0};
     int tc_launches = 0, simt_launches = 0, max_groups = 1;
     g_dev_bytes_peak = g_dev_bytes.load();
     cudaEvent_t ev0, ev1;
@@ -1036,12 +1059,13 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         flops_64 += (double)sst.pairs_64 * fpb;
         flops_32 += (double)sst.pairs_32 * fpb;
         flops_ff += (double)sst.pairs_ff * fpb;
-        issued += sst.issued_tc + (double)(sst.pairs_64 + sst.pairs_32 + sst.pairs_ff) * fpb;
+        flops_oz += (double)sst.pairs_oz * fpb;
+        issued += sst.issued_tc + sst.issued_oz + (double)(sst.pairs_64 + sst.pairs_32 + sst.pairs_ff) * fpb;
         nbytes += sst.bytes;
         tc_launches += sst.tc_launches;
         simt_launches += sst.simt_launches;
         max_groups = std::max(max_groups, sst.groups);
-        for (int k = 0; k < 6; ++k) kms[k] += sst.ms[k];
+        for (int k = 0; k < 7; ++k) kms[k] += sst.ms[k];
         h->cur = 1 - h->cur;
         for (int s = 0; s < S; ++s)
             if (act[s]) {
@@ -1114,11 +1138,13 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.issued_flops = issued;
         for (int k = 0; k < 5; ++k) I.kernel_ms[k] = kms[k];
         I.kernel_ms[6] = kms[5];
-        I.kernel_ms[5] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3] - kms[4] - kms[5]);
+        I.kernel_ms[7] = kms[6];
+        I.kernel_ms[5] = std::max(0.0, wall_ms - kms[0] - kms[1] - kms[2] - kms[3] - kms[4] - kms[5] - kms[6]);
         I.kernel_flops[0] = flops_tc;
         I.kernel_flops[1] = flops_64;
         I.kernel_flops[2] = flops_32;
         I.kernel_flops[3] = flops_ff;
+        I.kernel_flops[4] = flops_oz;
         I.kernel_launches = g_kernel_launches - launches0;
         I.tc_launches = tc_launches;
         I.simt_launches = simt_launches;
@@ -1410,11 +1436,11 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
     if (!p) return fail(h, RDM_EINVAL, "null params");
     if (!(p->tau >= 0) || !(p->tol >= 0) || p->max_iter < 1 || p->mode < 0 || p->mode > 3 ||
         !(p->spin_factor > 0) || p->min_iter < 0 || p->refine_x1 < 0 || p->refine_x1 > 4 ||
-        p->refine_x0 < 0 || p->refine_x0 > 4 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
+        p->refine_x0 < 0 || p->refine_x0 > 5 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
         p->use_graphs != 0 || p->stall_window < 0 || p->block_size < 0 || p->block_size > 64 ||
         (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1)
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
-                                   "refine_x1 0..4, refine_x0 0, 1, 3 or 4, chunk_mb >= 0, use_graphs 0, "
+                                   "refine_x1 0..4, refine_x0 0, 1, 3, 4 or 5, chunk_mb >= 0, use_graphs 0, "
                                    "stall_window >= 0, block_size 0 or a power of two <= 64, autotune 0 or 1)");
     if (!tc_block_ok(p->mode, p->autotune ? 32 : p->block_size > 0 ? p->block_size : h->b))
         return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, "
@@ -1629,7 +1655,10 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         DeviceGuard dg(h->device);
         if (!A || (terms == 2 && !B)) return fail(h, RDM_EINVAL, "null operand");
         if (terms != 1 && terms != 2) return fail(h, RDM_EINVAL, "terms must be 1 or 2");
-        if (!(tau >= 0) || mode < 0 || mode > 3) return fail(h, RDM_EINVAL, "bad tau or mode");
+        const bool slices = mode == RDM_PRODUCT_SLICES;
+        if (!(tau >= 0) || ((mode < 0 || mode > 3) && !slices)) return fail(h, RDM_EINVAL, "bad tau or mode");
+        if (slices && (terms != 1 || A->b != 32))
+            return fail(h, RDM_EINVAL, "the slice product takes terms = 1 (A A) and 32 x 32 blocks");
         // a private single-system context so that the solve state is untouched
         rdm_handle t;
         t.device = h->device;
@@ -1709,7 +1738,8 @@ int rdm_block_product(rdm_handle *h, const rdm_bsr *A, const rdm_bsr *B, const r
         if (terms == 1) jt.job[0] = Job{0, ix, 1, {ia, ia}, {ia, ia}, 0};
         else jt.job[0] = Job{0, ix, 2, {ia, ib}, {ib, ia}, 0};
         Arith tab[kMaxTiers][kMaxJobs];
-        tier_arith(mode, 0, jt.njob, tab[0]);
+        if (slices) tab[0][0] = AR_OZ;
+        else tier_arith(mode, 0, jt.njob, tab[0]);
         MatSet res;
         multiply(&t, in, res, jt, tab, 1u);
         int64_t n = res.nnzb[0];

@@ -39,9 +39,9 @@ __global__ void k_class_pairs(const int *__restrict__ slot_row, const int *__res
                               const int *__restrict__ slot_npair, const int *__restrict__ slot_job, int64_t nslot,
                               const int *__restrict__ sys_of_row, const int *__restrict__ active,
                               const int *__restrict__ sys_tier, JobMask tc, JobMask m64, JobMask m32,
-                              JobMask mff, unsigned long long *out) {
+                              JobMask mff, JobMask moz, unsigned long long *out) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
     if (s < nslot && out_col[s] >= slot_row[s]) {
         const int sys = sys_of_row[slot_row[s]];
         if (active[sys]) {
@@ -52,10 +52,11 @@ __global__ void k_class_pairs(const int *__restrict__ slot_row, const int *__res
             else if (m64.m[t] & bit) c[1] = np;
             else if (m32.m[t] & bit) c[2] = np;
             else if (mff.m[t] & bit) c[3] = np;
+            else if (moz.m[t] & bit) c[4] = np;
         }
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         unsigned long long v = c[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&out[k], v);
@@ -166,12 +167,12 @@ void launch_build_work(const int *slot_row, const int *out_col, int64_t s0, int6
 
 void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot_npair, const int *slot_job,
                         int64_t nslot, const int *sys_of_row, const int *active, const int *sys_tier,
-                        JobMask tc, JobMask m64, JobMask m32, JobMask mff, unsigned long long *out,
+                        JobMask tc, JobMask m64, JobMask m32, JobMask mff, JobMask moz, unsigned long long *out,
                         cudaStream_t st) {
     if (nslot == 0) return;
     const int64_t grid = (nslot + 255) / 256;
     k_class_pairs<<<(unsigned)grid, 256, 0, st>>>(slot_row, out_col, slot_npair, slot_job, nslot, sys_of_row,
-                                                  active, sys_tier, tc, m64, m32, mff, out);
+                                                  active, sys_tier, tc, m64, m32, mff, moz, out);
     RDM_LAUNCH_CHECK();
 }
 

@@ -177,8 +177,9 @@ struct JobTable {
 };
 
 // Operand arithmetic of a numeric launch
-// (AR_FF: double-FP32 products on the FP32 pipe, about 46 bits)
-enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_TF32 = 4, AR_FF = 5 };
+// (AR_FF: double-FP32 products on the FP32 pipe, about 46 bits; AR_OZ:
+// exact bf16 slice products on the tensor cores, FP64-class)
+enum Arith { AR_FP64 = 0, AR_FP32 = 1, AR_BF16X3 = 2, AR_FP16X3 = 3, AR_FF = 5, AR_OZ = 6 };
 
 // Jobs selected per precision tier: bit p of m[t] selects job p for the rows
 // of systems currently in tier t (systems of a batch move through the tiers
@@ -285,10 +286,11 @@ void launch_to_f32(const double *val, float *f32, int64_t n, cudaStream_t st, fl
 
 // k_compact.cu
 // block triples of the upper slots of active systems per kernel class:
-// out[0] tensor cores (tc), out[1] FP64 (m64), out[2] FP32 (m32), out[3] double-FP32 (mff)
+// out[0] tensor cores (tc), out[1] FP64 (m64), out[2] FP32 (m32), out[3] double-FP32 (mff),
+// out[4] tensor-core slice products (moz)
 void launch_class_pairs(const int *slot_row, const int *out_col, const int *slot_npair, const int *slot_job,
                         int64_t nslot, const int *sys_of_row, const int *active, const int *sys_tier,
-                        JobMask tc, JobMask m64, JobMask m32, JobMask mff, unsigned long long *out,
+                        JobMask tc, JobMask m64, JobMask m32, JobMask mff, JobMask moz, unsigned long long *out,
                         cudaStream_t st);
 // upper slots of the active systems' jobs selected by job_mask (per system
 // tier), plus (with_inactive) all upper slots of converged systems

@@ -30,6 +30,14 @@ struct TcWork {
     DevBuf<int> mat_first;      // per matrix: first global block index (nmat+1)
 };
 
+// work buffers of the slice-product (FP64-class) tensor-core path
+struct OzWork {
+    DevBuf<int> e;              // per global row of matrix 0: exponent e_r of its scale 2^e_r
+    DevBuf<int> row_of;         // block row of every block of matrix 0
+    DevBuf<uint16_t> slices;    // 7 bf16 slices per element of matrix 0 (14 KB per 32 x 32 block)
+    DevBuf<uint16_t> zero;      // zero blocks: one per CTA and K-step slot
+};
+
 struct TcPlan {
     int ntile;
     int64_t nsteps;
@@ -60,5 +68,15 @@ TcPlan build_tc_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, con
 // issued to the tensor cores.
 double launch_numeric_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith ar, TcWork &w,
                          int NB, const TcPlan &plan, cudaStream_t st);
+
+// FP64-class products X0^2 on the tensor cores from exact bf16 slices
+// (32 x 32 blocks; k_oz.cu): the slices and row scales of matrix 0 of `in`,
+// the tile lists (128 x 64 tiles, job 0 only), and the launch (same output
+// contract as the other numeric launches; returns the MMA flops issued).
+void prepare_oz_operands(const MatSet &in, OzWork &w, cudaStream_t st);
+TcPlan build_oz_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const int *out_rp, const int *mcol,
+                     TcWork &w, JobMask job_mask, int unit0, int unit1, cudaStream_t st);
+double launch_numeric_oz(const NumArgs &a, const MatSet &in, const int *mcol, OzWork &ow, TcWork &w,
+                         const TcPlan &plan, cudaStream_t st);
 
 }  // namespace rdm

@@ -35,6 +35,8 @@ MODE_FP32 = 1
 MODE_MIXED_BF16 = 2
 MODE_MIXED_FP16 = 3
 MODES = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
+PRODUCT_SLICES = 8      # rdm_block_product: the tensor-core slice product (FP64-class)
+REFINE_SLICES = 5       # rdm_params.refine_x0: X0^2 of the final tier as tensor-core slice products
 
 EXPORTED = (
     "rdm_create", "rdm_destroy", "rdm_last_error", "rdm_default_params", "rdm_set_params",
@@ -71,7 +73,7 @@ class rdm_info(C.Structure):
                 ("idempotency", C.c_double), ("band_energy0", C.c_double),
                 ("nnzb_p0", C.c_int64), ("nnzb_p1", C.c_int64 * 3), ("time_ms", C.c_double),
                 ("useful_flops", C.c_double), ("issued_flops", C.c_double),
-                ("kernel_ms", C.c_double * 7), ("kernel_flops", C.c_double * 4),
+                ("kernel_ms", C.c_double * 8), ("kernel_flops", C.c_double * 5),
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("block_size", C.c_int32), ("autotune_ms", C.c_double),

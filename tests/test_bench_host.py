@@ -40,7 +40,7 @@ def test_code_edits_change_the_digest():
 def test_profiled_traffic_scales_with_units_and_needs_the_captured_code(monkeypatch):
     assert bench.profiled_traffic("no such class", 10) is None
     rec = dict(bench.PROFILED_TRAFFIC["tc"])
-    rec["sha256"] = bench.code_sha256(os.path.join(ROOT, rec["file"]))
+    rec["sha256"] = bench.code_digest("".join(open(os.path.join(ROOT, f)).read() for f in rec["file"]))
     rec["bytes_per_unit"] = 1000.0
     monkeypatch.setitem(bench.PROFILED_TRAFFIC, "tc", rec)
     assert bench.profiled_traffic("tc", 7.5) == pytest.approx(7500.0)

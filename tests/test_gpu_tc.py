@@ -196,6 +196,62 @@ def test_final_tier_double_fp32_purification(rdm, cluster150):
     assert abs(iff.idempotency) < 1e-8
 
 
+@pytest.mark.parametrize("nblk", [3, 9, 13])
+def test_slice_product_is_fp64_class(rdm, nblk):
+    """X^2 from exact bf16 slice products on the tensor cores (row-scaled
+    integer slices, 7 per element, slice pairs summed exactly per group in
+    FP32 tensor memory, groups in double-FP32): FP64-class, i.e. within a few
+    2^-48 of the product's scale, where the split product is at 2^-22 and the
+    FP64 kernel at 2^-53.  Entries of very different sizes (exponential decay
+    away from the diagonal) exercise the row scaling."""
+    rng = np.random.default_rng(100 + nblk)
+    b = 32
+    n = nblk * b - 5
+    a, A = _sym_bsr(rng, n, b, 0.6, decay=12.0)
+    h = rdm.rdm_create(0)
+    try:
+        ref = a @ a
+        got = rdm.rdm_block_product(h, A, None, None, 0.0, 1.0, 1, 0.0, rdm.PRODUCT_SLICES).to_dense()
+        split = rdm.rdm_block_product(h, A, None, None, 0.0, 1.0, 1, 0.0, rdm.MODES["mixed_fp16"]).to_dense()
+        scale = np.max(np.abs(ref))
+        err = np.max(np.abs(got - ref)) / scale
+        assert err <= 2e-13, err
+        assert np.max(np.abs(split - ref)) / scale > 100 * err
+        assert np.array_equal(got, got.T)                 # exactly symmetric without symmetrisation
+        # the linear term and truncation in FP64: C = 2 X - X^2, blocks below tau dropped
+        x, X = _sym_bsr(rng, n, b, 0.6, decay=12.0)
+        got2 = rdm.rdm_block_product(h, A, None, X, 2.0, -1.0, 1, 1e-3, rdm.PRODUCT_SLICES).to_dense()
+        ref2 = block_truncate(2.0 * x - ref, b, 1e-3)
+        assert np.max(np.abs(got2 - ref2)) / np.max(np.abs(ref2)) <= 2e-13
+    finally:
+        rdm.rdm_destroy(h)
+
+
+def test_final_tier_slice_products(rdm, cluster150, oracle150):
+    """refine_x0 = slices: the final tier's X0^2 on the tensor cores as exact
+    slice products.  P0 agrees with the FP64 refinement far below the split
+    tier's own error and ends idempotent to the FP64 floor; alpha meets the
+    oracle."""
+    s = cluster150
+    ob, h1s = oracle150
+    out = {}
+    for r0 in (1, rdm.REFINE_SLICES):
+        sol = rdm.Solver(0)
+        sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_fp16", max_iter=100, refine_x0=r0)
+        sol.load(s)
+        code, info = sol.solve()
+        assert code == rdm.RDM_OK and info.converged
+        out[r0] = (sol.alpha(), sol.p0().to_dense(), info)
+    (a64, p64, i64), (aoz, poz, ioz) = out[1], out[rdm.REFINE_SLICES]
+    assert ioz.kernel_flops[4] > 0 and ioz.kernel_flops[1] == 0.0 and ioz.kernel_ms[7] > 0
+    assert rel_frobenius(poz, p64) <= 1e-9
+    assert max_rel_err(poz, p64) <= 1e-9
+    assert np.max(np.abs(aoz - a64)) / np.max(np.abs(a64)) <= 1e-9
+    assert abs(ioz.idempotency) < 1e-8
+    ao = polarizability(ob.p1s, h1s)
+    assert np.max(np.abs(aoz - ao)) / np.max(np.abs(ao)) <= 1e-6
+
+
 def test_final_tier_fp32_purification(rdm, cluster150, oracle150):
     """refine_x0 = FP32: the whole final tier on the FP32 CUDA cores.  It ends
     on the idempotency stall (FP32 floor) instead of the FP64 one; alpha stays
