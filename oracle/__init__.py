@@ -12,6 +12,9 @@ Contents (each function cites the paper passage it follows):
                 occupied eigenvectors, P1 by the sum-over-states formula
                 (Sec. 2.1, Eqs. DM1, CPSCF-U, epsilon1, cpscf-LCAO), and the
                 polarizability (Eq. polar).
+* ``lowdin``  - the non-orthogonal basis (Sec. 2.2): S^(-1/2) from the
+                eigenpairs of S, the orthogonal-form Hamiltonians, Oracle A
+                there, and the back-transform of P0 and P1.
 * ``tc2``     - Oracle B, the algorithm step by step: Gershgorin bounds, the
                 initial matrices, the TC2 recursion (Eq. TC2) coupled to the
                 first-order recursion (Eq. TC2-CPSCF), block-norm truncation
@@ -29,6 +32,7 @@ from .dense import (  # noqa: F401
     projector_invariants,
     response_invariants,
 )
+from .lowdin import inverse_sqrt, lowdin_response  # noqa: F401
 from .tc2 import (  # noqa: F401
     gershgorin_bounds,
     block_truncate,

@@ -14,5 +14,6 @@ from .systems import (  # noqa: F401
     make_config,
     make_batch_config,
     carve_sphere,
+    make_overlap,
     CONFIGS,
 )

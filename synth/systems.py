@@ -399,3 +399,43 @@ def make_batch_config(n_systems: int = 24, lo: int = 300, hi: int = 8000, b: int
             out.append(make_cluster(int(sizes[s]), opa=8, b=b, cutoff=10.0, seed=1000 + s,
                                     dirs=dirs, name=f"batch{s}-cluster"))
     return out
+
+
+# --------------------------------------------------------------------------
+# non-orthogonal basis: an overlap matrix for a system
+# --------------------------------------------------------------------------
+
+OVL_SCALE = 0.04            # overlap between orbitals of neighbouring atoms
+OVL_DECAY = 2.0             # bohr
+
+
+def make_overlap(sys_: System, seed_offset: int = 7777) -> Bsr:
+    """A synthetic overlap matrix S for the atoms of `sys_`, in its block layout:
+    identity inside every atom, and for every pair of atoms closer than the
+    system's cutoff a block of iid N(0,1) * OVL_SCALE * exp(-r / OVL_DECAY)
+    (S[J,I] = S[I,J]^T).  Drawn from default_rng(seed + seed_offset), pairs in
+    lexicographic order, so the system's own matrices do not change.  S is
+    checked positive definite through a Gershgorin lower bound > 0.1."""
+    rng = np.random.default_rng(sys_.seed + seed_offset)
+    coords, opa, n_atoms = sys_.coords, sys_.opa, sys_.coords.shape[0]
+    pairs = cKDTree(coords).query_pairs(sys_.cutoff, output_type="ndarray")
+    if pairs.size == 0:
+        pairs = np.zeros((0, 2), dtype=np.int64)
+    pairs = pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))].astype(np.int64)
+    r = np.linalg.norm(coords[pairs[:, 0]] - coords[pairs[:, 1]], axis=1)
+    blk = rng.standard_normal((pairs.shape[0], opa, opa)) * (OVL_SCALE * np.exp(-r / OVL_DECAY))[:, None, None]
+    eye = np.broadcast_to(np.eye(opa), (n_atoms, opa, opa)).copy()
+    ai = np.concatenate([np.arange(n_atoms), pairs[:, 0], pairs[:, 1]])
+    aj = np.concatenate([np.arange(n_atoms), pairs[:, 1], pairs[:, 0]])
+    s = _atom_blocks_to_bsr(ai, aj, np.concatenate([eye, blk, np.transpose(blk, (0, 2, 1))]), n_atoms, opa,
+                            sys_.b)
+    # Gershgorin: 1 - sum of the off-diagonal magnitudes in every row
+    rows = np.zeros(sys_.n)
+    for t in range(pairs.shape[0]):
+        I, J = pairs[t]
+        a = np.abs(blk[t])
+        rows[I * opa:(I + 1) * opa] += a.sum(axis=1)
+        rows[J * opa:(J + 1) * opa] += a.sum(axis=0)
+    if rows.size and 1.0 - rows.max() <= 0.1:
+        raise ValueError("synthetic overlap not safely positive definite")
+    return s

@@ -391,3 +391,71 @@ def test_golden_values_reproduce():
         _, p1s, _, _ = exact_response(h0, h1s, s.n_occ)
         a = polarizability(p1s, h1s)
         assert np.allclose(a, np.array(case["alpha"]), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# non-orthogonal basis (Sec. 2.2): the Loewdin oracle against the generalized
+# eigenproblem solved directly, finite differences and S-metric invariants
+# ---------------------------------------------------------------------------
+
+def _nonorth_case():
+    from synth import make_overlap
+    s_ = make_cluster(40, opa=8, b=32, cutoff=10.0, seed=12, dirs=("x", "y"))
+    return s_, s_.h0.to_dense(), [m.to_dense() for m in s_.h1], make_overlap(s_).to_dense()
+
+
+def _generalized(h0, s, n_occ):
+    import scipy.linalg
+    eps, c = scipy.linalg.eigh(h0, s)          # C^T S C = I
+    return eps, c, c[:, :n_occ] @ c[:, :n_occ].T
+
+
+def test_lowdin_reduces_to_the_orthogonal_oracle_for_identity_overlap():
+    from oracle import lowdin_response
+    s_ = chain_sys(10)
+    h0, h1s = s_.h0.to_dense(), [m.to_dense() for m in s_.h1]
+    p0, p1s, z = lowdin_response(h0, h1s, np.eye(h0.shape[0]), s_.n_occ)
+    q0, q1s, _, _ = exact_response(h0, h1s, s_.n_occ)
+    assert np.allclose(z, np.eye(h0.shape[0]), atol=1e-14)
+    assert rel_frobenius(p0, q0) < 1e-13
+    assert max(rel_frobenius(a, b) for a, b in zip(p1s, q1s)) < 1e-12
+
+
+def test_lowdin_p0_equals_the_generalized_eigenproblem_projector():
+    from oracle import lowdin_response
+    s_, h0, h1s, s = _nonorth_case()
+    p0, p1s, z = lowdin_response(h0, h1s, s, s_.n_occ)
+    eps, c, pg = _generalized(h0, s, s_.n_occ)
+    assert rel_frobenius(p0, pg) < 1e-11
+    # S-metric projector: P S P = P, Tr(P S) = N_occ
+    assert rel_frobenius(p0 @ s @ p0, p0) < 1e-11
+    assert abs(np.trace(p0 @ s) - s_.n_occ) < 1e-9
+    # Z really is S^(-1/2)
+    assert rel_frobenius(z @ s @ z, np.eye(s.shape[0])) < 1e-13
+
+
+def test_lowdin_p1_and_alpha_match_generalized_sum_over_states_and_finite_differences():
+    from oracle import lowdin_response, polarizability
+    s_, h0, h1s, s = _nonorth_case()
+    p0, p1s, _ = lowdin_response(h0, h1s, s, s_.n_occ)
+    eps, c, _ = _generalized(h0, s, s_.n_occ)
+    n_occ = s_.n_occ
+    co, cv = c[:, :n_occ], c[:, n_occ:]
+    for h1, p1 in zip(h1s, p1s):
+        v = cv.T @ h1 @ co                                   # V_ai in the S-orthonormal eigenbasis
+        u = v / (eps[:n_occ][None, :] - eps[n_occ:][:, None])
+        t = cv @ u @ co.T
+        assert rel_frobenius(p1, t + t.T) < 1e-10
+        # central finite difference of the generalized projector (S fixed)
+        e = 1e-4 / np.max(np.abs(h1))
+        fd = (_generalized(h0 + e * h1, s, n_occ)[2] - _generalized(h0 - e * h1, s, n_occ)[2]) / (2 * e)
+        assert rel_frobenius(p1, fd) < 1e-6
+        # S-metric response invariant: P1 = P0 S P1 + P1 S P0, and Tr(P1 S) = 0
+        assert rel_frobenius(p0 @ s @ p1 + p1 @ s @ p0, p1) < 1e-9
+        assert abs(np.trace(p1 @ s)) < 1e-9 * np.max(np.abs(p1)) * s.shape[0]
+    # alpha: Tr(P1 H1) is the same in both bases, and equals 4 sum V^2 / (e_a - e_i)
+    a = polarizability(p1s, h1s)
+    vs = [cv.T @ h1 @ co for h1 in h1s]
+    d = eps[n_occ:][:, None] - eps[:n_occ][None, :]
+    a2 = np.array([[4.0 * np.sum(vg * vd / d) for vd in vs] for vg in vs])
+    assert np.allclose(a, a2, rtol=1e-10, atol=0)
