@@ -63,14 +63,17 @@ extern "C" {
 #define RDM_MODE_FP32        1   /* every product in FP32 (CUDA cores), FP64 scalars */
 #define RDM_MODE_MIXED_BF16  2   /* bf16 hi+lo split products on the tensor cores
                                     (tcgen05, FP32 accumulate) until the idempotency
-                                    error stalls, then a final tier on the CUDA cores:
-                                    X0^2 in FP64, the first-order products in FP64
-                                    (refine_x0 / refine_x1 choose otherwise) */
+                                    error stalls, then a final tier: X0^2 FP64-class
+                                    (RDM_REFINE_SLICES for 32 x 32 blocks, else FP64),
+                                    the first-order products in FP64 (refine_x0 /
+                                    refine_x1 choose otherwise) */
 #define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
                                     by a power of two into fp16's normal range
                                     (22-bit products instead of 16-bit); final tier:
-                                    X0^2 in double-FP32 (FP64-class) on the CUDA
-                                    cores, first-order products still split */
+                                    X0^2 as exact bf16 slice products on the tensor
+                                    cores (FP64-class, RDM_REFINE_SLICES; FP64 on the
+                                    CUDA cores for blocks other than 32 x 32),
+                                    first-order products still split */
 
 /* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
 #define RDM_REFINE_DEFAULT   0   /* refine_x1: the split product for RDM_MODE_MIXED_FP16, FP64 for
@@ -135,8 +138,8 @@ typedef struct {
                                one super-row per group).  0: automatic, from the free device
                                memory.  Results do not depend on the grouping. */
     int32_t refine_x0;      /* mixed modes, final tier, arithmetic of X0^2: RDM_REFINE_DEFAULT
-                               (RDM_REFINE_FP32X2 for RDM_MODE_MIXED_FP16 with 32 x 32 blocks,
-                               otherwise RDM_REFINE_FP64), RDM_REFINE_FP64, RDM_REFINE_FP32X2
+                               (RDM_REFINE_SLICES with 32 x 32 blocks, otherwise
+                               RDM_REFINE_FP64), RDM_REFINE_FP64, RDM_REFINE_FP32X2
                                (32 x 32 blocks only), or RDM_REFINE_FP32 (the final tier then ends
                                on the FP32 idempotency stall) */
     int32_t stall_window;   /* mixed modes: the idempotency error e "stalls" when |e_n| >= |e_{n-w}| / 2
@@ -146,9 +149,11 @@ typedef struct {
                                re-blocks every system (the same matrices in b' x b' blocks; the
                                filter then acts on b' x b' blocks) and the getters return P0 and P1
                                in the uploaded layout.  Ignored while autotune is on. */
-    int32_t autotune;       /* 1: the first solve after an upload times one probe solve at each block
+    int32_t autotune;       /* 1: the first solve of a problem shape (number of systems, b, block rows
+                               and H0 blocks of every system) times one probe solve at each block
                                size in {16, 32, 64} and keeps the fastest for this and later solves
-                               (rdm_info.block_size, probe_ms); 0: off */
+                               of that shape, whatever values are uploaded (rdm_info.block_size,
+                               probe_ms); setting parameters forgets the choice; 0: off */
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -185,6 +190,8 @@ typedef struct {
     int32_t block_size;        /* block size the products ran at (rdm_params.block_size / autotune) */
     double  autotune_ms;       /* wall time of the autotuner's probe solves (0 when it did not run) */
     double  probe_ms[3];       /* device time of the probe solve at b = 16, 32, 64 (0: not probed) */
+    int32_t lowdin_iterations; /* Newton-Schulz iterations for S^(-1/2) (0: orthogonal basis) */
+    int32_t pad1;
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */
@@ -234,29 +241,61 @@ int rdm_batch_create(rdm_handle *h, int n_systems);
 int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons);
 
 /* Upload H1 for direction dir (0 = x, 1 = y, 2 = z) of system sys: the
- * matrix dH/dlambda (for a field this is the dipole matrix D_dir; the field
- * term -r.E enters through the sign convention of alpha).  Same checks as
- * H0 (the diagonal need not be present); same nb, b, n as H0. */
+ * matrix dH/dlambda of the first-order perturbation (Sec. 2.1, the H^(1) of
+ * Eq. CPSCF-U; for a homogeneous field this is the dipole matrix D_dir, the
+ * field term -r.E of Sec. 2 entering through the sign convention of alpha).
+ * Same checks as H0 (the diagonal need not be present); same nb, b, n as H0. */
 int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1);
+
+/* Upload the overlap matrix S of system sys for a NON-ORTHOGONAL basis
+ * (Sec. 2.2: H C = S C E).  The solve then forms S^(-1/2) by the coupled
+ * Newton-Schulz iteration (with the same block products and filter as the
+ * purification), transforms H0 and every H1 to the orthogonal form
+ * S^(-1/2) H S^(-1/2), runs the solve there and transforms P0 and P1 back
+ * (P = S^(-1/2) P_orth S^(-1/2)); alpha is basis independent.  rdm_get_p0 /
+ * rdm_get_p1 return the non-orthogonal-basis matrices (Tr(P0 S) = N_occ);
+ * rdm_info's trace and idempotency are those of the orthogonal form.  S must
+ * be symmetric positive definite with the pattern rules of H0 (diagonal blocks
+ * present, padding zero) and the same nb, b, n; upload it for every system of
+ * a batch or for none (RDM_EINVAL at the solve otherwise).  A perturbation
+ * that changes S (atomic displacements) is out of scope: H1 is a field term. */
+int rdm_upload_s(rdm_handle *h, int sys, const rdm_bsr *S);
 
 /* ---- solve -------------------------------------------------------------- */
 
 /* Run the coupled TC2 / first-order recursion for every uploaded system and
- * direction, then the polarizability.  Blocks until done.  *info (may be
- * NULL) receives the summary of system 0.  Returns RDM_OK, the warning
- * RDM_NOT_CONVERGED, or an error (RDM_ECAPACITY, RDM_ECUDA, RDM_ENOMEM,
- * RDM_ETIMEOUT). */
+ * direction (Sec. 2.2: X0_0, X1_0 from the Gershgorin bounds; Eq. TC2 for X0
+ * and Eq. TC2-CPSCF for every X1 in the branch the trace test of Eq. TC2
+ * picks; the filter of Sec. 2.3 after every product; stop on the band-energy
+ * change, the "tolerance" of Sec. 2.3), then the polarizability (Eq. polar).
+ * Blocks until done.  *info (may be NULL) receives the summary of system 0.
+ * Returns RDM_OK, the warning RDM_NOT_CONVERGED, or an error (RDM_ECAPACITY,
+ * RDM_ECUDA, RDM_ENOMEM, RDM_ETIMEOUT). */
 int rdm_solve(rdm_handle *h, rdm_info *info);
 
-/* Test hook: force the branch of iteration n to seq[n] (1 = X^2,
+/* The same solve, asynchronous: it runs on a host thread of the library that
+ * drives the handle's stream, and the call returns at once (RDM_OK, or
+ * RDM_ESTATE when nothing is uploaded).  rdm_sync waits for it and returns its
+ * status (as rdm_solve would) with *info (may be NULL) for system 0;
+ * RDM_ESTATE if no solve is in flight.  Every other call on the handle waits
+ * for a solve in flight first, so results are never read half-written. */
+int rdm_solve_async(rdm_handle *h);
+int rdm_sync(rdm_handle *h, rdm_info *info);
+
+/* Test hook: force the branch of Eq. TC2 at iteration n to seq[n] (1 = X^2,
  * 2 = 2X - X^2) for n < len; len = 0 clears it.  Applies to every system. */
 int rdm_force_branches(rdm_handle *h, const uint8_t *seq, int len);
 
 /* ---- results ------------------------------------------------------------ */
 
+/* Summary of system sys of the last solve (iterations, branch tiers, the
+ * Gershgorin bounds of Sec. 2.2, Tr P0 - N_occ and the idempotency error of
+ * Eq. TC2's fixed point, the band energy Tr(P0 H0) of the Sec. 2.3 stopping
+ * rule, block counts, timings).  RDM_ESTATE before a solve. */
 int rdm_get_info(rdm_handle *h, int sys, rdm_info *info);
 
-/* Number of stored blocks of P0 (resp. P1_dir) of system sys. */
+/* Number of stored blocks of P0 = lim X0_n (Eq. TC2) (resp. P1_dir = lim X1_n,
+ * Eq. TC2-CPSCF) of system sys, in the uploaded block layout. */
 int rdm_get_p0_nnzb(rdm_handle *h, int sys, int64_t *nnzb);
 int rdm_get_p1_nnzb(rdm_handle *h, int sys, int dir, int64_t *nnzb);
 
@@ -272,7 +311,9 @@ int rdm_get_p1(rdm_handle *h, int sys, int dir, rdm_bsr_out *out);
  * entries of directions that were not uploaded are NaN. */
 int rdm_get_alpha(rdm_handle *h, int sys, double alpha[9]);
 
-/* Copy up to cap per-iteration records of the last solve; *n gets the count. */
+/* Copy up to cap per-iteration records of the last solve (branch of Eq. TC2,
+ * tier, Tr X0_n, idempotency error, the band energies of the Sec. 2.3
+ * stopping rule, block counts); *n gets the count. */
 int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n);
 
 /* ---- single-product primitive (kernel-level testing and benchmarking) ---- */

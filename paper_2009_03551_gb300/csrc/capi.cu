@@ -38,6 +38,8 @@ struct SysMats {
     DevBuf<double> val;
     std::vector<int> rp1[3], col1[3];  // H1_dir
     DevBuf<double> val1[3];
+    std::vector<int> rps, cols;        // S (non-orthogonal basis)
+    DevBuf<double> vals;
 };
 
 struct HostSys {
@@ -49,6 +51,9 @@ struct HostSys {
     bool has_h1[3] = {false, false, false};
     std::vector<int> rp1[3], col1[3];
     DevBuf<double> val1[3];
+    bool has_s = false;                // overlap matrix uploaded (non-orthogonal basis, Sec. 2.2)
+    std::vector<int> rps, cols;
+    DevBuf<double> vals;
     SysMats rb;                        // the same matrices at the solve's block size (when it differs)
 };
 
@@ -75,7 +80,8 @@ struct rdm_handle {
     int S = 1;
     int b = 0;                 // block size of the uploaded matrices
     int bs = 0;                // block size of the current solve (b, or the re-blocked size)
-    int tuned_b = 0;           // autotuner's choice for the uploaded problem (0: not tuned)
+    int tuned_b = 0;           // autotuner's choice (0: not tuned) ...
+    std::vector<int64_t> tuned_key;   // ... for problems of this shape: systems, b, block rows, blocks of H0
     double autotune_ms = 0, probe_ms[3] = {0, 0, 0};
     std::thread worker;        // rdm_solve_async
     bool pending = false;
@@ -89,6 +95,10 @@ struct rdm_handle {
     int dirs[3] = {0, 0, 0};
     std::vector<int> row0, nbs, norb;
     MatSet H0, H1;
+    MatSet Sm;                  // overlap matrices (non-orthogonal basis), when uploaded
+    bool has_s = false;
+    MatSet Zm, Lm;              // S^(-1/2) and S^(-1) of the last solve (Loewdin transform)
+    int lowdin_iters = 0;
     SysDev sd;
     MatSet X[2];
     int cur = 0;
@@ -291,9 +301,13 @@ void ensure_reblocked(rdm_handle *h, int s, int bs) {
     one(y.rp, y.col, y.val.p, r.rp, r.col, r.val);
     for (int d = 0; d < 3; ++d)
         if (y.has_h1[d]) one(y.rp1[d], y.col1[d], y.val1[d].p, r.rp1[d], r.col1[d], r.val1[d]);
+    if (y.has_s) one(y.rps, y.cols, y.vals.p, r.rps, r.cols, r.vals);
     r.nb = (int)r.rp.size() - 1;
     r.b = bs;
 }
+
+void init_x(rdm_handle *h);
+void init_sys_scalars(rdm_handle *h);
 
 void assemble(rdm_handle *h) {
     const int S = h->S;
@@ -376,7 +390,24 @@ void assemble(rdm_handle *h) {
                   return (const double *)(rb ? h->hs[s].rb.val1[h->dirs[m]].p : h->hs[s].val1[h->dirs[m]].p);
               });
     }
-    // X0 has the pattern of H0, X1_g that of H1_g
+    h->has_s = false;
+    int ns = 0;
+    for (int s2 = 0; s2 < S; ++s2) ns += h->hs[s2].has_s ? 1 : 0;
+    if (ns && ns != S) throw Error{RDM_EINVAL, "upload an overlap matrix for every system of the batch or for none"};
+    if (ns) {
+        h->has_s = true;
+        build(h->Sm, 1, [&](int s2, int) -> const std::vector<int> & { return rb ? h->hs[s2].rb.rps : h->hs[s2].rps; },
+              [&](int s2, int) -> const std::vector<int> & { return rb ? h->hs[s2].rb.cols : h->hs[s2].cols; },
+              [&](int s2, int) { return (const double *)(rb ? h->hs[s2].rb.vals.p : h->hs[s2].vals.p); });
+    }
+    init_sys_scalars(h);
+    init_x(h);
+}
+
+// X0 has the pattern of H0, X1_g that of H1_g
+void init_x(rdm_handle *h) {
+    const int NB = h->NB, nd = h->nd, b = h->bs;
+    const size_t bb = (size_t)b * b;
     MatSet &X = h->X[0];
     h->cur = 0;
     X.nmat = 1 + nd;
@@ -411,7 +442,11 @@ void assemble(rdm_handle *h) {
     if (nd)
         RDM_CUDA_TRY(cudaMemcpyAsync(X.col.p + h->H0.total, h->H1.col.p, h->H1.total * sizeof(int),
                                      cudaMemcpyDeviceToDevice, h->stream));
-    // per-system device scalars
+}
+
+// per-system device scalars
+void init_sys_scalars(rdm_handle *h) {
+    const int S = h->S, NB = h->NB;
     SysDev &sd = h->sd;
     sd.row0.ensure(S); sd.nbs.ensure(S); sd.n_orb.ensure(S);
     sd.emin.ensure(S); sd.emax.ensure(S); sd.c_lin.ensure(S); sd.c_sq.ensure(S);
@@ -449,29 +484,31 @@ bool tc_block_ok(int mode, int b) {
 }
 
 // Arithmetic of every job (job 0 = X0^2, jobs 1.. = X1 products) for a tier.
-// Mixed modes: tier 0 runs every product as a split product on the tensor
-// cores.  In the final tier the purification X0^2 is refined on the CUDA
-// cores (`refine_x0`): by default in double-FP32 (FP64-class, ~46 bits, on
-// the FP32 pipe) for the fp16 mode and in FP64 for the bf16 mode; the
-// first-order products use `refine_x1`: by default they stay split products
-// on the tensor cores for the fp16 mode (with the segmented accumulation of
-// the tensor-core kernel they are as accurate as FP32 CUDA-core products
-// there) and FP64 for the bf16 mode.
-// The double-FP32 kernel takes 32 x 32 blocks only: with other block sizes the
-// fp16 mode's default X0^2 refinement is FP64.
+// The fp16 ladder has two tiers: every product as a scaled fp16 split product
+// on the tensor cores (22 bits), then the final tier, where X0^2 is refined
+// (`refine_x0`; by default as exact bf16 slice products on the tensor cores,
+// FP64-class) and the first-order products use `refine_x1` (by default they
+// stay split: with the segmented accumulation of the tensor-core kernel they
+// are as accurate as FP32 CUDA-core products).  The bf16 ladder: bf16 split
+// products (16 bits), then the final tier (X0^2 as for fp16, the first-order
+// products in FP64 by default).  A three-tier bf16 ladder with an FP32 tier
+// between (X1 in FP32 on the CUDA cores through both later tiers) was measured
+// and left 2e-6 in alpha on a 90-atom cluster where this one leaves 1e-6.
+int final_tier_of(int mode) { return mode == RDM_MODE_MIXED_BF16 || mode == RDM_MODE_MIXED_FP16 ? 1 : 0; }
+
 void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0, int b = 32) {
-    if (refine_x1 == RDM_REFINE_DEFAULT)
-        refine_x1 = mode == RDM_MODE_MIXED_FP16 ? RDM_REFINE_SPLIT : RDM_REFINE_FP64;
-    if (refine_x0 == RDM_REFINE_DEFAULT)
-        refine_x0 = mode == RDM_MODE_MIXED_FP16 && b == 32 ? RDM_REFINE_FP32X2 : RDM_REFINE_FP64;
+    const bool bf16 = mode == RDM_MODE_MIXED_BF16;
+    if (refine_x1 == RDM_REFINE_DEFAULT) refine_x1 = bf16 ? RDM_REFINE_FP64 : RDM_REFINE_SPLIT;
+    if (refine_x0 == RDM_REFINE_DEFAULT) refine_x0 = b == 32 ? RDM_REFINE_SLICES : RDM_REFINE_FP64;
+    const int final_tier = final_tier_of(mode);
     for (int p = 0; p < njob; ++p) {
-        Arith split = mode == RDM_MODE_MIXED_BF16 ? AR_BF16X3 : AR_FP16X3;
+        const Arith split = bf16 ? AR_BF16X3 : AR_FP16X3;
         switch (mode) {
             case RDM_MODE_FP64: ar[p] = AR_FP64; break;
             case RDM_MODE_FP32: ar[p] = AR_FP32; break;
             case RDM_MODE_MIXED_BF16:
             case RDM_MODE_MIXED_FP16:
-                if (tier == 0) ar[p] = split;
+                if (tier == 0 || tier < final_tier) ar[p] = split;
                 else if (p == 0) ar[p] = refine_x0 == RDM_REFINE_FP32 ? AR_FP32
                                         : refine_x0 == RDM_REFINE_FP32X2 ? AR_FF
                                         : refine_x0 == RDM_REFINE_SLICES ? AR_OZ : AR_FP64;
@@ -856,6 +893,217 @@ std::vector<double> stats(rdm_handle *h, MatSet &X) {
     return q;
 }
 
+// ---------------------------------------------------------------------------
+// non-orthogonal basis: the Loewdin transform of Sec. 2.2 with the block
+// products of the solve (FP64, truncated at tau)
+// ---------------------------------------------------------------------------
+
+// out = matrices [first, first + count) of each listed set, in that order
+struct SetRange {
+    const MatSet *m;
+    int first, count;
+};
+void concat(rdm_handle *h, std::initializer_list<SetRange> parts, MatSet &out) {
+    const int NB = h->NB, b = h->bs;
+    const size_t bb = (size_t)b * b;
+    int nmat = 0;
+    int64_t total = 0;
+    std::vector<std::vector<int>> rps;
+    for (const auto &r : parts) {
+        std::vector<int> rp((size_t)r.m->nmat * NB + 1);
+        d2h(rp.data(), r.m->row_ptr.p, rp.size(), h->stream);
+        rps.push_back(std::move(rp));
+        nmat += r.count;
+    }
+    sync(h);
+    std::vector<int> rp((size_t)nmat * NB + 1);
+    out.nmat = nmat;
+    out.NB = NB;
+    out.b = b;
+    out.nnzb.assign(nmat, 0);
+    int m = 0;
+    for (size_t k = 0; k < parts.size(); ++k) {
+        const SetRange &r = *(parts.begin() + k);
+        for (int q = r.first; q < r.first + r.count; ++q, ++m) {
+            const int a0 = rps[k][(size_t)q * NB];
+            for (int i = 0; i < NB; ++i) rp[(size_t)m * NB + i] = (int)(total + rps[k][(size_t)q * NB + i] - a0);
+            out.nnzb[m] = rps[k][(size_t)(q + 1) * NB] - a0;
+            total += out.nnzb[m];
+        }
+    }
+    rp[(size_t)nmat * NB] = (int)total;
+    out.total = total;
+    out.row_ptr.ensure(rp.size());
+    out.col.ensure(std::max<int64_t>(total, 1));
+    out.val.ensure((size_t)std::max<int64_t>(total, 1) * bb);
+    out.nrm.ensure(std::max<int64_t>(total, 1));
+    h2d(out.row_ptr.p, rp.data(), rp.size(), h->stream);
+    int64_t off = 0;
+    for (size_t k = 0; k < parts.size(); ++k) {
+        const SetRange &r = *(parts.begin() + k);
+        const int64_t a0 = rps[k][(size_t)r.first * NB], a1 = rps[k][(size_t)(r.first + r.count) * NB];
+        if (a1 > a0) {
+            RDM_CUDA_TRY(cudaMemcpyAsync(out.col.p + off, r.m->col.p + a0, (a1 - a0) * sizeof(int),
+                                         cudaMemcpyDeviceToDevice, h->stream));
+            RDM_CUDA_TRY(cudaMemcpyAsync(out.val.p + off * bb, r.m->val.p + a0 * bb, (a1 - a0) * bb * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, h->stream));
+        }
+        off += a1 - a0;
+    }
+    launch_block_norms(out.val.p, out.nrm.p, total, b, h->stream);
+}
+
+// every job of jt, C = c_lin X + c_sq (A B [+ B A]), in FP64 for every system
+void fp64_products(rdm_handle *h, MatSet &in, const JobTable &jt, double c_lin, double c_sq, double tau,
+                   MatSet &out) {
+    const int S = h->S;
+    std::vector<double> cl(S, c_lin), cq(S, c_sq), t(S, tau);
+    std::vector<int> one(S, 1), zero(S, 0);
+    h2d(h->sd.c_lin.p, cl.data(), S, h->stream);
+    h2d(h->sd.c_sq.p, cq.data(), S, h->stream);
+    h2d(h->sd.tau0.p, t.data(), S, h->stream);
+    h2d(h->sd.tau1.p, t.data(), S, h->stream);
+    h2d(h->sd.active.p, one.data(), S, h->stream);
+    h2d(h->sd.tier.p, zero.data(), S, h->stream);
+    Arith tab[kMaxTiers][kMaxJobs];
+    for (int p = 0; p < kMaxJobs; ++p) tab[0][p] = AR_FP64;
+    multiply(h, in, out, jt, tab, 1u);
+}
+
+// Job: out p = c_lin X_x + c_sq (A B + B A), or A A (a == b, one term)
+Job sym_job(int out, int x, int a, int b) { return a == b ? Job{out, x, 1, {a, a}, {a, a}, 0} : Job{out, x, 2, {a, b}, {b, a}, 0}; }
+
+// M -> Z M Z for the k matrices of `ms` (Z = S^(-1/2), L = Z^2 = S^(-1)), with
+// products of symmetric matrices only:  Z M Z = (Z K + K Z)/2 - (L M + M L)/2,
+// K = Z M + M Z.
+void lowdin_apply(rdm_handle *h, MatSet &ms, MatSet &out, double tau) {
+    const int k = ms.nmat;
+    MatSet in, K, M1;
+    JobTable jt{};
+    jt.njob = k;
+    concat(h, {{&h->Zm, 0, 1}, {&ms, 0, k}}, in);
+    for (int m = 0; m < k; ++m) jt.job[m] = sym_job(m, -1, 0, 1 + m);
+    fp64_products(h, in, jt, 0.0, 1.0, tau, K);
+    concat(h, {{&h->Zm, 0, 1}, {&K, 0, k}}, in);
+    fp64_products(h, in, jt, 0.0, 1.0, tau, M1);
+    K.release();
+    concat(h, {{&M1, 0, k}, {&h->Lm, 0, 1}, {&ms, 0, k}}, in);
+    for (int m = 0; m < k; ++m) jt.job[m] = sym_job(m, m, k, k + 1 + m);
+    fp64_products(h, in, jt, 0.5, -0.5, tau, out);
+}
+
+// Z = S^(-1/2) by the coupled Newton-Schulz iteration (Higham): Y_0 = S / c,
+// Z_0 = I with c a Gershgorin bound of every S; T = (3 I - Z Y) / 2,
+// Y <- Y T, Z <- T Z until ||T - I||_F stops shrinking below 1e-6 sqrt(n) or
+// drops below 1e-13 sqrt(n); then Z / sqrt(c).  Z and Y are polynomials in
+// S, so every product is one of commuting symmetric matrices (taken as
+// (A B + B A) / 2).  Then H0 and H1 are transformed in place.
+void lowdin_forward(rdm_handle *h) {
+    const int S = h->S, NB = h->NB, b = h->bs, nd = h->nd;
+    const double tau = h->prm.tau;
+    cudaStream_t st = h->stream;
+    // c: Gershgorin upper bound of each system's S
+    h->row_lo.ensure(NB);
+    h->row_hi.ensure(NB);
+    launch_gershgorin(h->Sm.row_ptr.p, h->Sm.col.p, h->Sm.val.p, NB, b, h->sd.sys_of_row.p, h->sd.row0.p,
+                      h->sd.n_orb.p, h->row_lo.p, h->row_hi.p, st);
+    launch_sys_minmax(h->row_lo.p, h->row_hi.p, h->sd.row0.p, h->sd.nbs.p, S, h->sd.emin.p, h->sd.emax.p, st);
+    std::vector<double> lo(S), hi(S);
+    d2h(lo.data(), h->sd.emin.p, S, st);
+    d2h(hi.data(), h->sd.emax.p, S, st);
+    sync(h);
+    std::vector<double> inv_c(S), inv_sqrt_c(S);
+    for (int s = 0; s < S; ++s) {
+        if (!(hi[s] > 0)) throw Error{RDM_EBADBSR, "overlap matrix has no positive Gershgorin bound"};
+        inv_c[s] = 1.0 / hi[s];
+        inv_sqrt_c[s] = 1.0 / std::sqrt(hi[s]);
+    }
+    DevBuf<double> fac;
+    fac.ensure(S);
+    h2d(fac.p, inv_c.data(), S, st);
+    MatSet Y, Z, I, T, in, YZ;
+    concat(h, {{&h->Sm, 0, 1}}, Y);
+    launch_scale_sys(Y.row_ptr.p, Y.col.p, Y.val.p, NB, b, h->sd.sys_of_row.p, h->sd.row0.p, h->sd.n_orb.p, fac.p, 1,
+                     Y.val.p, st);
+    launch_block_norms(Y.val.p, Y.nrm.p, Y.total, b, st);
+    {   // identity: diagonal blocks only
+        std::vector<int> rp(NB + 1), col(NB);
+        for (int i = 0; i <= NB; ++i) rp[i] = i;
+        for (int i = 0; i < NB; ++i) col[i] = i;
+        I.nmat = 1; I.NB = NB; I.b = b; I.total = NB; I.nnzb.assign(1, NB);
+        I.row_ptr.ensure(NB + 1); I.col.ensure(std::max(NB, 1)); I.val.ensure((size_t)std::max(NB, 1) * b * b);
+        I.nrm.ensure(std::max(NB, 1));
+        h2d(I.row_ptr.p, rp.data(), rp.size(), st);
+        h2d(I.col.p, col.data(), col.size(), st);
+        launch_identity_blocks(I.val.p, NB, b, st);
+        launch_block_norms(I.val.p, I.nrm.p, NB, b, st);
+    }
+    concat(h, {{&I, 0, 1}}, Z);
+    JobTable jt{};
+    double prev = 1e300;
+    int it = 0;
+    const int nq = 3;     // Tr T, ||T||^2, Tr(T T) from the stats of a one-matrix set
+    for (it = 0; it < 100; ++it) {
+        concat(h, {{&Z, 0, 1}, {&Y, 0, 1}, {&I, 0, 1}}, in);
+        jt.njob = 1;
+        jt.job[0] = sym_job(0, 2, 0, 1);
+        fp64_products(h, in, jt, 1.5, -0.25, tau, T);       // T = 3/2 I - (Z Y + Y Z)/4
+        // ||T - I||_F^2 = ||T||^2 - 2 Tr T + n per system (padding rows included)
+        h->row_part.ensure((size_t)nq * NB);
+        h->sys_q.ensure((size_t)nq * S);
+        launch_row_stats(T.row_ptr.p, T.col.p, T.val.p, 1, NB, b, T.row_ptr.p, T.col.p, T.val.p, h->row_part.p, st);
+        launch_sys_sum(h->row_part.p, nq, NB, h->sd.row0.p, h->sd.nbs.p, S, h->sys_q.p, st);
+        std::vector<double> q((size_t)nq * S);
+        d2h(q.data(), h->sys_q.p, q.size(), st);
+        sync(h);
+        double dev = 0;
+        for (int s = 0; s < S; ++s) {
+            const double n = (double)h->nbs[s] * b;
+            const double d2 = q[(size_t)s * nq + 1] - 2.0 * q[(size_t)s * nq] + n;
+            dev = std::max(dev, std::sqrt(std::max(d2, 0.0)) / std::sqrt(n));
+        }
+        concat(h, {{&Y, 0, 1}, {&T, 0, 1}, {&Z, 0, 1}}, in);
+        jt.njob = 2;
+        jt.job[0] = sym_job(0, -1, 0, 1);                    // Y T
+        jt.job[1] = sym_job(1, -1, 1, 2);                    // T Z
+        fp64_products(h, in, jt, 0.0, 0.5, tau, YZ);
+        concat(h, {{&YZ, 0, 1}}, Y);
+        concat(h, {{&YZ, 1, 1}}, Z);
+        if (dev < 1e-13 || (dev < 1e-6 && dev >= 0.5 * prev)) break;
+        if (!std::isfinite(dev) || (it > 20 && dev > 1.0))
+            throw Error{RDM_EBADBSR, "the Newton-Schulz iteration for S^(-1/2) does not converge (is S positive definite?)"};
+        prev = dev;
+    }
+    h->lowdin_iters = it + 1;
+    h2d(fac.p, inv_sqrt_c.data(), S, st);
+    concat(h, {{&Z, 0, 1}}, h->Zm);
+    launch_scale_sys(h->Zm.row_ptr.p, h->Zm.col.p, h->Zm.val.p, NB, b, h->sd.sys_of_row.p, h->sd.row0.p,
+                     h->sd.n_orb.p, fac.p, 0, h->Zm.val.p, st);
+    launch_block_norms(h->Zm.val.p, h->Zm.nrm.p, h->Zm.total, b, st);
+    Y.release(); Z.release(); T.release(); YZ.release(); I.release();
+    concat(h, {{&h->Zm, 0, 1}}, in);
+    jt.njob = 1;
+    jt.job[0] = sym_job(0, -1, 0, 0);
+    fp64_products(h, in, jt, 0.0, 1.0, tau, h->Lm);       // L = Z Z = S^-1
+    // H0 and every H1 in the orthogonal form
+    MatSet hs, ho;
+    if (nd) concat(h, {{&h->H0, 0, 1}, {&h->H1, 0, nd}}, hs);
+    else concat(h, {{&h->H0, 0, 1}}, hs);
+    lowdin_apply(h, hs, ho, tau);
+    concat(h, {{&ho, 0, 1}}, h->H0);
+    if (nd) concat(h, {{&ho, 1, nd}}, h->H1);
+}
+
+// P -> Z P Z for the solve's result set (P0 and every P1)
+void lowdin_back(rdm_handle *h) {
+    MatSet &X = h->X[h->cur];
+    MatSet xs, out;
+    concat(h, {{&X, 0, X.nmat}}, xs);
+    lowdin_apply(h, xs, out, h->prm.tau);
+    X.release();
+    concat(h, {{&out, 0, out.nmat}}, X);
+}
+
 int run_solve(rdm_handle *h, rdm_info *info_out) {
     DeviceGuard dg(h->device);
     if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
@@ -864,12 +1112,16 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_kernel_launches;
     assemble(h);
+    if (h->has_s) {
+        lowdin_forward(h);   // H0, H1 to the orthogonal form (Sec. 2.2)
+        init_x(h);
+    }
     const int S = h->S, NB = h->NB, nd = h->nd, b = h->bs;
     const rdm_params &P = h->prm;
     cudaStream_t st = h->stream;
     const bool mixed = P.mode == RDM_MODE_MIXED_BF16 || P.mode == RDM_MODE_MIXED_FP16;
     const bool lowprec = P.mode != RDM_MODE_FP64;
-    const int final_tier = mixed ? 1 : 0;
+    const int final_tier = final_tier_of(P.mode);
 
     // Gershgorin bounds and the initial matrices
     h->row_lo.ensure(NB);
@@ -982,7 +1234,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
                 continue;
             }
             // tier switch on idempotency stall (mixed modes)
-            if (mixed && y.tier < final_tier && stalled) {
+            // a stall moves a system to the next tier (after at least W
+            // iterations in a tier above the first, so that the stall is its own)
+            if (mixed && y.tier < final_tier && stalled && (y.tier == 0 || n - y.tier_start >= W)) {
                 y.tier++;
                 y.tier_start = n;
             }
@@ -1159,6 +1413,23 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         h->info[s].trace_error = q[(size_t)s * nq] - nocc[s];
         h->info[s].idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
     }
+    if (h->has_s) {
+        // P0 and P1 back to the non-orthogonal basis; the summary above stays
+        // that of the orthogonal form (Tr P0 = N_occ there)
+        lowdin_back(h);
+        MatSet &Xb = h->X[h->cur];
+        h->final_rp.resize((size_t)Xb.nmat * NB + 1);
+        d2h(h->final_rp.data(), Xb.row_ptr.p, h->final_rp.size(), st);
+        sync(h);
+        for (int s = 0; s < S; ++s) {
+            const int r0 = h->row0[s], r1 = r0 + h->nbs[s];
+            h->info[s].nnzb_p0 = h->final_rp[r1] - h->final_rp[r0];
+            for (int d = 0; d < nd; ++d)
+                h->info[s].nnzb_p1[h->dirs[d]] =
+                    h->final_rp[(size_t)(1 + d) * NB + r1] - h->final_rp[(size_t)(1 + d) * NB + r0];
+            h->info[s].lowdin_iterations = h->lowdin_iters;
+        }
+    }
     h->conv.assign((size_t)S * 4, {});
     for (int s = 0; s < S; ++s) h->info[s].block_size = b;
     h->solved = true;
@@ -1205,6 +1476,14 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
     if (h->hs.empty() || !h->b) return fail(h, RDM_ESTATE, "no system uploaded");
     bool have_result = false;
     int status = RDM_OK;
+    // the autotuner's choice is kept for later uploads of the same shape
+    // (a size class: number of systems, block size, block rows, H0 blocks)
+    std::vector<int64_t> key{h->S, h->b};
+    for (const auto &y : h->hs) {
+        key.push_back(y.nb);
+        key.push_back((int64_t)y.col.size());
+    }
+    if (key != h->tuned_key) h->tuned_b = 0;
     if (P.autotune && !h->tuned_b) {
         const int cand[3] = {16, 32, 64};
         const auto t0 = std::chrono::steady_clock::now();
@@ -1237,6 +1516,7 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
         h->autotune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (!best_b) return fail(h, RDM_ENOMEM, "autotune: no block size in {16, 32, 64} fits the device");
         h->tuned_b = best_b;
+        h->tuned_key = key;
         have_result = last_b == best_b;   // the last probe already is the solve at the chosen size
     } else if (!P.autotune) {
         h->autotune_ms = 0;
@@ -1461,7 +1741,6 @@ int rdm_batch_create(rdm_handle *h, int n_systems) {
         h->hs.resize(n_systems);
         h->S = n_systems;
         h->b = 0;
-        h->tuned_b = 0;
         h->solved = false;
         return RDM_OK;
     });
@@ -1490,13 +1769,14 @@ int rdm_upload_h0(rdm_handle *h, int sys, const rdm_bsr *H0, int64_t n_electrons
         }
         y.has_h0 = true;
         y.rb = SysMats{};
-        h->tuned_b = 0;
         y.nb = H0->nb;
         y.n = H0->n;
         y.n_elec = n_electrons;
-        if (h->S == 1)
+        if (h->S == 1) {
             for (int d = 0; d < 3; ++d)
                 if (y.has_h1[d] && (int)y.rp1[d].size() != y.nb + 1) y.has_h1[d] = false;
+            if (y.has_s && (int)y.rps.size() != y.nb + 1) y.has_s = false;
+        }
         h->solved = false;
         return RDM_OK;
     });
@@ -1517,7 +1797,25 @@ int rdm_upload_h1(rdm_handle *h, int sys, int dir, const rdm_bsr *H1) {
         upload_matrix(h, H1, y.rp1[dir], y.col1[dir], y.val1[dir], false);
         y.has_h1[dir] = true;
         y.rb = SysMats{};
-        h->tuned_b = 0;
+        h->solved = false;
+        return RDM_OK;
+    });
+}
+
+int rdm_upload_s(rdm_handle *h, int sys, const rdm_bsr *S) {
+    if (!h) return RDM_EINVAL;
+    join_pending(h);
+    if (sys < 0 || sys >= h->S) return fail(h, RDM_EINVAL, "system index out of range");
+    return guarded(h, [&] {
+        DeviceGuard dg(h->device);
+        HostSys &y = h->hs[sys];
+        if (!y.has_h0) return fail(h, RDM_ESTATE, "upload H0 of the system before S");
+        if (!S) return fail(h, RDM_EINVAL, "null matrix");
+        if (S->nb != y.nb || S->n != y.n || S->b != h->b)
+            return fail(h, RDM_EINVAL, "S must have the same nb, b and n as H0");
+        upload_matrix(h, S, y.rps, y.cols, y.vals, true);
+        y.has_s = true;
+        y.rb = SysMats{};
         h->solved = false;
         return RDM_OK;
     });

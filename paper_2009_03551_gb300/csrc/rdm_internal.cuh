@@ -330,6 +330,13 @@ void launch_compact_count(const CompactArgs &c, int *cnt, cudaStream_t st);
 // output blocks [d0, d1) of the group
 void launch_compact_copy(const CompactArgs &c, int d1, cudaStream_t st);
 
+// k_lowdin.cu: out = fac[sys] * val for every block of the first NB block rows
+// (pad_one: the diagonal of padding rows set to 1), and identity blocks.
+void launch_scale_sys(const int *row_ptr, const int *col, const double *val, int NB, int b, const int *sys_of_row,
+                      const int *row0, const int *n_orb, const double *fac, int pad_one, double *out,
+                      cudaStream_t st);
+void launch_identity_blocks(double *val, int64_t nblk, int b, cudaStream_t st);
+
 // k_reblock.cu: the same matrix in b_out x b_out instead of b_in x b_in blocks.
 // Host pattern (rp/col of one matrix, local block indices; n orbitals): an
 // output block exists where a stored input block overlaps it.

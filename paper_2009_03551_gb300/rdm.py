@@ -43,7 +43,7 @@ EXPORTED = (
     "rdm_batch_create", "rdm_upload_h0", "rdm_upload_h1", "rdm_solve", "rdm_force_branches",
     "rdm_get_info", "rdm_get_p0_nnzb", "rdm_get_p1_nnzb", "rdm_get_p0", "rdm_get_p1",
     "rdm_get_alpha", "rdm_get_log", "rdm_block_product", "rdm_version", "rdm_bsr_dot_noalloc",
-    "rdm_set_test_knobs", "rdm_solve_async", "rdm_sync",
+    "rdm_set_test_knobs", "rdm_solve_async", "rdm_sync", "rdm_upload_s",
 )
 
 
@@ -77,7 +77,7 @@ class rdm_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("block_size", C.c_int32), ("autotune_ms", C.c_double),
-                ("probe_ms", C.c_double * 3)]
+                ("probe_ms", C.c_double * 3), ("lowdin_iterations", C.c_int32), ("pad1", C.c_int32)]
 
 
 class rdm_test_knobs(C.Structure):
@@ -106,6 +106,7 @@ def _load():
         "rdm_batch_create": (C.c_int, [H, C.c_int]),
         "rdm_upload_h0": (C.c_int, [H, C.c_int, C.POINTER(rdm_bsr), C.c_int64]),
         "rdm_upload_h1": (C.c_int, [H, C.c_int, C.c_int, C.POINTER(rdm_bsr)]),
+        "rdm_upload_s": (C.c_int, [H, C.c_int, C.POINTER(rdm_bsr)]),
         "rdm_solve": (C.c_int, [H, C.POINTER(rdm_info)]),
         "rdm_solve_async": (C.c_int, [H]),
         "rdm_sync": (C.c_int, [H, C.POINTER(rdm_info)]),
@@ -221,6 +222,13 @@ def rdm_upload_h0(h, sys: int, m, n_electrons: int) -> None:
 def rdm_upload_h1(h, sys: int, direction: int, m) -> None:
     s, keep = to_bsr(m)
     _check(h, _lib.rdm_upload_h1(h, sys, direction, C.byref(s)))
+    del keep
+
+
+def rdm_upload_s(h, sys: int, m) -> None:
+    """Overlap matrix of system `sys` (non-orthogonal basis, see include/rdm.h)."""
+    b, keep = to_bsr(m)
+    _check(h, _lib.rdm_upload_s(h, sys, C.byref(b)))
     del keep
 
 
@@ -429,6 +437,8 @@ class Solver:
             dirs = getattr(y, "dirs", ("x", "y", "z")[: len(y.h1)])
             for d, m in zip(dirs, y.h1):
                 rdm_upload_h1(self.h, s, "xyz".index(d), m)
+            if getattr(y, "s", None) is not None:
+                rdm_upload_s(self.h, s, y.s)
 
     def solve(self):
         code, info = rdm_solve(self.h)

@@ -75,9 +75,14 @@ def test_autotune_probes_every_block_size_and_keeps_the_fastest(rdm, exact_alpha
     a = sol.alpha()
     assert np.max(np.abs(a - exact_alpha)) / np.max(np.abs(exact_alpha)) <= 1e-6
     assert sol.p0().b == 32
-    # later solves keep the choice without probing again
+    # later solves keep the choice without probing again, also after a new
+    # upload of a problem of the same shape
     code, info2 = sol.solve()
     assert info2.block_size == info.block_size and list(info2.probe_ms) == probes
+    sol.load(s)
+    code, info3 = sol.solve()
+    assert info3.block_size == info.block_size and list(info3.probe_ms) == probes
+    assert info3.time_ms < 0.8 * info.autotune_ms
     assert np.max(np.abs(sol.alpha() - exact_alpha)) / np.max(np.abs(exact_alpha)) <= 1e-6
 
 

@@ -157,7 +157,7 @@ def test_mixed_solve_vs_oracle(rdm, cluster150, oracle150, mode):
 
 @pytest.mark.parametrize("refine,tol", [(1, 1e-6), (3, 1e-6), (2, 1e-6)])
 def test_final_tier_first_order_arithmetic(rdm, cluster150, oracle150, refine, tol):
-    """Final tier of the fp16 ladder (X0^2 refined in double-FP32): X1 products in FP64 (1),
+    """Final tier of the fp16 ladder (X0^2 refined as tensor-core slice products, the default): X1 products in FP64 (1),
     FP32 on the CUDA cores (3), or kept on the tensor cores (2, the default;
     with segmented accumulation as accurate as FP32)."""
     s = cluster150
