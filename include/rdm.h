@@ -179,7 +179,7 @@ typedef struct {
     double  kernel_flops[5];   /* useful flops (2 b^3 per block triple) of the tensor-core split (0),
                                   FP64 (1), FP32 (2), double-FP32 (3) and slice-product (4) launches */
     int64_t kernel_launches;   /* kernels launched by the solve */
-    int32_t tc_launches;       /* launches of the tensor-core product kernel */
+    int32_t tc_launches;       /* launches of the tensor-core split-product kernel */
     int32_t simt_launches;     /* launches of the CUDA-core product kernel */
     double  numeric_bytes;  /* algorithmic bytes of the product launches: operand blocks read
                                once (8 bytes/element FP64, 4 bytes hi+lo planes) + output
@@ -191,7 +191,7 @@ typedef struct {
     double  autotune_ms;       /* wall time of the autotuner's probe solves (0 when it did not run) */
     double  probe_ms[3];       /* device time of the probe solve at b = 16, 32, 64 (0: not probed) */
     int32_t lowdin_iterations; /* Newton-Schulz iterations for S^(-1/2) (0: orthogonal basis) */
-    int32_t pad1;
+    int32_t oz_launches;       /* launches of the tensor-core slice-product kernel */
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */
@@ -326,7 +326,8 @@ int rdm_get_log(rdm_handle *h, rdm_iter_log *out, int cap, int *n);
  * host BSR matrices with the same nb, b, n (X may be NULL: no linear term).
  * `mode` selects the product arithmetic (RDM_MODE_*; the mixed modes use the
  * hi+lo split tensor-core product; RDM_PRODUCT_SLICES the exact bf16 slice
- * product of RDM_REFINE_SLICES, for terms = 1 and 32 x 32 blocks).  The result goes to *out as for
+ * product of RDM_REFINE_SLICES, for terms = 1 and 32 x 32 blocks; both take symmetric block
+ * patterns, else RDM_EBADBSR).  The result goes to *out as for
  * rdm_get_p0; call with out->nnzb = 0 / NULL arrays to query the size only
  * (*needed receives the block count). */
 #define RDM_PRODUCT_SLICES   8   /* rdm_block_product only: the tensor-core slice product */
@@ -379,10 +380,16 @@ typedef struct {
                                 builders of the tensor-core tile and K-step lists; rows whose columns
                                 span more take the serial merges.  0 = 16,384.  Results do not depend
                                 on it. */
+    int32_t tc_block_copies; /* 1: the split-precision kernel's operand planes sit at their blocks' own
+                                positions and every block is one bulk copy (0: at the positions of the
+                                transposed blocks, so that neighbouring slots of a K-step share a copy).
+                                Results do not depend on it. */
+    int32_t pad0;            /* zero */
 } rdm_test_knobs;
 
 /* Set the test settings of h (NULL restores all zeros).  RDM_EINVAL for a
- * negative value or a window that is not a multiple of 32 up to 16,384. */
+ * negative value, a window that is not a multiple of 32 up to 16,384, or a
+ * flag other than 0 or 1. */
 int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k);
 
 /* Library version string. */

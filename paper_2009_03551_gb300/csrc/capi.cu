@@ -472,7 +472,7 @@ struct StepStats {
     double issued_tc = 0, issued_oz = 0;
     double bytes = 0;
     double ms[7] = {0, 0, 0, 0, 0, 0, 0};   // symbolic, tc, fp64, fp32, compaction, double-fp32, slice products
-    int tc_launches = 0, simt_launches = 0;
+    int tc_launches = 0, oz_launches = 0, simt_launches = 0;
     int groups = 1;                         // job groups of the numeric phase
 };
 
@@ -802,7 +802,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         if (oz_g) {
             const long long lt = g_kernel_launches;
             ss.issued_oz += launch_numeric_oz(a, in, mcol, h->ozw, h->tcw_oz, oplan, st);
-            ss.tc_launches += (int)(g_kernel_launches - lt);
+            ss.oz_launches += (int)(g_kernel_launches - lt);
         }
         RDM_CUDA_TRY(cudaEventRecord(h->ev[7], st));
 
@@ -820,6 +820,7 @@ StepStats multiply(rdm_handle *h, MatSet &in, MatSet &out, const JobTable &jt,
         if (oz_g) d2h(&oz_err, h->tcw_oz.counters.p, 1, st);
         sync(h);
         tc_err |= oz_err;
+        if (tc_err & 8) throw Error{RDM_EBADBSR, "an operand's block pattern is not symmetric"};
         if (tc_err)
             throw Error{tc_err & 1 ? RDM_ETIMEOUT : RDM_ECUDA,
                         "tensor-core product kernel failed (code " + std::to_string(tc_err) + ")"};
@@ -1159,7 +1160,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     std::vector<int> act(S);
     double useful = 0, issued = 0, nbytes = 0, flops_tc = 0, flops_64 = 0, flops_32 = 0, flops_ff = 0, flops_oz = 0;
     double kms[7] = {0, 0, 0, 0, 0, 0, 0};
-    int tc_launches = 0, simt_launches = 0, max_groups = 1;
+    int tc_launches = 0, oz_launches = 0, simt_launches = 0, max_groups = 1;
     g_dev_bytes_peak = g_dev_bytes.load();
     cudaEvent_t ev0, ev1;
     RDM_CUDA_TRY(cudaEventCreate(&ev0));
@@ -1317,6 +1318,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         issued += sst.issued_tc + sst.issued_oz + (double)(sst.pairs_64 + sst.pairs_32 + sst.pairs_ff) * fpb;
         nbytes += sst.bytes;
         tc_launches += sst.tc_launches;
+        oz_launches += sst.oz_launches;
         simt_launches += sst.simt_launches;
         max_groups = std::max(max_groups, sst.groups);
         for (int k = 0; k < 7; ++k) kms[k] += sst.ms[k];
@@ -1401,6 +1403,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         I.kernel_flops[4] = flops_oz;
         I.kernel_launches = g_kernel_launches - launches0;
         I.tc_launches = tc_launches;
+        I.oz_launches = oz_launches;
         I.simt_launches = simt_launches;
         I.numeric_bytes = nbytes;
         I.device_bytes_peak = (int64_t)g_dev_bytes_peak.load();
@@ -1865,11 +1868,13 @@ int rdm_set_test_knobs(rdm_handle *h, const rdm_test_knobs *k) {
     rdm_test_knobs z{};
     if (!k) k = &z;
     if (k->tc_wait_cycles < 0 || k->tc_hold < 0 || k->tc_hold > 1 || k->tc_window_cols < 0 ||
-        k->tc_window_cols > 16384 || (k->tc_window_cols & 31))
+        k->tc_window_cols > 16384 || (k->tc_window_cols & 31) || k->tc_block_copies < 0 ||
+        k->tc_block_copies > 1 || k->pad0 != 0)
         return fail(h, RDM_EINVAL, "invalid test settings");
     h->tcw.knobs.wait_cycles = k->tc_wait_cycles;
     h->tcw.knobs.hold = k->tc_hold;
     h->tcw.knobs.window_words = k->tc_window_cols / 32;
+    h->tcw.knobs.block_copies = k->tc_block_copies;
     return RDM_OK;
 }
 

@@ -94,6 +94,48 @@ __global__ void __launch_bounds__(256) k_oz_row_exp(const int *__restrict__ row_
     if (q == 0) e[(size_t)i * 32 + r] = mx > 0.0 ? ilogb(mx) + 1 : 0;
 }
 
+// The kOzSlices base-128 digits of x0 = v 2^-er (|x0| < 1: 2^er bounds the
+// row), each the round-half-even of the remainder times 128, as in the
+// slicing of Ozaki, Ogita, Oishi and Rump: x0 = sum_i a_i 2^(-7(i+1)) + a
+// remainder below 2^-49.  Integer arithmetic, exact (FP64 throughput is low
+// on this part): X = x0 2^60 is held as its floor plus a sticky bit for the
+// bits below; digit i has unit 2^(53 - 7i) in X.
+__device__ __forceinline__ void oz_digits(double v, int er, int (&a)[kOzSlices]) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(v);
+    const bool neg = (bits >> 63) != 0;
+    const int E = (int)((bits >> 52) & 0x7FF);
+    uint64_t M = bits & ((1ull << 52) - 1);
+    int ex = 1 - 1075;                                   // subnormal
+    if (E != 0) {
+        M |= 1ull << 52;
+        ex = E - 1075;
+    }
+    const int sh = ex - er + 60;                         // |x0| 2^60 = M 2^sh
+    int64_t X = 0;
+    bool sticky = false;
+    if (M != 0) {
+        if (sh >= 0) {
+            X = (int64_t)(M << sh);                      // sh <= 7: M 2^sh < 2^60
+        } else {
+            const int rs = -sh;
+            const uint64_t q = rs >= 64 ? 0ull : M >> rs;
+            sticky = rs >= 64 ? true : (M & ((1ull << rs) - 1)) != 0;
+            X = (int64_t)q;
+        }
+        if (neg) X = -X - (sticky ? 1 : 0);              // the floor of the negative value
+    }
+#pragma unroll
+    for (int i = 0; i < kOzSlices; ++i) {
+        const int s = 53 - 7 * i;
+        int64_t q = X >> s;                              // floor
+        const int64_t r = X - (q << s);                  // in [0, 2^s); true fraction (r + sticky) / 2^s
+        const int64_t half = 1ll << (s - 1);
+        if (r > half || (r == half && (sticky || (q & 1)))) q += 1;
+        a[i] = (int)q;
+        X -= q << s;
+    }
+}
+
 // slices of matrix-0 blocks: one thread per 8 consecutive elements of a block row
 __global__ void k_oz_slices(const double *__restrict__ val, const int *__restrict__ row_of_blk,
                             const int *__restrict__ e, int64_t nblk, __nv_bfloat16 *__restrict__ out) {
@@ -103,17 +145,18 @@ __global__ void k_oz_slices(const double *__restrict__ val, const int *__restric
     const int rc0 = (int)(g & 127) * 8;
     const int r = rc0 >> 5, c0 = rc0 & 31;
     const int er = e[(size_t)row_of_blk[p] * 32 + r];
-    const double *v = val + p * 1024 + rc0;
+    const double2 *v2 = reinterpret_cast<const double2 *>(val + p * 1024 + rc0);
     uint16_t s[kOzSlices][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        double x = ldexp(v[u], -er);
+    for (int k = 0; k < 4; ++k) {
+        const double2 x2 = v2[k];
+        const double xs[2] = {x2.x, x2.y};
 #pragma unroll
-        for (int i = 0; i < kOzSlices; ++i) {
-            const double y = x * 128.0;
-            const double a = rint(y);
-            x = y - a;
-            s[i][u] = __bfloat16_as_ushort(__float2bfloat16_rn((float)a));
+        for (int u = 0; u < 2; ++u) {
+            int a[kOzSlices];
+            oz_digits(xs[u], er, a);
+#pragma unroll
+            for (int i = 0; i < kOzSlices; ++i) s[i][2 * k + u] = __bfloat16_as_ushort(__float2bfloat16_rn((float)a[i]));
         }
     }
     __nv_bfloat16 *o = out + p * (kOzSlices * 1024);

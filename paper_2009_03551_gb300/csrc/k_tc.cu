@@ -29,9 +29,14 @@
 // streaming probe (one CTA per SM, no MMA) moves at most ~6.5 TB/s over the
 // GPU in 4 KB bulk copies, from L2 as from DRAM, and ~7.4-8.9 TB/s in
 // 16-32 KB copies: the rate of such copies into each SM bounds this kernel.
+// So the planes of the operand block (i, k) are stored at the position of
+// block (k, i) (the patterns are symmetric): the A blocks (i_0..i_3, k) of a
+// K-step are then neighbours in block row k, and so are its B blocks
+// (j_0..j_7, k) wherever row k holds them all, and the copy warp moves every
+// run of slots whose blocks are neighbours in memory with one copy.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over a static tile
-// schedule): warp 0 issues the bulk copies into a ring of stages, warp 1
+// schedule, tiles round robin): warp 0 issues the bulk copies into a ring of stages, warp 1
 // owns the tensor-memory allocation and one thread issues the MMAs, warps
 // 2-9 (two per TMEM lane quarter, 128 accumulator columns each) run the
 // epilogue.  Ten warps put three on some SM sub-partitions, which caps a
@@ -51,9 +56,10 @@
 // buffer.  The drift is then that of one segment (-7e-7 relative),
 // independent of the tile's length.  After the last segment:
 // C = c_lin X + c_sq D, diagonal blocks symmetrised, block Frobenius norm,
-// truncation flag, FP64 store of the (upper-triangle) block.  Every wait is
-// bounded: on timeout the kernel raises an error flag, drains what it issued
-// and frees its tensor memory.
+// truncation flag, FP64 store of the (upper-triangle) block; the old X
+// blocks of the next tile's linear terms are prefetched into L2 two segments
+// before this tile ends.  Every wait is bounded: on timeout the kernel raises
+// an error flag, drains what it issued and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -92,6 +98,9 @@ template <int B>
 constexpr int meta_words() { return B == 16 ? 16 * 8 : 0; }
 template <int B>
 constexpr int meta_stride() { return B == 16 ? 1 : 33; }
+// output blocks whose metadata an epilogue warp holds (one lane each)
+template <int B>
+constexpr int blocks_per_warp() { return B == 16 ? 16 : B == 32 ? 4 : 2; }
 static_assert(kSegBufs >= 2 && (kSegBufs & (kSegBufs - 1)) == 0, "tile shape");
 
 // Stays 0 for the life of the program: the test setting `hold` makes the
@@ -125,30 +134,46 @@ __device__ __forceinline__ int pair_offset(int r, int c, int plane) {
     return (r >> 3) * (16 * B) + plane * (8 * B) + ((c >> 3) << 6) + ((r & 7) << 3) + (c & 7);
 }
 
+// Largest block norm of every matrix of the set: each CTA takes a contiguous
+// chunk of blocks and folds the part of every matrix it overlaps into mx[m]
+// (norms are non-negative, so their bit patterns order like the values).
+__global__ void k_matrix_max(const float *__restrict__ nrm, const int *__restrict__ mat_first, int nmat,
+                             unsigned *__restrict__ mx) {
+    const int64_t total = mat_first[nmat];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
+    __shared__ float sh[32];
+    for (int m = 0; m < nmat; ++m) {
+        const int64_t a = c0 > mat_first[m] ? c0 : mat_first[m];
+        const int64_t b = c1 < mat_first[m + 1] ? c1 : mat_first[m + 1];
+        if (a >= b) continue;                               // the same for the whole CTA
+        float v = 0.f;
+        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) v = fmaxf(v, nrm[p]);
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmaxf(v, sh[k]);
+            atomicMax(&mx[m], __float_as_uint(v));
+        }
+        __syncthreads();
+    }
+}
+
 // per matrix m: scale[m] = 2^floor(log2(2^14 / max block norm)) for fp16 (the
 // largest element then sits below 2^14, far from fp16 overflow, and values
 // down to ~1e-9 of it stay normal); 1 for bf16, whose exponent range is FP32's
-__global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__restrict__ mat_first, int nmat,
-                                int fp16, float *__restrict__ scale) {
-    const int m = blockIdx.x;
+__global__ void k_matrix_scales(const unsigned *__restrict__ mxbits, int nmat, int fp16, float *__restrict__ scale) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nmat) return;
-    float mx = 0.f;
-    for (int p = mat_first[m] + threadIdx.x; p < mat_first[m + 1]; p += blockDim.x) mx = fmaxf(mx, nrm[p]);
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ float sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmaxf(mx, sh[k]);
-        mx = fmaxf(mx, sh[0]);
-        float s = 1.f;
-        if (fp16 && mx > 0.f) {
-            int e = (int)floorf(log2f(16384.f / mx));
-            e = max(-60, min(60, e));
-            s = ldexpf(1.f, e);
-        }
-        scale[m] = s;
+    const float mx = __uint_as_float(mxbits[m]);
+    float s = 1.f;
+    if (fp16 && mx > 0.f) {
+        int e = (int)floorf(log2f(16384.f / mx));
+        e = max(-60, min(60, e));
+        s = ldexpf(1.f, e);
     }
+    scale[m] = s;
 }
 
 // one thread per 8 consecutive elements of a block row (one core-matrix row):
@@ -156,7 +181,7 @@ __global__ void k_matrix_scales(const float *__restrict__ nrm, const int *__rest
 template <bool BF16, int B>
 __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uint16_t *__restrict__ hi,
                                const float *__restrict__ scale,
-                               const int *__restrict__ mat_first, int nmat) {
+                               const int *__restrict__ mat_first, int nmat, const int *__restrict__ tpos) {
     constexpr int kPE = B * B;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nblk * (kPE / 8)) return;
@@ -193,10 +218,42 @@ __global__ void k_split_planes(const double *__restrict__ val, int64_t nblk, uin
     hv.z = h[4] | ((uint32_t)h[5] << 16); hv.w = h[6] | ((uint32_t)h[7] << 16);
     lv.x = l[0] | ((uint32_t)l[1] << 16); lv.y = l[2] | ((uint32_t)l[3] << 16);
     lv.z = l[4] | ((uint32_t)l[5] << 16); lv.w = l[6] | ((uint32_t)l[7] << 16);
-    // columns c0..c0+7 of row r are 8 consecutive elements of one core matrix
-    uint16_t *o = hi + p * (2 * kPE);
+    // columns c0..c0+7 of row r are 8 consecutive elements of one core matrix;
+    // the block's planes go to the position of its transpose (tpos), or to
+    // its own position without one
+    const int64_t at = tpos ? (int64_t)tpos[p] : p;
+    if (at < 0) return;
+    uint16_t *o = hi + at * (2 * kPE);
     *reinterpret_cast<uint4 *>(o + pair_offset<B>(r, c0, 0)) = hv;
     *reinterpret_cast<uint4 *>(o + pair_offset<B>(r, c0, 1)) = lv;
+}
+
+// Position of the transposed block: for block e = (i, k) of matrix m of the
+// set, the global index of block (k, i) of the same matrix.  The patterns of
+// the set are symmetric, so it exists; if not, -1 and error bit 8.
+__global__ void k_transpose_pos(const int *__restrict__ rp, const int *__restrict__ col, int nrow_flat, int NB,
+                                int64_t total, int *__restrict__ tpos, int *__restrict__ err) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    // flat row r of e: the last r with rp[r] <= e
+    int lo = 0, hi = nrow_flat - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int m = lo / NB, i = lo - m * NB, k = col[e];
+    const int end = rp[m * NB + k + 1];
+    int a = rp[m * NB + k], z = end;
+    while (a < z) {
+        const int mid = (a + z) >> 1;
+        if (col[mid] < i) a = mid + 1; else z = mid;
+    }
+    if (a < end && col[a] == i) {
+        tpos[e] = a;
+    } else {
+        tpos[e] = -1;
+        atomicOr(err, 8);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -226,6 +283,8 @@ struct TcArgs {
     int *err;
     long long wait_cycles;        // bound of every mbarrier wait
     int hold;                     // test setting: the MMA thread waits for g_never_set first
+    int runs;                     // 1: slots whose blocks are neighbours in memory share a copy
+    const int *pre_err;           // error bits of the operand preparation, passed on to err
 };
 
 struct __align__(8) SmemCtl {
@@ -240,8 +299,7 @@ struct __align__(8) SmemCtl {
 
 // Epilogue metadata of one output block, gathered by one lane while the
 // tile's MMAs run and parked in shared memory (8 words per block: slot, old
-// slot, diagonal, output index, c_lin, c_sq, tau lo, tau hi); the old X
-// block of the linear term is prefetched into L2.
+// slot, diagonal, output index, c_lin, c_sq, tau lo, tau hi).
 template <int B>
 __device__ __forceinline__ void gather_meta(const TcArgs &A, int s, float *q) {
     constexpr int W = meta_stride<B>();
@@ -259,10 +317,6 @@ __device__ __forceinline__ void gather_meta(const TcArgs &A, int s, float *q) {
         m_sx = A.slot_x[s];
         m_diag = A.slot_t[s] == s;
         m_keepidx = A.uidx[s] - (int)A.u0;
-        if (m_sx >= 0 && m_cl != 0.f) {
-            const double *px = A.in_val + (size_t)m_sx * (B * B);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8 * B * B) : "memory");
-        }
     }
     q[0] = __int_as_float(s);
     q[W] = __int_as_float(m_sx);
@@ -272,6 +326,34 @@ __device__ __forceinline__ void gather_meta(const TcArgs &A, int s, float *q) {
     q[5 * W] = m_cq;
     q[6 * W] = __int_as_float(__double2loint(m_tau));
     q[7 * W] = __int_as_float(__double2hiint(m_tau));
+}
+
+// The output block (slot) whose metadata lane `lane` of epilogue warp
+// (eq, colhalf) gathers, from tile record d; -1 for lanes without one.
+template <int B, class G>
+__device__ __forceinline__ int lane_slot(const int *d, int eq, int colhalf, int lane) {
+    if constexpr (B == 32) {
+        // block row eq of the tile, block columns 4 colhalf .. 4 colhalf + 3
+        return lane < 4 ? d[4 + eq * G::TBN + 4 * colhalf + lane] : -1;
+    } else if constexpr (B == 16) {
+        // block rows 2 eq (lanes 0-7) and 2 eq + 1 (lanes 8-15), block columns 8 colhalf .. + 7
+        return lane < 16 ? d[4 + (2 * eq + (lane >> 3)) * G::TBN + 8 * colhalf + (lane & 7)] : -1;
+    } else {
+        // block row eq / 2 (row half eq & 1), block columns 2 colhalf, 2 colhalf + 1
+        return lane < 2 ? d[4 + (eq >> 1) * G::TBN + 2 * colhalf + lane] : -1;
+    }
+}
+
+// Prefetch into L2 the old X blocks of the linear terms of tile tn (the
+// warp's next tile), two segments before they are read.
+template <int B, class G>
+__device__ __forceinline__ void prefetch_old_blocks(const TcArgs &A, int tn, int eq, int colhalf, int lane) {
+    const int s = lane_slot<B, G>(A.tiles + (size_t)tn * G::kTileInts, eq, colhalf, lane);
+    if (s < 0) return;
+    const int sx = A.slot_x[s];
+    if (sx < 0 || A.c_lin[A.sys_of_row[A.slot_row[s]]] == 0.0) return;
+    const double *px = A.in_val + (size_t)sx * (B * B);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(px), "r"(8 * B * B) : "memory");
 }
 
 // b = 64: one step of the handshake of the two epilogue warps that share a
@@ -306,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
     volatile int *abort_flag = &ctl->abort_flag;
 
     if (threadIdx.x == 0) {
+        if (blockIdx.x == 0 && *A.pre_err) atomicOr(A.err, *A.pre_err);
         for (int s = 0; s < G::kStages; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
         for (int b = 0; b < kSegBufs; ++b) { mbar_init(&ctl->seg_full[b], 1); mbar_init(&ctl->seg_empty[b], kEpiWarps); }
         mbar_init(&ctl->drain, 1);
@@ -330,10 +413,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
         // ---------------- producer: bulk copies of the operand blocks ----------------
         // Lane m < kSlots owns slot m of every stage (slot m < TBM: A block row
         // m, else B block row m - TBM; slot m at m * kPairBytes): it loads the
-        // block index of the next K-step while the current step's copies, one
-        // copy per slot (hi and lo planes), are issued by all lanes at once.
-        // A slot whose block is missing needs zeros; a stage slot that already
-        // holds zeros from its previous use is not copied again (zmask).
+        // block index of the next K-step while the current step's copies are
+        // issued.  A slot whose block is missing needs zeros; a stage slot that
+        // already holds zeros from its previous use is not copied again (zmask).
         uint32_t it = 0;
         bool ok = true;
         uint32_t zmask[G::kStages];
@@ -364,12 +446,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
 #pragma unroll
                 for (int k = 0; k < G::kStages; ++k)
                     if (k == st) zmask[k] = zbits;
-                if (!skip) {
-                    // zero blocks: one per CTA and slot, so that the CTAs do not all
-                    // read the same few L2 sectors
-                    const uint16_t *src = cur >= 0 ? A.planes + (size_t)cur * (2 * G::kPlaneElems)
-                                                   : A.zero + ((size_t)blockIdx.x * G::kSlots + lane) * (2 * G::kPlaneElems);
-                    bulk_g2s(stages + st * G::kStageBytes + lane * G::kPairBytes, src, G::kPairBytes, &ctl->full[st]);
+                // zero blocks: one per CTA and slot (so that the CTAs do not all
+                // read the same few L2 sectors), adjacent like the slots
+                const uint16_t *src = cur >= 0 ? A.planes + (size_t)cur * (2 * G::kPlaneElems)
+                                               : A.zero + ((size_t)blockIdx.x * G::kSlots + lane) * (2 * G::kPlaneElems);
+                // runs: a slot whose source follows its left neighbour's in
+                // memory joins that neighbour's copy; the first slot of a run
+                // copies the whole run
+                const uint16_t *left = reinterpret_cast<const uint16_t *>(
+                    __shfl_up_sync(0xffffffffu, reinterpret_cast<unsigned long long>(src), 1));
+                const bool joins = A.runs && lane > 0 && !skip && ((need >> (lane - 1)) & 1u) &&
+                                   src == left + 2 * G::kPlaneElems;
+                const uint32_t jm = __ballot_sync(0xffffffffu, joins);
+                if (!skip && !joins) {
+                    const uint32_t above = lane < 31 ? jm >> (lane + 1) : 0u;
+                    const uint32_t len = (uint32_t)__ffs(~above);      // this slot and the slots that join it
+                    bulk_g2s(stages + st * G::kStageBytes + lane * G::kPairBytes, src, len * G::kPairBytes,
+                             &ctl->full[st]);
                 }
             }
         }
@@ -443,16 +536,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
         for (int t = blockIdx.x; t < A.ntile && !*abort_flag; t += gridDim.x) {
             const int *d = A.tiles + (size_t)t * G::kTileInts;
             // metadata of this warp's output blocks, one lane each
-            if constexpr (B == 32) {
-                // block row eq of the tile, block columns 4 colhalf .. 4 colhalf + 3
-                if (lane < 4) gather_meta<B>(A, d[4 + eq * G::TBN + 4 * colhalf + lane], meta + lane * 8 * MW);
-            } else if constexpr (B == 16) {
-                // block rows 2 eq (lanes 0-7) and 2 eq + 1 (lanes 8-15), block columns 8 colhalf .. + 7
-                if (lane < 16)
-                    gather_meta<B>(A, d[4 + (2 * eq + (lane >> 3)) * G::TBN + 8 * colhalf + (lane & 7)], meta + lane * 8 * MW);
-            } else {
-                // block row eq / 2 (row half eq & 1), block columns 2 colhalf, 2 colhalf + 1
-                if (lane < 2) gather_meta<B>(A, d[4 + (eq >> 1) * G::TBN + 2 * colhalf + lane], meta + lane * 8 * MW);
+            {
+                const int s = lane_slot<B, G>(d, eq, colhalf, lane);
+                // blocks per warp: 4 at b = 32, 16 at b = 16, 2 at b = 64 (each shared
+                // with the partner warp that holds the other row half)
+                if (lane < blocks_per_warp<B>()) gather_meta<B>(A, s, meta + lane * 8 * MW);
             }
             __syncwarp();
             const int nst = d[3];
@@ -467,6 +555,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_bf16x3(TcArgs A) {
             for (int g = 0; g < nseg; ++g, ++seg) {
                 const int buf = seg & (kSegBufs - 1);
                 const uint32_t use = seg / kSegBufs;
+                if (g == (nseg > 2 ? nseg - 2 : 0) && t + (int)gridDim.x < A.ntile)
+                    prefetch_old_blocks<B, G>(A, t + gridDim.x, eq, colhalf, lane);
                 if (!mbar_wait(&ctl->seg_full[buf], use & 1, abort_flag, A.wait_cycles)) { ok = false; break; }
                 fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(32 * eq) << 16) + buf * kTileN + 128 * colhalf;
@@ -729,12 +819,13 @@ template <int B>
 void split_planes(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
     const int64_t n = in.total * (int64_t)(B * B);
     const int64_t grid = (n / 8 + 255) / 256;
+    const int *tpos = w.tpos_valid ? w.tpos.p : nullptr;
     if (ar == AR_BF16X3)
         k_split_planes<true, B><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
-                                                                w.mat_first.p, in.nmat);
+                                                                w.mat_first.p, in.nmat, tpos);
     else
         k_split_planes<false, B><<<(unsigned)grid, 256, 0, st>>>(in.val.p, in.total, in.ophi.p, w.scale.p,
-                                                                 w.mat_first.p, in.nmat);
+                                                                 w.mat_first.p, in.nmat, tpos);
     RDM_LAUNCH_CHECK();
 }
 
@@ -769,6 +860,8 @@ double launch_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith a
     A.err = w.counters.p;
     A.wait_cycles = w.knobs.wait_cycles > 0 ? w.knobs.wait_cycles : kWaitCycles;
     A.hold = w.knobs.hold;
+    A.runs = w.tpos_valid ? 1 : 0;
+    A.pre_err = w.pre_err.p;
     static bool attr = false;
     if (!attr) {
         RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -796,11 +889,31 @@ void prepare_operands(MatSet &in, Arith ar, TcWork &w, cudaStream_t st) {
     w.mat_first.ensure(nmat + 1);
     w.scale.ensure(std::max(nmat, 1));
     RDM_CUDA_TRY(cudaMemcpyAsync(w.mat_first.p, first.data(), (nmat + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_matrix_scales<<<nmat, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
+    w.mx.ensure(std::max(nmat, 1));
+    RDM_CUDA_TRY(cudaMemsetAsync(w.mx.p, 0, std::max(nmat, 1) * sizeof(unsigned), st));
+    if (in.total > 0) {
+        const int grid = (int)std::min<int64_t>(4 * 152, (in.total + 255) / 256);
+        k_matrix_max<<<grid, 256, 0, st>>>(in.nrm.p, w.mat_first.p, nmat, w.mx.p);
+        RDM_LAUNCH_CHECK();
+    }
+    k_matrix_scales<<<(nmat + 31) / 32, 32, 0, st>>>(w.mx.p, nmat, ar == AR_FP16X3 ? 1 : 0, w.scale.p);
     RDM_LAUNCH_CHECK();
     const int64_t n = in.total * (int64_t)in.b * in.b;
     in.ophi.ensure(std::max<int64_t>(2 * n, 1));   // hi and lo, interleaved per block
+    w.pre_err.ensure(1);
+    RDM_CUDA_TRY(cudaMemsetAsync(w.pre_err.p, 0, sizeof(int), st));
+    w.tpos_valid = false;
     if (n == 0) return;
+    // planes at the positions of the transposed blocks (the plan builder
+    // points the K-step lists there), unless the test setting asks for one
+    // copy per block
+    if (!w.knobs.block_copies) {
+        w.tpos.ensure(in.total);
+        k_transpose_pos<<<(unsigned)((in.total + 255) / 256), 256, 0, st>>>(
+            in.row_ptr.p, in.col.p, nmat * in.NB, in.NB, in.total, w.tpos.p, w.pre_err.p);
+        RDM_LAUNCH_CHECK();
+        w.tpos_valid = true;
+    }
     switch (in.b) {
         case 16: split_planes<16>(in, ar, w, st); break;
         case 32: split_planes<32>(in, ar, w, st); break;

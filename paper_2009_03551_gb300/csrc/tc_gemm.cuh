@@ -12,6 +12,7 @@ struct TcKnobs {
     int hold = 0;               // 1: the MMA thread first waits for a flag that nothing sets
     int window_words = 0;       // bitmap window of the tile-plan builders in 32-column words
                                 // (0: 512, i.e. 16,384 columns; wider windows take the serial merge)
+    int block_copies = 0;       // 1: planes at their own positions and one bulk copy per block
 };
 
 // work buffers of the tensor-core path (tile lists, per-tile K-step lists)
@@ -27,7 +28,11 @@ struct TcWork {
     DevBuf<int> scan32;
     DevBuf<int64_t> scan64;
     DevBuf<float> scale;        // per matrix: power-of-two scale of its operand planes
+    DevBuf<unsigned> mx;        // per matrix: largest block norm (bit pattern)
     DevBuf<int> mat_first;      // per matrix: first global block index (nmat+1)
+    DevBuf<int> tpos;           // per block (i, k) of the input set: global index of block (k, i)
+    DevBuf<int> pre_err;        // error bits of the operand preparation (8: a transposed block missing)
+    bool tpos_valid = false;    // the planes sit at tpos and the K-step lists point there
 };
 
 // work buffers of the slice-product (FP64-class) tensor-core path

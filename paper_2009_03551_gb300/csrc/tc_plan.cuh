@@ -42,6 +42,7 @@ struct TileBuild {
     int *steps;          // [nsteps * kSlots]
     int ntile;
     int max_words;       // bitmap window in 32-column words (<= 512); wider windows: serial merge
+    const int *tpos;     // K-step entries point at tpos[e] (the planes' position), or at e if null
 };
 
 // upper mask range [cur, end) of block row TBM I + m of job p, empty for rows
@@ -244,7 +245,7 @@ __device__ void tile_steps_serial(const TileBuild &T, int t, int fill) {
             if (anyA && anyB) {
                 if (fill && w + n < T.step_off[t + 1]) {
                     int *s = T.steps + (size_t)(w + n) * G::kSlots;
-                    for (int q = 0; q < G::kSlots; ++q) s[q] = idx[q];
+                    for (int q = 0; q < G::kSlots; ++q) s[q] = idx[q] >= 0 && T.tpos ? T.tpos[idx[q]] : idx[q];
                 }
                 ++n;
             }
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(32 * kStepWarps) k_tile_steps(TileBuild T, int
                     const unsigned word = ba[kk >> 5];
                     if (!((word >> (kk & 31)) & 1u)) continue;
                     const int r = wr[kk >> 5] + __popc(word & ((1u << (kk & 31)) - 1u));
-                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * G::kSlots + q] = e;
+                    if (w + n + r < wend) T.steps[(size_t)(w + n + r) * G::kSlots + q] = T.tpos ? T.tpos[e] : e;
                 }
             __syncwarp();
         }
@@ -398,6 +399,7 @@ TcPlan build_plan(const MatSet &in, const JobTable &jt, const SysDev &sd, const 
     T.u0 = unit0; T.u1 = unit1;
     T.sys_tier = sd.tier.p;
     T.tile_cnt = w.tile_cnt.p; T.tile_off = w.tile_off.p;
+    T.tpos = w.tpos_valid ? w.tpos.p : nullptr;
     static_assert(kTileRowWords == kStepWords, "one window bound for both plan builders");
     T.max_words = w.knobs.window_words > 0 && w.knobs.window_words < kTileRowWords ? w.knobs.window_words
                                                                                     : kTileRowWords;

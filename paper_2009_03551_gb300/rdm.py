@@ -77,11 +77,12 @@ class rdm_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("block_size", C.c_int32), ("autotune_ms", C.c_double),
-                ("probe_ms", C.c_double * 3), ("lowdin_iterations", C.c_int32), ("pad1", C.c_int32)]
+                ("probe_ms", C.c_double * 3), ("lowdin_iterations", C.c_int32), ("oz_launches", C.c_int32)]
 
 
 class rdm_test_knobs(C.Structure):
-    _fields_ = [("tc_wait_cycles", C.c_int64), ("tc_hold", C.c_int32), ("tc_window_cols", C.c_int32)]
+    _fields_ = [("tc_wait_cycles", C.c_int64), ("tc_hold", C.c_int32), ("tc_window_cols", C.c_int32),
+                ("tc_block_copies", C.c_int32), ("pad0", C.c_int32)]
 
 
 class rdm_iter_log(C.Structure):
@@ -382,10 +383,11 @@ def rdm_bsr_dot_noalloc(A, B, out_ptr: int, stream=None) -> None:
                              "nb <= 262144)")
 
 
-def rdm_set_test_knobs(h, tc_wait_cycles: int = 0, tc_hold: int = 0, tc_window_cols: int = 0) -> None:
+def rdm_set_test_knobs(h, tc_wait_cycles: int = 0, tc_hold: int = 0, tc_window_cols: int = 0,
+                       tc_block_copies: int = 0) -> None:
     """Test settings of the tensor-core path (see include/rdm.h); all zeros
     restore production behaviour."""
-    k = rdm_test_knobs(tc_wait_cycles, tc_hold, tc_window_cols)
+    k = rdm_test_knobs(tc_wait_cycles, tc_hold, tc_window_cols, tc_block_copies, 0)
     _check(h, _lib.rdm_set_test_knobs(h, C.byref(k)))
 
 

@@ -56,8 +56,8 @@ int main(void) {
          sizeof(rdm_info), sizeof(rdm_iter_log));
   printf("%zu %zu %zu %zu\n", offsetof(rdm_bsr, nnzb), offsetof(rdm_params, max_iter),
          offsetof(rdm_info, eps_min), offsetof(rdm_iter_log, nnzb0));
-  printf("%zu %zu %zu\n", sizeof(rdm_test_knobs), offsetof(rdm_test_knobs, tc_hold),
-         offsetof(rdm_test_knobs, tc_window_cols));
+  printf("%zu %zu %zu %zu\n", sizeof(rdm_test_knobs), offsetof(rdm_test_knobs, tc_hold),
+         offsetof(rdm_test_knobs, tc_window_cols), offsetof(rdm_test_knobs, tc_block_copies));
   return 0;
 }
 """
@@ -75,7 +75,7 @@ int main(void) {
                     rdm.rdm_info.eps_min.offset, rdm.rdm_iter_log.nnzb0.offset]
     knobs = [int(x) for x in lines[2].split()]
     assert knobs == [C.sizeof(rdm.rdm_test_knobs), rdm.rdm_test_knobs.tc_hold.offset,
-                     rdm.rdm_test_knobs.tc_window_cols.offset]
+                     rdm.rdm_test_knobs.tc_window_cols.offset, rdm.rdm_test_knobs.tc_block_copies.offset]
 
 
 def test_default_params_without_gpu(rdm):

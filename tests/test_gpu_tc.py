@@ -61,7 +61,8 @@ def test_tc_block_product(rdm, b, mode, terms, nblk):
     x, X = _sym_bsr(rng, n, b, 0.5, 0.25)
     h = rdm.rdm_create(0)
     try:
-        for c_lin, c_sq, tau in ((0.0, 1.0, 0.0), (2.0, -1.0, 2.0)):
+        # the solver's coefficients, and a ratio c_lin / c_sq that is not a power of two
+        for c_lin, c_sq, tau in ((0.0, 1.0, 0.0), (2.0, -1.0, 2.0), (0.5, 3.0, 0.0)):
             prod = a @ a if terms == 1 else a @ bd + bd @ a
             exact = c_lin * x + c_sq * prod
             ref = block_truncate(exact, b, tau)
@@ -80,6 +81,22 @@ def test_tc_block_product(rdm, b, mode, terms, nblk):
             if tau > 0:
                 assert not np.any(kept[nrm < tau * 0.999])
             assert np.allclose(got, got.T, rtol=0, atol=0)     # exactly symmetric
+    finally:
+        rdm.rdm_destroy(h)
+
+
+def test_tc_product_with_c_sq_zero_is_the_linear_term(rdm):
+    """c_sq = 0 leaves C = c_lin X: on the tensor-core paths X enters the
+    epilogue rounded to FP32, so C matches c_lin X to FP32 rounding."""
+    rng = np.random.default_rng(5)
+    a, A = _sym_bsr(rng, 3 * 32, 32, 0.5)
+    h = rdm.rdm_create(0)
+    try:
+        for mode in (rdm.MODE_MIXED_BF16, rdm.MODE_MIXED_FP16):
+            r = rdm.rdm_block_product(h, A, None, A, 1.5, 0.0, 1, 0.0, mode).to_dense()
+            assert max_rel_err(r, 1.5 * a) <= 1e-7
+        r = rdm.rdm_block_product(h, A, None, A, 1.5, 0.0, 1, 0.0, rdm.MODE_FP64).to_dense()
+        assert np.array_equal(r, 1.5 * a)
     finally:
         rdm.rdm_destroy(h)
 
@@ -371,10 +388,33 @@ def test_serial_plan_builders_give_the_same_tiles(rdm, cluster150):
         assert np.array_equal(res[0][2][d], res[1][2][d])
 
 
+@pytest.mark.parametrize("b,mode", [(16, "mixed_fp16"), (32, "mixed_fp16"), (32, "mixed_bf16"), (64, "mixed_fp16")])
+def test_run_copies_give_the_same_bits_as_block_copies(rdm, b, mode):
+    """The operand planes sit at the positions of the transposed blocks so
+    that neighbouring slots of a K-step come in one bulk copy; with the test
+    setting the planes sit at their own positions and every block is a copy
+    of its own.  The MMAs see the same operands either way: every bit of the
+    result is the same."""
+    s = make_cluster(150, opa=8, b=b, cutoff=10.0, seed=11, dirs=("x", "y", "z"))
+    res = []
+    for block_copies in (0, 1):
+        sol = rdm.Solver(0)
+        rdm.rdm_set_test_knobs(sol.h, tc_block_copies=block_copies)
+        sol.set_params(tau=1e-6, tol=1e-9, mode=mode, max_iter=100, block_size=b, autotune=0)
+        sol.load(s)
+        code, info = sol.solve()
+        assert code == rdm.RDM_OK and info.tc_launches > 0
+        res.append((sol.alpha().copy(), sol.p0().vals.copy(), [sol.p1(0, d).vals.copy() for d in range(3)]))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    for d in range(3):
+        assert np.array_equal(res[0][2][d], res[1][2][d])
+
+
 def test_test_knobs_are_validated(rdm):
     h = rdm.rdm_create(0)
     try:
-        for bad in (dict(tc_window_cols=33), dict(tc_window_cols=16416), dict(tc_wait_cycles=-1), dict(tc_hold=2)):
+        for bad in (dict(tc_window_cols=33), dict(tc_window_cols=16416), dict(tc_wait_cycles=-1), dict(tc_hold=2),
+                    dict(tc_block_copies=2), dict(tc_block_copies=-1)):
             with pytest.raises(rdm.RdmError):
                 rdm.rdm_set_test_knobs(h, **bad)
     finally:
