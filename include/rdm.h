@@ -220,12 +220,14 @@ int rdm_destroy(rdm_handle *h);
 const char *rdm_last_error(const rdm_handle *h);
 
 /* Fill *p with the defaults: tau 1e-6, tau_x1/tau_refine -1, tol 1e-9,
- * stall_tol 0, spin 2, max_iter 100, mode FP64, min_iter 1, graphs 0. */
+ * stall_tol 0, spin 2, max_iter 100, mode FP64, min_iter 1, graphs 0, the
+ * rest 0. */
 int rdm_default_params(rdm_params *p);
 
 /* Set the solve parameters.  Validated: tau >= 0, tol >= 0, max_iter >= 1, a
- * known mode, refine_x1 in 0..4, refine_x0 in {0, 1, 3, 4}, chunk_mb >= 0,
- * use_graphs == 0; anything else returns RDM_EINVAL and keeps the old set. */
+ * known mode, refine_x1 in 0..4, refine_x0 in {0, 1, 3, 4, 5}, chunk_mb >= 0,
+ * use_graphs == 0, stall_window >= 0, block_size 0 or a power of two up to 64,
+ * autotune 0 or 1; anything else returns RDM_EINVAL and keeps the old set. */
 int rdm_set_params(rdm_handle *h, const rdm_params *p);
 
 /* ---- problem definition ------------------------------------------------ */
