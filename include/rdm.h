@@ -154,6 +154,12 @@ typedef struct {
                                size in {16, 32, 64} and keeps the fastest for this and later solves
                                of that shape, whatever values are uploaded (rdm_info.block_size,
                                probe_ms); setting parameters forgets the choice; 0: off */
+    int32_t split_directions; /* 1: the field directions are solved one after another (each solve holds
+                               P0 and one P1 instead of P0 and every P1: about half the device memory
+                               at three directions, for a repeated X0 recursion); the results, alpha
+                               with its cross terms included, are those of the joint solve up to the
+                               stopping tolerance.  Not with an overlap matrix (RDM_EINVAL at the
+                               solve).  0: off */
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -227,7 +233,8 @@ int rdm_default_params(rdm_params *p);
 /* Set the solve parameters.  Validated: tau >= 0, tol >= 0, max_iter >= 1, a
  * known mode, refine_x1 in 0..4, refine_x0 in {0, 1, 3, 4, 5}, chunk_mb >= 0,
  * use_graphs == 0, stall_window >= 0, block_size 0 or a power of two up to 64,
- * autotune 0 or 1; anything else returns RDM_EINVAL and keeps the old set. */
+ * autotune and split_directions 0 or 1; anything else returns RDM_EINVAL and
+ * keeps the old set. */
 int rdm_set_params(rdm_handle *h, const rdm_params *p);
 
 /* ---- problem definition ------------------------------------------------ */

@@ -93,6 +93,7 @@ struct rdm_handle {
     int NB = 0;
     int nd = 0;
     int dirs[3] = {0, 0, 0};
+    int dir_only = -1;          // >= 0: assemble only this field direction (split_directions)
     std::vector<int> row0, nbs, norb;
     MatSet H0, H1;
     MatSet Sm;                  // overlap matrices (non-orthogonal basis), when uploaded
@@ -328,7 +329,7 @@ void assemble(rdm_handle *h) {
     // directions: the set uploaded for system 0; every system must match
     int nd = 0;
     for (int d = 0; d < 3; ++d)
-        if (h->hs[0].has_h1[d]) h->dirs[nd++] = d;
+        if (h->hs[0].has_h1[d] && (h->dir_only < 0 || d == h->dir_only)) h->dirs[nd++] = d;
     for (int s = 1; s < S; ++s)
         for (int d = 0; d < 3; ++d)
             if (h->hs[s].has_h1[d] != h->hs[0].has_h1[d])
@@ -1105,6 +1106,30 @@ void lowdin_back(rdm_handle *h) {
     concat(h, {{&out, 0, out.nmat}}, X);
 }
 
+// alpha[g][d] = -spin <P1_d, H1_g> (Eq. polar) for every pair of the solved
+// directions, from the result set (P0, P1_1..P1_nd) and the H1 set
+void compute_alpha(rdm_handle *h) {
+    const int S = h->S, NB = h->NB, nd = h->nd, b = h->bs;
+    cudaStream_t st = h->stream;
+    MatSet &Xf = h->X[h->cur];
+    h->alpha.assign((size_t)S * 9, NAN);
+    if (!nd) return;
+    const int nq = nd * nd;
+    h->row_part.ensure((size_t)nq * NB);
+    h->sys_q.ensure((size_t)nq * S);
+    launch_row_dots(Xf.row_ptr.p + NB, Xf.col.p, Xf.val.p, nd, h->H1.row_ptr.p, h->H1.col.p, h->H1.val.p, nd, NB, b,
+                    h->row_part.p, st);
+    launch_sys_sum(h->row_part.p, nq, NB, h->sd.row0.p, h->sd.nbs.p, S, h->sys_q.p, st);
+    std::vector<double> dq((size_t)nq * S);
+    d2h(dq.data(), h->sys_q.p, dq.size(), st);
+    sync(h);
+    for (int s = 0; s < S; ++s)
+        for (int g = 0; g < nd; ++g)
+            for (int d = 0; d < nd; ++d)
+                h->alpha[(size_t)s * 9 + 3 * h->dirs[g] + h->dirs[d]] =
+                    -h->prm.spin_factor * dq[(size_t)s * nq + g * nd + d];
+}
+
 int run_solve(rdm_handle *h, rdm_info *info_out) {
     DeviceGuard dg(h->device);
     if (h->hs.empty()) return fail(h, RDM_ESTATE, "no system uploaded");
@@ -1348,23 +1373,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
 
     // polarizability: alpha[g][d] = -spin * <P1_d, H1_g>
     MatSet &Xf = h->X[h->cur];
-    h->alpha.assign((size_t)S * 9, NAN);
-    if (nd) {
-        const int nq = nd * nd;
-        h->row_part.ensure((size_t)nq * NB);
-        h->sys_q.ensure((size_t)nq * S);
-        launch_row_dots(Xf.row_ptr.p + NB, Xf.col.p, Xf.val.p, nd, h->H1.row_ptr.p, h->H1.col.p,
-                        h->H1.val.p, nd, NB, b, h->row_part.p, st);
-        launch_sys_sum(h->row_part.p, nq, NB, h->sd.row0.p, h->sd.nbs.p, S, h->sys_q.p, st);
-        std::vector<double> dq((size_t)nq * S);
-        d2h(dq.data(), h->sys_q.p, dq.size(), st);
-        sync(h);
-        for (int s = 0; s < S; ++s)
-            for (int g = 0; g < nd; ++g)
-                for (int d = 0; d < nd; ++d)
-                    h->alpha[(size_t)s * 9 + 3 * h->dirs[g] + h->dirs[d]] =
-                        -P.spin_factor * dq[(size_t)s * nq + g * nd + d];
-    }
+    compute_alpha(h);
     // final pattern on the host for the getters, summary per system
     h->final_rp.resize((size_t)Xf.nmat * NB + 1);
     d2h(h->final_rp.data(), Xf.row_ptr.p, h->final_rp.size(), st);
@@ -1440,6 +1449,93 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     return all_conv ? RDM_OK : RDM_NOT_CONVERGED;
 }
 
+// split_directions: the field directions one after another, each a solve
+// with that H1 alone (the X set then holds P0 and one P1, about halving the
+// solve's device memory at three directions; the X0 recursion is repeated),
+// then the result set P0, P1_x, P1_y, P1_z and every alpha component
+// (cross terms <P1_d, H1_g> included).  The summary adds up the passes'
+// times and work; iterations and convergence are the worst pass's.
+int run_solve(rdm_handle *h, rdm_info *info_out);
+int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
+    int all[3], na = 0;
+    if (!h->hs.empty())
+        for (int d = 0; d < 3; ++d)
+            if (h->hs[0].has_h1[d]) all[na++] = d;
+    if (!h->prm.split_directions || na <= 1) return run_solve(h, info_out);
+    const int S = h->S;
+    for (int s = 0; s < S; ++s)
+        if (h->hs[s].has_s) return fail(h, RDM_EINVAL, "split_directions does not take an overlap matrix");
+    MatSet p0, p1[3], h1[3];
+    std::vector<rdm_info> acc;
+    std::vector<rdm_iter_log> log0;
+    int status = RDM_OK;
+    for (int k = 0; k < na; ++k) {
+        h->dir_only = all[k];
+        int st;
+        try {
+            st = run_solve(h, nullptr);
+        } catch (...) {
+            h->dir_only = -1;
+            throw;
+        }
+        h->dir_only = -1;
+        if (st < 0) return st;
+        if (st == RDM_NOT_CONVERGED) status = st;
+        MatSet &X = h->X[h->cur];
+        if (k == 0) {
+            concat(h, {{&X, 0, 1}}, p0);
+            acc = h->info;
+            log0 = h->log;
+        } else {
+            for (int s = 0; s < S; ++s) {
+                rdm_info &A = acc[s];
+                const rdm_info &I = h->info[s];
+                A.iterations = std::max(A.iterations, I.iterations);
+                A.converged = A.converged && I.converged;
+                A.time_ms += I.time_ms;
+                A.useful_flops += I.useful_flops;
+                A.issued_flops += I.issued_flops;
+                for (int q = 0; q < 8; ++q) A.kernel_ms[q] += I.kernel_ms[q];
+                for (int q = 0; q < 5; ++q) A.kernel_flops[q] += I.kernel_flops[q];
+                A.kernel_launches += I.kernel_launches;
+                A.tc_launches += I.tc_launches;
+                A.oz_launches += I.oz_launches;
+                A.simt_launches += I.simt_launches;
+                A.numeric_bytes += I.numeric_bytes;
+                A.device_bytes_peak = std::max(A.device_bytes_peak, I.device_bytes_peak);
+                A.product_groups = std::max(A.product_groups, I.product_groups);
+            }
+        }
+        for (int s = 0; s < S; ++s) acc[s].nnzb_p1[all[k]] = h->info[s].nnzb_p1[all[k]];
+        concat(h, {{&X, 1, 1}}, p1[k]);
+        concat(h, {{&h->H1, 0, 1}}, h1[k]);
+    }
+    // the result set and the H1 set of every direction
+    h->nd = na;
+    for (int k = 0; k < na; ++k) h->dirs[k] = all[k];
+    MatSet &X = h->X[h->cur];
+    X.release();
+    h->H1.release();
+    if (na == 2) {
+        concat(h, {{&p0, 0, 1}, {&p1[0], 0, 1}, {&p1[1], 0, 1}}, X);
+        concat(h, {{&h1[0], 0, 1}, {&h1[1], 0, 1}}, h->H1);
+    } else {
+        concat(h, {{&p0, 0, 1}, {&p1[0], 0, 1}, {&p1[1], 0, 1}, {&p1[2], 0, 1}}, X);
+        concat(h, {{&h1[0], 0, 1}, {&h1[1], 0, 1}, {&h1[2], 0, 1}}, h->H1);
+    }
+    p0.release();
+    for (int k = 0; k < 3; ++k) { p1[k].release(); h1[k].release(); }
+    compute_alpha(h);
+    h->final_rp.resize((size_t)X.nmat * h->NB + 1);
+    d2h(h->final_rp.data(), X.row_ptr.p, h->final_rp.size(), h->stream);
+    sync(h);
+    h->info = acc;
+    h->log = log0;
+    h->conv.assign((size_t)S * 4, {});
+    if (info_out) *info_out = h->info[0];
+    return status;
+}
+
 // Free the solve's work buffers and matrix sets (the uploaded matrices stay):
 // between autotuning probes at different block sizes, whose grow-only buffers
 // would otherwise add up.
@@ -1500,7 +1596,7 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
             try {
                 for (int sy = 0; sy < h->S; ++sy)
                     if (h->hs[sy].has_h0) ensure_reblocked(h, sy, cand[k]);   // outside the timed solve
-                st = run_solve(h, nullptr);
+                st = run_solve_dirs(h, nullptr);
             } catch (const Error &e) {
                 st = e.code;
                 h->err = e.msg;
@@ -1529,7 +1625,7 @@ int solve_entry(rdm_handle *h, rdm_info *info_out) {
         const int want = P.autotune ? h->tuned_b : P.block_size > 0 ? P.block_size : h->b;
         if (P.autotune && h->bs != want) release_work(h);
         h->bs = want;
-        status = run_solve(h, nullptr);
+        status = run_solve_dirs(h, nullptr);
         if (status < 0) return status;
     }
     for (auto &I : h->info) {
@@ -1721,10 +1817,12 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
         !(p->spin_factor > 0) || p->min_iter < 0 || p->refine_x1 < 0 || p->refine_x1 > 4 ||
         p->refine_x0 < 0 || p->refine_x0 > 5 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
         p->use_graphs != 0 || p->stall_window < 0 || p->block_size < 0 || p->block_size > 64 ||
-        (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1)
+        (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1 || p->split_directions < 0 ||
+        p->split_directions > 1)
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
                                    "refine_x1 0..4, refine_x0 0, 1, 3, 4 or 5, chunk_mb >= 0, use_graphs 0, "
-                                   "stall_window >= 0, block_size 0 or a power of two <= 64, autotune 0 or 1)");
+                                   "stall_window >= 0, block_size 0 or a power of two <= 64, autotune and "
+                                   "split_directions 0 or 1)");
     if (!tc_block_ok(p->mode, p->autotune ? 32 : p->block_size > 0 ? p->block_size : h->b))
         return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, "
                                    "32 x 32 or 64 x 64 blocks (the uploaded matrices have b = " + std::to_string(h->b) +

@@ -12,6 +12,7 @@ import pytest
 
 from oracle import exact_response, polarizability
 from synth import make_cluster
+from blockcheck import max_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -112,3 +113,48 @@ def test_stall_window_sets_when_the_ladder_moves_on(rdm, exact_alpha):
         tiers[w] = info.tier_iters[0]
         assert np.max(np.abs(sol.alpha() - exact_alpha)) / np.max(np.abs(exact_alpha)) <= 1e-6
     assert tiers[4] >= tiers[2]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed_fp16"])
+def test_split_directions_match_the_joint_solve(rdm, mode):
+    """split_directions: each field direction solved on its own (P0 and one P1
+    in the X set), then P0, every P1 and every alpha component, cross terms
+    included.  Against the joint solve of the same batch (two systems, two
+    directions and three directions)."""
+    from synth import make_chain
+    for dirs in (("x", "z"), ("x", "y", "z")):
+        systems = [make_cluster(60, opa=8, b=32, cutoff=10.0, seed=41, dirs=dirs),
+                   make_chain(30, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=42, dirs=dirs)]
+        res = []
+        for split in (0, 1):
+            sol = rdm.Solver(0)
+            sol.set_params(tau=1e-6, tol=1e-9, mode=mode, max_iter=100, split_directions=split)
+            sol.load(systems)
+            code, info = sol.solve()
+            assert code == rdm.RDM_OK and info.converged
+            res.append(([sol.alpha(k) for k in range(2)], [sol.p0(k).to_dense() for k in range(2)],
+                        [[sol.p1(k, "xyz".index(d)).to_dense() for d in dirs] for k in range(2)],
+                        sol.info(1)))
+        tol = 1e-8 if mode == "fp64" else 1e-6
+        for k in range(2):
+            a0, a1 = res[0][0][k], res[1][0][k]
+            m = ~np.isnan(a0)
+            assert np.array_equal(m, ~np.isnan(a1)) and m.sum() == len(dirs) ** 2
+            assert np.max(np.abs(a1[m] - a0[m])) / np.max(np.abs(a0[m])) <= tol
+            assert max_rel_err(res[1][1][k], res[0][1][k]) <= tol
+            for q in range(len(dirs)):
+                assert max_rel_err(res[1][2][k][q], res[0][2][k][q]) <= 100 * tol
+        # the summary adds up the passes
+        assert res[1][3].time_ms > 0 and res[1][3].tc_launches >= res[0][3].tc_launches
+
+
+def test_split_directions_refuse_an_overlap(rdm):
+    from synth import make_overlap
+    s = make_cluster(40, opa=8, b=32, cutoff=10.0, seed=12, dirs=("x", "y"))
+    s.s = make_overlap(s)
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, mode="fp64", split_directions=1)
+    sol.load(s)
+    with pytest.raises(rdm.RdmError) as e:
+        sol.solve()
+    assert e.value.code == rdm.RDM_EINVAL
