@@ -1450,12 +1450,13 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
 }
 
 // split_directions: the field directions one after another, each a solve
-// with that H1 alone (the X set then holds P0 and one P1, about halving the
-// solve's device memory at three directions; the X0 recursion is repeated),
+// with that H1 alone from freed work buffers (the X sets then hold P0 and one
+// P1; the X0 recursion is repeated),
 // then the result set P0, P1_x, P1_y, P1_z and every alpha component
 // (cross terms <P1_d, H1_g> included).  The summary adds up the passes'
 // times and work; iterations and convergence are the worst pass's.
 int run_solve(rdm_handle *h, rdm_info *info_out);
+void release_work(rdm_handle *h);
 int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
     int all[3], na = 0;
     if (!h->hs.empty())
@@ -1470,6 +1471,9 @@ int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
     std::vector<rdm_iter_log> log0;
     int status = RDM_OK;
     for (int k = 0; k < na; ++k) {
+        // the passes share nothing but the saved results: each starts from
+        // freed work buffers and matrix sets
+        if (k > 0) release_work(h);
         h->dir_only = all[k];
         int st;
         try {
@@ -1511,11 +1515,10 @@ int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
         concat(h, {{&h->H1, 0, 1}}, h1[k]);
     }
     // the result set and the H1 set of every direction
+    release_work(h);
     h->nd = na;
     for (int k = 0; k < na; ++k) h->dirs[k] = all[k];
     MatSet &X = h->X[h->cur];
-    X.release();
-    h->H1.release();
     if (na == 2) {
         concat(h, {{&p0, 0, 1}, {&p1[0], 0, 1}, {&p1[1], 0, 1}}, X);
         concat(h, {{&h1[0], 0, 1}, {&h1[1], 0, 1}}, h->H1);
@@ -1532,6 +1535,7 @@ int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
     h->info = acc;
     h->log = log0;
     h->conv.assign((size_t)S * 4, {});
+    h->solved = true;
     if (info_out) *info_out = h->info[0];
     return status;
 }
