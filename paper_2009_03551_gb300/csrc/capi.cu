@@ -17,7 +17,9 @@
 #include <exception>
 #include <memory>
 #include <new>
+#include <mutex>
 #include <numeric>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -28,6 +30,17 @@
 using namespace rdm;
 
 long long rdm::g_kernel_launches = 0;
+
+void rdm::func_smem_once(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    RDM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({func, dev})) return;
+    RDM_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.insert({func, dev});
+}
 
 namespace {
 

@@ -202,12 +202,7 @@ void launch_compact_copy(const CompactArgs &c, int d1, cudaStream_t st) {
     RDM_LAUNCH_CHECK();
     if (d1 <= c.d0) return;
     const size_t smem = (size_t)c.b * (c.b + 1) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_compact_vals, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          64 * 65 * (int)sizeof(double)));
-        attr = true;
-    }
+    func_smem_once((const void *)k_compact_vals, 64 * 65 * (int)sizeof(double));
     const int grid = (int)std::min<int64_t>((int64_t)d1 - c.d0, 152 * 16);
     k_compact_vals<<<grid, 128, smem, st>>>(c, d1);
     RDM_LAUNCH_CHECK();

@@ -367,12 +367,7 @@ void launch_b(const NumArgs &a, cudaStream_t st) {
     size_t smem = (size_t)B * LD * sizeof(double);
     size_t ab = 2 * (size_t)B * LD * sizeof(T);
     if (ab > smem) smem = ab;
-    static bool attr = false;
-    if (!attr) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_numeric_simt<B, T>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    func_smem_once((const void *)k_numeric_simt<B, T>, (int)smem);
     static int resident = 0;
     if (!resident) {
         int per_sm = 0, dev = 0, nsm = 0;

@@ -482,11 +482,7 @@ double launch_numeric_oz(const NumArgs &a, const MatSet &in, const int *mcol, Oz
     A.out_val = a.out_val; A.out_nrm = a.out_nrm; A.keep = a.keep; A.uidx = a.uidx; A.u0 = a.u0;
     A.err = w.counters.p;
     A.wait_cycles = w.knobs.wait_cycles > 0 ? w.knobs.wait_cycles : kWaitCycles;
-    static bool attr = false;
-    if (!attr) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem));
-        attr = true;
-    }
+    func_smem_once((const void *)k_tc_oz, (int)kOzSmem);
     const int grid = plan.ntile < nsm ? plan.ntile : nsm;
     k_tc_oz<<<grid, kOzThreads, kOzSmem, st>>>(A);
     RDM_LAUNCH_CHECK();

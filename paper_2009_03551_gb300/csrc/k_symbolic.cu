@@ -449,14 +449,8 @@ void launch_symbolic(const MatSet &in, const JobTable &jt, const SysDev &sd, int
     P.sys_of_row = sd.sys_of_row.p; P.row0 = sd.row0.p; P.nbs = sd.nbs.p;
     P.c_lin = sd.c_lin.p; P.c_sq = sd.c_sq.p; P.tau0 = sd.tau0.p; P.tau1 = sd.tau1.p;
     P.active = sd.active.p; P.so = so;
-    static bool attr_set = false;
-    if (!attr_set) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kSymMaxNs * 12));
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_symbolic_hash, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kHashSlots * 16));
-        attr_set = true;
-    }
+    func_smem_once((const void *)k_symbolic, kSymMaxNs * 12);
+    func_smem_once((const void *)k_symbolic_hash, kHashSlots * 16);
     if (max_ns <= kSymMaxNs) {
         size_t smem = (size_t)max_ns * (sizeof(unsigned long long) + sizeof(unsigned int));
         k_symbolic<<<dim3(in.NB, jt.njob), kSymThreads, smem, st>>>(P);

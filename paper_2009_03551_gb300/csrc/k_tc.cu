@@ -862,12 +862,7 @@ double launch_tc(const NumArgs &a, const MatSet &in, const JobTable &jt, Arith a
     A.hold = w.knobs.hold;
     A.runs = w.tpos_valid ? 1 : 0;
     A.pre_err = w.pre_err.p;
-    static bool attr = false;
-    if (!attr) {
-        RDM_CUDA_TRY(cudaFuncSetAttribute(k_tc_bf16x3<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_bytes<B>()));
-        attr = true;
-    }
+    func_smem_once((const void *)k_tc_bf16x3<B>, (int)smem_bytes<B>());
     const int grid = plan.ntile < nsm ? plan.ntile : nsm;
     k_tc_bf16x3<B><<<grid, kThreads, smem_bytes<B>(), st>>>(A);
     RDM_LAUNCH_CHECK();

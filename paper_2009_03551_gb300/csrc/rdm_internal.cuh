@@ -51,6 +51,11 @@ extern long long g_kernel_launches;
         RDM_CUDA_TRY(cudaGetLastError());       \
     } while (0)
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize of kernel `func`, set once per
+// kernel and device (the attribute is per device; handles of one process may
+// use several, and solves may run on worker threads)
+void func_smem_once(const void *func, int bytes);
+
 // device bytes held by all DevBufs of the process (current and high-water mark)
 inline std::atomic<size_t> g_dev_bytes{0};
 inline std::atomic<size_t> g_dev_bytes_peak{0};
