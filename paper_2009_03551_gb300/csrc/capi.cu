@@ -29,7 +29,7 @@
 
 using namespace rdm;
 
-long long rdm::g_kernel_launches = 0;
+thread_local long long rdm::g_kernel_launches = 0;
 
 void rdm::func_smem_once(const void *func, int bytes) {
     static std::mutex mu;

@@ -44,7 +44,7 @@ struct Error {
 
 // every kernel launch of the library goes through RDM_LAUNCH_CHECK, which
 // also counts it (the count is reported per solve in rdm_info)
-extern long long g_kernel_launches;
+extern thread_local long long g_kernel_launches;   // launches of this thread (a solve runs on one thread)
 #define RDM_LAUNCH_CHECK()                      \
     do {                                        \
         ++::rdm::g_kernel_launches;             \
