@@ -60,8 +60,8 @@ def tc_flops_per_kstep(b):
 PROFILED_TRAFFIC = {
     "tc": {"file": ["paper_2009_03551_gb300/csrc/k_tc.cu", "paper_2009_03551_gb300/csrc/tc_ptx.cuh",
                     "paper_2009_03551_gb300/csrc/tc_plan.cuh"],
-           "sha256": "100cfde25d20991afd59443e1969267261bb1e31801d1ba6a64efad23d42ab55",
-           "bytes_per_unit": 15080.0, "unit": "K-step", "b": 32,
+           "sha256": "db478c16abca005fcca1f40d0b5bf63327422468ad2a3836d58b99a077079b46",
+           "bytes_per_unit": 15071.0, "unit": "K-step", "b": 32,
            "capture": "profiles/k_tc_bf16x3_dram_cluster1000.md"},
     "ff": {"file": "paper_2009_03551_gb300/csrc/k_numeric.cu",
            "sha256": "1c9d3e76e36659e5d06b0d237474522761ebecc2732c37eb20f037dc4adcb12e",
