@@ -158,3 +158,13 @@ def test_split_directions_refuse_an_overlap(rdm):
     with pytest.raises(rdm.RdmError) as e:
         sol.solve()
     assert e.value.code == rdm.RDM_EINVAL
+
+
+def test_split_directions_parameter_is_validated(rdm):
+    sol = rdm.Solver(0)
+    for bad in (2, -1):
+        with pytest.raises(rdm.RdmError) as e:
+            sol.set_params(tau=1e-6, mode="fp64", split_directions=bad)
+        assert e.value.code == rdm.RDM_EINVAL
+    sol.set_params(tau=1e-6, mode="fp64", split_directions=1)
+    sol.close()
