@@ -65,7 +65,7 @@ extern "C" {
                                     (tcgen05, FP32 accumulate) until the idempotency
                                     error stalls, then a final tier: X0^2 FP64-class
                                     (RDM_REFINE_SLICES for 32 x 32 blocks, else FP64),
-                                    the first-order products in FP64 (refine_x0 /
+                                    the first-order products still split (refine_x0 /
                                     refine_x1 choose otherwise) */
 #define RDM_MODE_MIXED_FP16  3   /* the same with fp16 hi+lo operands, each matrix scaled
                                     by a power of two into fp16's normal range
@@ -76,8 +76,8 @@ extern "C" {
                                     first-order products still split */
 
 /* ---- final-tier arithmetic of the first-order products (rdm_params.refine_x1) */
-#define RDM_REFINE_DEFAULT   0   /* refine_x1: the split product for RDM_MODE_MIXED_FP16, FP64 for
-                                    RDM_MODE_MIXED_BF16; refine_x0: see rdm_params */
+#define RDM_REFINE_DEFAULT   0   /* refine_x1: the split product (both mixed modes);
+                                    refine_x0: see rdm_params */
 #define RDM_REFINE_FP64      1
 #define RDM_REFINE_SPLIT     2   /* keep the tensor-core split product */
 #define RDM_REFINE_FP32      3   /* FP32 on the CUDA cores (round-to-nearest accumulation) */

@@ -505,14 +505,17 @@ bool tc_block_ok(int mode, int b) {
 // stay split: with the segmented accumulation of the tensor-core kernel they
 // are as accurate as FP32 CUDA-core products).  The bf16 ladder: bf16 split
 // products (16 bits), then the final tier (X0^2 as for fp16, the first-order
-// products in FP64 by default).  A three-tier bf16 ladder with an FP32 tier
-// between (X1 in FP32 on the CUDA cores through both later tiers) was measured
-// and left 2e-6 in alpha on a 90-atom cluster where this one leaves 1e-6.
+// products still bf16 split: alpha's error is the bulk tier's rotation of the
+// occupied subspace, and FP64 first-order products in the final tier gave the
+// same alpha at 11 times the solve time).  A three-tier bf16 ladder with an
+// FP32 tier between (X1 in FP32 on the CUDA cores through both later tiers)
+// was measured and left 2e-6 in alpha on a 90-atom cluster where this one
+// leaves 1e-6.
 int final_tier_of(int mode) { return mode == RDM_MODE_MIXED_BF16 || mode == RDM_MODE_MIXED_FP16 ? 1 : 0; }
 
 void tier_arith(int mode, int tier, int njob, Arith *ar, int refine_x1 = 0, int refine_x0 = 0, int b = 32) {
     const bool bf16 = mode == RDM_MODE_MIXED_BF16;
-    if (refine_x1 == RDM_REFINE_DEFAULT) refine_x1 = bf16 ? RDM_REFINE_FP64 : RDM_REFINE_SPLIT;
+    if (refine_x1 == RDM_REFINE_DEFAULT) refine_x1 = RDM_REFINE_SPLIT;
     if (refine_x0 == RDM_REFINE_DEFAULT) refine_x0 = b == 32 ? RDM_REFINE_SLICES : RDM_REFINE_FP64;
     const int final_tier = final_tier_of(mode);
     for (int p = 0; p < njob; ++p) {

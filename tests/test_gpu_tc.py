@@ -296,8 +296,8 @@ def test_mixed_batch_with_converged_copies(rdm):
     code, info = sol.solve()
     assert code == rdm.RDM_OK
     # the chain's alpha carries the dipole range (|x| up to 55 bohr) as an error
-    # amplifier: the 16-bit bf16 split reaches ~3e-6 there (the CPU emulation
-    # of the same split gives 2.9e-6), the cluster 1e-6
+    # amplifier: the 16-bit bf16 split reaches ~2e-6 there (the CPU emulation
+    # of the same split gives 2.9e-6), the cluster 8e-7
     tol = [5e-6, 1e-6]
     for k, s in enumerate(systems):
         one = rdm.Solver(0)
@@ -318,6 +318,30 @@ def test_mixed_batch_with_converged_copies(rdm):
         one.solve()
         a1, a0 = sol.alpha(k), one.alpha()
         assert np.max(np.abs(a1 - a0)) / np.max(np.abs(a0)) <= 1e-6
+
+
+def test_bf16_final_tier_keeps_the_first_order_products_split(rdm, cluster150, oracle150):
+    """The bf16 ladder's final tier refines X0^2 (slice products) and keeps the
+    first-order products as bf16 split products by default: no FP64 products
+    at all, alpha within 1e-6 of the oracle and within 5e-7 of the same ladder
+    with FP64 first-order products in the final tier (the bulk tier's error
+    dominates both)."""
+    s = cluster150
+    ob, h1s = oracle150
+    ao = polarizability(ob.p1s, h1s)
+    out = {}
+    for r1 in (0, 1):
+        sol = rdm.Solver(0)
+        sol.set_params(tau=1e-6, tol=1e-9, mode="mixed_bf16", max_iter=100, refine_x1=r1)
+        sol.load(s)
+        code, info = sol.solve()
+        assert code == rdm.RDM_OK and info.converged
+        assert info.tier_iters[0] > 0 and info.tier_iters[1] > 0
+        out[r1] = (sol.alpha().copy(), info)
+    (a_split, i_split), (a_64, i_64) = out[0], out[1]
+    assert i_split.kernel_flops[1] == 0.0 and i_64.kernel_flops[1] > 0
+    assert np.max(np.abs(a_split - ao)) / np.max(np.abs(ao)) <= 1e-6
+    assert np.max(np.abs(a_split - a_64)) / np.max(np.abs(a_64)) <= 5e-7
 
 
 @pytest.mark.parametrize("b", [16, 64])
