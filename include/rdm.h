@@ -160,6 +160,17 @@ typedef struct {
                                with its cross terms included, are those of the joint solve up to the
                                stopping tolerance.  Not with an overlap matrix (RDM_EINVAL at the
                                solve).  0: off */
+    int32_t correct;        /* 1: after the solve, correct P0 and P1 for the residuals of their
+                               defining conditions (Sec. 2.1: [H0, P0] = 0 and, with P1 occupied-
+                               virtual, [H0, P1] + [H1, P0] = 0) by two more solves of the same
+                               mode: the error of P0 is the response to H'0 = [[H0, P0], P0], that
+                               of P1, with the corrected P0, the response to H'1 = [R1, P0], R1 the
+                               residual; the H' are formed by FP64-class block products (double-
+                               FP32 at b = 32, else FP64) with a filter of tau / 1000.  Removes the
+                               rounding error of the reduced-precision tiers (the rotation of the
+                               occupied subspace they leave); costs the two response solves and
+                               about 3 + 5 nd FP64-class products.  Not with an overlap matrix or
+                               split_directions (RDM_EINVAL).  0: off */
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */
@@ -198,6 +209,10 @@ typedef struct {
     double  probe_ms[3];       /* device time of the probe solve at b = 16, 32, 64 (0: not probed) */
     int32_t lowdin_iterations; /* Newton-Schulz iterations for S^(-1/2) (0: orthogonal basis) */
     int32_t oz_launches;       /* launches of the tensor-core slice-product kernel */
+    double  correction_ms;     /* wall time of the correction (rdm_params.correct; included in
+                                  time_ms; 0: off); the other fields describe the solve before it,
+                                  except the summary of P0 and P1 (trace, idempotency, band energy,
+                                  nnzb), which is that of the corrected matrices */
 } rdm_info;
 
 /* One record per iteration (rdm_get_log). */
@@ -233,8 +248,8 @@ int rdm_default_params(rdm_params *p);
 /* Set the solve parameters.  Validated: tau >= 0, tol >= 0, max_iter >= 1, a
  * known mode, refine_x1 in 0..4, refine_x0 in {0, 1, 3, 4, 5}, chunk_mb >= 0,
  * use_graphs == 0, stall_window >= 0, block_size 0 or a power of two up to 64,
- * autotune and split_directions 0 or 1; anything else returns RDM_EINVAL and
- * keeps the old set. */
+ * autotune, split_directions and correct 0 or 1, not both of the last two;
+ * anything else returns RDM_EINVAL and keeps the old set. */
 int rdm_set_params(rdm_handle *h, const rdm_params *p);
 
 /* ---- problem definition ------------------------------------------------ */

@@ -107,6 +107,8 @@ struct rdm_handle {
     int nd = 0;
     int dirs[3] = {0, 0, 0};
     int dir_only = -1;          // >= 0: assemble only this field direction (split_directions)
+    bool keep_assembled = false;  // run_solve starts from the current H0, H1 (the correction's response solves)
+    std::vector<int> stop_at;     // non-empty: system s stops after stop_at[s] updates (the same)
     std::vector<int> row0, nbs, norb;
     MatSet H0, H1;
     MatSet Sm;                  // overlap matrices (non-orthogonal basis), when uploaded
@@ -971,11 +973,12 @@ void concat(rdm_handle *h, std::initializer_list<SetRange> parts, MatSet &out) {
     launch_block_norms(out.val.p, out.nrm.p, total, b, h->stream);
 }
 
-// every job of jt, C = c_lin X + c_sq (A B [+ B A]), in FP64 for every system
-void fp64_products(rdm_handle *h, MatSet &in, const JobTable &jt, double c_lin, double c_sq, double tau,
-                   MatSet &out) {
+// every job of jt, C = c_lin X + c_sq (A B [+ B A]) with per-system
+// coefficients, in arithmetic `ar`, for every system
+void set_products(rdm_handle *h, MatSet &in, const JobTable &jt, const std::vector<double> &cl,
+                  const std::vector<double> &cq, double tau, Arith ar, MatSet &out) {
     const int S = h->S;
-    std::vector<double> cl(S, c_lin), cq(S, c_sq), t(S, tau);
+    std::vector<double> t(S, tau);
     std::vector<int> one(S, 1), zero(S, 0);
     h2d(h->sd.c_lin.p, cl.data(), S, h->stream);
     h2d(h->sd.c_sq.p, cq.data(), S, h->stream);
@@ -984,12 +987,39 @@ void fp64_products(rdm_handle *h, MatSet &in, const JobTable &jt, double c_lin, 
     h2d(h->sd.active.p, one.data(), S, h->stream);
     h2d(h->sd.tier.p, zero.data(), S, h->stream);
     Arith tab[kMaxTiers][kMaxJobs];
-    for (int p = 0; p < kMaxJobs; ++p) tab[0][p] = AR_FP64;
+    for (int p = 0; p < kMaxJobs; ++p) tab[0][p] = ar;
     multiply(h, in, out, jt, tab, 1u);
+}
+
+// the same with one coefficient pair, in FP64
+void fp64_products(rdm_handle *h, MatSet &in, const JobTable &jt, double c_lin, double c_sq, double tau,
+                   MatSet &out) {
+    set_products(h, in, jt, std::vector<double>(h->S, c_lin), std::vector<double>(h->S, c_sq), tau, AR_FP64, out);
+}
+
+// FP64-class products: double-FP32 at b = 32 (about 46 bits), FP64 otherwise
+void fp64_class_products(rdm_handle *h, MatSet &in, const JobTable &jt, const std::vector<double> &cl,
+                         const std::vector<double> &cq, double tau, MatSet &out) {
+    set_products(h, in, jt, cl, cq, tau, h->bs == 32 ? AR_FF : AR_FP64, out);
 }
 
 // Job: out p = c_lin X_x + c_sq (A B + B A), or A A (a == b, one term)
 Job sym_job(int out, int x, int a, int b) { return a == b ? Job{out, x, 1, {a, a}, {a, a}, 0} : Job{out, x, 2, {a, b}, {b, a}, 0}; }
+
+// identity matrix of the batch layout: diagonal blocks only
+void make_identity(rdm_handle *h, MatSet &I) {
+    const int NB = h->NB, b = h->bs;
+    std::vector<int> rp(NB + 1), col(NB);
+    for (int i = 0; i <= NB; ++i) rp[i] = i;
+    for (int i = 0; i < NB; ++i) col[i] = i;
+    I.nmat = 1; I.NB = NB; I.b = b; I.total = NB; I.nnzb.assign(1, NB);
+    I.row_ptr.ensure(NB + 1); I.col.ensure(std::max(NB, 1)); I.val.ensure((size_t)std::max(NB, 1) * b * b);
+    I.nrm.ensure(std::max(NB, 1));
+    h2d(I.row_ptr.p, rp.data(), rp.size(), h->stream);
+    h2d(I.col.p, col.data(), col.size(), h->stream);
+    launch_identity_blocks(I.val.p, NB, b, h->stream);
+    launch_block_norms(I.val.p, I.nrm.p, NB, b, h->stream);
+}
 
 // M -> Z M Z for the k matrices of `ms` (Z = S^(-1/2), L = Z^2 = S^(-1)), with
 // products of symmetric matrices only:  Z M Z = (Z K + K Z)/2 - (L M + M L)/2,
@@ -1044,18 +1074,7 @@ void lowdin_forward(rdm_handle *h) {
     launch_scale_sys(Y.row_ptr.p, Y.col.p, Y.val.p, NB, b, h->sd.sys_of_row.p, h->sd.row0.p, h->sd.n_orb.p, fac.p, 1,
                      Y.val.p, st);
     launch_block_norms(Y.val.p, Y.nrm.p, Y.total, b, st);
-    {   // identity: diagonal blocks only
-        std::vector<int> rp(NB + 1), col(NB);
-        for (int i = 0; i <= NB; ++i) rp[i] = i;
-        for (int i = 0; i < NB; ++i) col[i] = i;
-        I.nmat = 1; I.NB = NB; I.b = b; I.total = NB; I.nnzb.assign(1, NB);
-        I.row_ptr.ensure(NB + 1); I.col.ensure(std::max(NB, 1)); I.val.ensure((size_t)std::max(NB, 1) * b * b);
-        I.nrm.ensure(std::max(NB, 1));
-        h2d(I.row_ptr.p, rp.data(), rp.size(), st);
-        h2d(I.col.p, col.data(), col.size(), st);
-        launch_identity_blocks(I.val.p, NB, b, st);
-        launch_block_norms(I.val.p, I.nrm.p, NB, b, st);
-    }
+    make_identity(h, I);
     concat(h, {{&I, 0, 1}}, Z);
     JobTable jt{};
     double prev = 1e300;
@@ -1153,8 +1172,9 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, 32 x 32 or 64 x 64 blocks");
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_kernel_launches;
-    assemble(h);
-    if (h->has_s) {
+    if (h->keep_assembled) init_x(h);
+    else assemble(h);
+    if (h->has_s && !h->keep_assembled) {
         lowdin_forward(h);   // H0, H1 to the orthogonal form (Sec. 2.2)
         init_x(h);
     }
@@ -1266,6 +1286,10 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
             y.have_eb = true;
             y.eb0 = eb0;
             for (int d = 0; d < nd; ++d) y.eb1[d] = q[(size_t)s * nq + 3 + d];
+            // a response solve of the correction repeats the solve's X0
+            // recursion bit for bit (the same inputs, kernels and decisions):
+            // it takes exactly as many updates
+            if (!h->stop_at.empty()) stop = n >= h->stop_at[s];
             if (stop) {
                 y.active = false;
                 y.converged = true;
@@ -1441,7 +1465,7 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
         h->info[s].trace_error = q[(size_t)s * nq] - nocc[s];
         h->info[s].idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
     }
-    if (h->has_s) {
+    if (h->has_s && !h->keep_assembled) {
         // P0 and P1 back to the non-orthogonal basis; the summary above stays
         // that of the orthogonal form (Tr P0 = N_occ there)
         lowdin_back(h);
@@ -1465,6 +1489,222 @@ int run_solve(rdm_handle *h, rdm_info *info_out) {
     return all_conv ? RDM_OK : RDM_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------------------
+// accuracy correction (rdm_params.correct)
+// ---------------------------------------------------------------------------
+
+// per system, the largest block norm of the matrices [first, first + count) of
+// m (the norms are computed afresh: the assembled H0 and H1 sets carry none)
+std::vector<double> sys_max_norm(rdm_handle *h, const MatSet &m, int first, int count) {
+    const int NB = h->NB;
+    launch_block_norms(m.val.p, m.nrm.p, m.total, h->bs, h->stream);
+    std::vector<int> rp((size_t)m.nmat * NB + 1);
+    std::vector<float> nrm((size_t)std::max<int64_t>(m.total, 1));
+    d2h(rp.data(), m.row_ptr.p, rp.size(), h->stream);
+    if (m.total) d2h(nrm.data(), m.nrm.p, (size_t)m.total, h->stream);
+    sync(h);
+    std::vector<double> mx(h->S, 0.0);
+    for (int k = first; k < first + count; ++k)
+        for (int s = 0; s < h->S; ++s)
+            for (int i = h->row0[s]; i < h->row0[s] + h->nbs[s]; ++i)
+                for (int p = rp[(size_t)k * NB + i]; p < rp[(size_t)k * NB + i + 1]; ++p)
+                    mx[s] = std::max(mx[s], (double)nrm[p]);
+    return mx;
+}
+
+// Scale every matrix of m, per system s, by lam_s: the power of two that
+// brings the largest block norm of s's matrices nearest to ref_s (1 where
+// either is 0).  Returns lam.
+std::vector<double> scale_to(rdm_handle *h, MatSet &m, const std::vector<double> &ref) {
+    const int S = h->S, NB = h->NB, b = h->bs;
+    const std::vector<double> mx = sys_max_norm(h, m, 0, m.nmat);
+    std::vector<double> lam(S, 1.0);
+    for (int s = 0; s < S; ++s)
+        if (mx[s] > 0 && ref[s] > 0) lam[s] = std::ldexp(1.0, (int)std::lround(std::log2(ref[s] / mx[s])));
+    DevBuf<double> fac;
+    fac.ensure(S);
+    h2d(fac.p, lam.data(), S, h->stream);
+    for (int k = 0; k < m.nmat; ++k)
+        launch_scale_sys(m.row_ptr.p + (size_t)k * NB, m.col.p, m.val.p, NB, b, h->sd.sys_of_row.p, h->sd.row0.p,
+                         h->sd.n_orb.p, fac.p, 0, m.val.p, h->stream);
+    launch_block_norms(m.val.p, m.nrm.p, m.total, b, h->stream);
+    sync(h);
+    return lam;
+}
+
+// Accuracy correction of P0 and P1.  P0 is fixed by [H0, P0] = 0 with
+// P0^2 = P0, P1 by [H0, P1] + [H1, P0] = 0 with P1 = P0 P1 + P1 P0
+// (Sec. 2.1).  The reduced-precision tiers leave a small rotation of the
+// occupied subspace in P0 (purification drives eigenvalues to 0 and 1 but
+// never refers to H0 again, so it does not undo a rotation of the
+// eigenvectors) and with it an error in P1.  Both errors are first-order
+// responses to symmetric perturbations made of the residuals
+// ({A, B} = A B + B A; every product one of symmetric matrices):
+//  - P0: dP0 = dP/dH[H'0] with H'0 = [[H0, P0], P0] = 2 G0 - {P0, G0},
+//        G0 = {P0, H0} (P0 idempotent);
+//  - P1, with the corrected P0: dP1 = dP/dH[H'1] with H'1 = [R1, P0],
+//        R1 = [H0, P1] + [H1, P0]:  H'1 = 2 G - {P0, G} + {D, P1},
+//        G = {P0, H1}, D = H0 - {P0, H0}; P1 + dP1 is then projected on
+//        its occupied-virtual part 2 {P0, X} - {P0, {P0, X}}.
+// Each response is one more solve of the same mode with the H' in place of
+// H1, scaled per system by a power of two to H1's size so that the solve's
+// filter treats it as it treats H1 (a response is linear in its
+// perturbation).  The residual products are FP64-class with a filter of
+// tau / 1000: the residuals are small differences of O(1) terms.
+int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
+    if (!h->prm.correct) return run_solve(h, info_out);
+    for (const auto &y : h->hs)
+        if (y.has_s) return fail(h, RDM_EINVAL, "correct does not take an overlap matrix");
+    int status = run_solve(h, nullptr);
+    if (status < 0) return status;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int S = h->S, NB = h->NB, nd = h->nd;
+    const int dirs0[3] = {h->dirs[0], h->dirs[1], h->dirs[2]};
+    const double tc = h->prm.tau * 1e-3;
+    const std::vector<rdm_info> info0 = h->info;
+    const std::vector<rdm_iter_log> log0 = h->log;
+    h->solved = false;
+    struct Reset {
+        rdm_handle *h;
+        ~Reset() {
+            h->keep_assembled = false;
+            h->stop_at.clear();
+        }
+    } reset{h};
+    const std::vector<double> c0(S, 0.0), c1(S, 1.0), c2(S, 2.0), cm1(S, -1.0), ch(S, 0.5);
+    std::vector<double> cq(S);
+    MatSet Pt, H1s, I, A, G0, H0p, P0c, P1c;
+    concat(h, {{&h->X[h->cur], 0, 1 + nd}}, Pt);      // P0~, P1~_1..nd
+    if (nd) H1s = std::move(h->H1);
+    make_identity(h, I);
+    // the size each H' is scaled to: H1's largest block norm (H0's without H1)
+    const std::vector<double> ref = nd ? sys_max_norm(h, H1s, 0, nd) : sys_max_norm(h, h->H0, 0, 1);
+    JobTable jt{};
+
+    // P0: H'0 = 2 G0 - {P0~, G0}, G0 = {P0~, H0}; P0 = P0~ + {I, E0} / (2 lam)
+    concat(h, {{&h->H0, 0, 1}, {&Pt, 0, 1}}, A);
+    jt.njob = 1;
+    jt.job[0] = sym_job(0, -1, 0, 1);
+    fp64_class_products(h, A, jt, c0, c1, tc, G0);
+    concat(h, {{&Pt, 0, 1}, {&G0, 0, 1}}, A);
+    jt.job[0] = sym_job(0, 1, 0, 1);
+    fp64_class_products(h, A, jt, c2, cm1, tc, H0p);
+    G0.release();
+    std::vector<double> lam = scale_to(h, H0p, ref);
+    h->H1 = std::move(H0p);
+    h->nd = 1;
+    h->dirs[0] = 0;
+    h->keep_assembled = true;
+    h->stop_at.assign(S, 0);
+    for (int s = 0; s < S; ++s) h->stop_at[s] = info0[s].iterations;
+    int st = run_solve(h, nullptr);
+    if (st < 0) return st;
+    if (st == RDM_NOT_CONVERGED) status = st;
+    if (h->prm.verbose) {
+        const std::vector<double> e = sys_max_norm(h, h->X[h->cur], 1, 1);
+        for (int s = 0; s < S; ++s)
+            fprintf(stderr, "[rdm] correction of P0, system %d: scale 2^%d, largest block of the response %.3e\n", s,
+                    (int)std::lround(std::log2(lam[s])), e[s] / lam[s]);
+    }
+    concat(h, {{&I, 0, 1}, {&Pt, 0, 1}, {&h->X[h->cur], 1, 1}}, A);
+    for (int s = 0; s < S; ++s) cq[s] = 0.5 / lam[s];
+    jt.job[0] = sym_job(0, 1, 0, 2);
+    fp64_class_products(h, A, jt, c1, cq, tc, P0c);
+
+    if (nd) {
+        // P1: H'1_d = U_d + {I, V_d} / 2, U_d = 2 G_d - {P0, G_d}, G_d = {P0, H1_d},
+        // V_d = {D, P1~_d}, D = H0 - {P0, H0}
+        MatSet G, D, U, V, H1p, P1s, W;
+        concat(h, {{&P0c, 0, 1}, {&h->H0, 0, 1}, {&H1s, 0, nd}}, A);
+        jt.njob = nd;
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, -1, 0, 2 + d);
+        fp64_class_products(h, A, jt, c0, c1, tc, G);
+        jt.njob = 1;
+        jt.job[0] = sym_job(0, 1, 0, 1);
+        fp64_class_products(h, A, jt, c1, cm1, tc, D);
+        concat(h, {{&P0c, 0, 1}, {&G, 0, nd}}, A);
+        jt.njob = nd;
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, 1 + d, 0, 1 + d);
+        fp64_class_products(h, A, jt, c2, cm1, tc, U);
+        G.release();
+        concat(h, {{&D, 0, 1}, {&Pt, 1, nd}}, A);
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, -1, 0, 1 + d);
+        fp64_class_products(h, A, jt, c0, c1, tc, V);
+        D.release();
+        concat(h, {{&I, 0, 1}, {&U, 0, nd}, {&V, 0, nd}}, A);
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, 1 + d, 0, 1 + nd + d);
+        fp64_class_products(h, A, jt, c1, ch, tc, H1p);
+        U.release();
+        V.release();
+        lam = scale_to(h, H1p, ref);
+        h->H1 = std::move(H1p);
+        h->nd = nd;
+        for (int d = 0; d < 3; ++d) h->dirs[d] = dirs0[d];
+        st = run_solve(h, nullptr);
+        if (st < 0) return st;
+        if (st == RDM_NOT_CONVERGED) status = st;
+        if (h->prm.verbose) {
+            const std::vector<double> e = sys_max_norm(h, h->X[h->cur], 1, nd);
+            for (int s = 0; s < S; ++s)
+                fprintf(stderr, "[rdm] correction of P1, system %d: scale 2^%d, largest block of the response %.3e\n",
+                        s, (int)std::lround(std::log2(lam[s])), e[s] / lam[s]);
+        }
+        // P1 = projection of P1~ + {I, E} / (2 lam)
+        concat(h, {{&I, 0, 1}, {&Pt, 1, nd}, {&h->X[h->cur], 1, nd}}, A);
+        for (int s = 0; s < S; ++s) cq[s] = 0.5 / lam[s];
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, 1 + d, 0, 1 + nd + d);
+        fp64_class_products(h, A, jt, c1, cq, tc, P1s);
+        concat(h, {{&P0c, 0, 1}, {&P1s, 0, nd}}, A);
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, -1, 0, 1 + d);
+        fp64_class_products(h, A, jt, c0, c1, tc, W);
+        concat(h, {{&P0c, 0, 1}, {&W, 0, nd}}, A);
+        for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, 1 + d, 0, 1 + d);
+        fp64_class_products(h, A, jt, c2, cm1, tc, P1c);
+    }
+    A.release();
+    Pt.release();
+    I.release();
+
+    // the result set (P0, P1_1..nd) with the uploaded H1 back in place
+    h->keep_assembled = false;
+    h->stop_at.clear();
+    if (nd) h->H1 = std::move(H1s);
+    h->nd = nd;
+    for (int d = 0; d < 3; ++d) h->dirs[d] = dirs0[d];
+    h->X[1 - h->cur].release();
+    MatSet &Xf = h->X[h->cur];
+    if (nd) concat(h, {{&P0c, 0, 1}, {&P1c, 0, nd}}, Xf);
+    else concat(h, {{&P0c, 0, 1}}, Xf);
+    P0c.release();
+    P1c.release();
+    compute_alpha(h);
+    h->final_rp.resize((size_t)Xf.nmat * NB + 1);
+    d2h(h->final_rp.data(), Xf.row_ptr.p, h->final_rp.size(), h->stream);
+    sync(h);
+    const std::vector<double> q = stats(h, Xf);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int nq = 3 + nd;
+    h->info = info0;
+    for (int s = 0; s < S; ++s) {
+        rdm_info &R = h->info[s];
+        const double nocc = (double)(h->hs[s].n_elec / 2);
+        R.correction_ms = ms;
+        R.time_ms += ms;
+        R.trace_error = q[(size_t)s * nq] - nocc;
+        R.idempotency = q[(size_t)s * nq] - q[(size_t)s * nq + 1];
+        R.band_energy0 = q[(size_t)s * nq + 2];
+        const int r0 = h->row0[s], r1 = r0 + h->nbs[s];
+        R.nnzb_p0 = h->final_rp[r1] - h->final_rp[r0];
+        for (int d = 0; d < nd; ++d)
+            R.nnzb_p1[h->dirs[d]] = h->final_rp[(size_t)(1 + d) * NB + r1] - h->final_rp[(size_t)(1 + d) * NB + r0];
+    }
+    h->log = log0;
+    h->conv.assign((size_t)S * 4, {});
+    h->solved = true;
+    if (info_out) *info_out = h->info[0];
+    return status;
+}
+
 // split_directions: the field directions one after another, each a solve
 // with that H1 alone from freed work buffers (the X sets then hold P0 and one
 // P1; the X0 recursion is repeated),
@@ -1478,7 +1718,7 @@ int run_solve_dirs(rdm_handle *h, rdm_info *info_out) {
     if (!h->hs.empty())
         for (int d = 0; d < 3; ++d)
             if (h->hs[0].has_h1[d]) all[na++] = d;
-    if (!h->prm.split_directions || na <= 1) return run_solve(h, info_out);
+    if (!h->prm.split_directions || na <= 1) return run_solve_corr(h, info_out);
     const int S = h->S;
     for (int s = 0; s < S; ++s)
         if (h->hs[s].has_s) return fail(h, RDM_EINVAL, "split_directions does not take an overlap matrix");
@@ -1838,11 +2078,11 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
         p->refine_x0 < 0 || p->refine_x0 > 5 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
         p->use_graphs != 0 || p->stall_window < 0 || p->block_size < 0 || p->block_size > 64 ||
         (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1 || p->split_directions < 0 ||
-        p->split_directions > 1)
+        p->split_directions > 1 || p->correct < 0 || p->correct > 1 || (p->correct && p->split_directions))
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
                                    "refine_x1 0..4, refine_x0 0, 1, 3, 4 or 5, chunk_mb >= 0, use_graphs 0, "
-                                   "stall_window >= 0, block_size 0 or a power of two <= 64, autotune and "
-                                   "split_directions 0 or 1)");
+                                   "stall_window >= 0, block_size 0 or a power of two <= 64, autotune, "
+                                   "split_directions and correct 0 or 1, not both of the last two)");
     if (!tc_block_ok(p->mode, p->autotune ? 32 : p->block_size > 0 ? p->block_size : h->b))
         return fail(h, RDM_EINVAL, "the mixed modes run their products on the tensor cores, which take 16 x 16, "
                                    "32 x 32 or 64 x 64 blocks (the uploaded matrices have b = " + std::to_string(h->b) +

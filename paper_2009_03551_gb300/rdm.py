@@ -65,7 +65,7 @@ class rdm_params(C.Structure):
                 ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
                 ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("refine_x0", C.c_int32),
                 ("stall_window", C.c_int32), ("block_size", C.c_int32), ("autotune", C.c_int32),
-                ("split_directions", C.c_int32)]
+                ("split_directions", C.c_int32), ("correct", C.c_int32)]
 
 
 class rdm_info(C.Structure):
@@ -78,7 +78,8 @@ class rdm_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("tc_launches", C.c_int32), ("simt_launches", C.c_int32),
                 ("numeric_bytes", C.c_double), ("device_bytes_peak", C.c_int64),
                 ("product_groups", C.c_int32), ("block_size", C.c_int32), ("autotune_ms", C.c_double),
-                ("probe_ms", C.c_double * 3), ("lowdin_iterations", C.c_int32), ("oz_launches", C.c_int32)]
+                ("probe_ms", C.c_double * 3), ("lowdin_iterations", C.c_int32), ("oz_launches", C.c_int32),
+                ("correction_ms", C.c_double)]
 
 
 class rdm_test_knobs(C.Structure):
