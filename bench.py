@@ -90,6 +90,9 @@ def parse():
                          "FP64 comparison solve runs at this threshold throughout")
     ap.add_argument("--split-directions", type=int, default=0,
                     help="1: solve the field directions one after another (about half the device memory)")
+    ap.add_argument("--correct", type=int, default=0,
+                    help="1: correct P0 and P1 for the residuals of their defining conditions after the solve "
+                         "(two more solves of the same mode)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1 (default): the library picks the block size of the products in {16, 32, 64} by timed "
                          "probe solves during the warm-up; 0: the uploaded 32 x 32 blocks")
@@ -403,7 +406,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
     sol = rdm.Solver(dev.index, stream.cuda_stream)
     params = dict(tau=args.tau, tau_refine=args.tau_refine, tol=1e-9, mode=args.mode, max_iter=100,
                   autotune=args.autotune, block_size=args.block_size, refine_x0=args.refine_x0,
-                  split_directions=args.split_directions)
+                  split_directions=args.split_directions, correct=args.correct)
     tau64 = args.tau_refine if args.tau_refine > 0 else args.tau
     sol.set_params(**params)
     if nsys:
@@ -567,7 +570,7 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
             "config": {"workload": wname, "mode": mode, "systems": len(systems),
                        "atoms": int(sum(s.n_atoms for s in systems)), "N": int(sum(s.n for s in systems)),
                        "b": sys_.b, "tau": args.tau, "tau_refine": tau64, "tol": 1e-9, "directions": 3,
-                       "split_directions": int(args.split_directions),
+                       "split_directions": int(args.split_directions), "correct": int(args.correct),
                        "iterations": int(max([i.iterations for i in sinfo], default=0)),
                        "nnzb_p0": int(sum(i.nnzb_p0 for i in sinfo)),
                        "nnzb_p1": [int(sum(i.nnzb_p1[d] for i in sinfo)) for d in range(3)],
