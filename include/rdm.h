@@ -166,11 +166,14 @@ typedef struct {
                                mode: the error of P0 is the response to H'0 = [[H0, P0], P0], that
                                of P1, with the corrected P0, the response to H'1 = [R1, P0], R1 the
                                residual; the H' are formed by FP64-class block products (double-
-                               FP32 at b = 32, else FP64) with a filter of tau / 1000.  Removes the
+                               FP32 at b = 32, else FP64) with the filter correct_tau.  Removes the
                                rounding error of the reduced-precision tiers (the rotation of the
                                occupied subspace they leave); costs the two response solves and
                                about 3 + 5 nd FP64-class products.  Not with an overlap matrix or
                                split_directions (RDM_EINVAL).  0: off */
+    double  correct_tau;    /* filter of the correction's block products (the residuals are small
+                               differences of O(1) terms, so it must lie well below tau); <= 0:
+                               tau / 100 */
 } rdm_params;
 
 /* Per-solve summary (per system s of a batch: rdm_get_info). */

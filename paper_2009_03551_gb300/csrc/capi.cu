@@ -1549,8 +1549,9 @@ std::vector<double> scale_to(rdm_handle *h, MatSet &m, const std::vector<double>
 // Each response is one more solve of the same mode with the H' in place of
 // H1, scaled per system by a power of two to H1's size so that the solve's
 // filter treats it as it treats H1 (a response is linear in its
-// perturbation).  The residual products are FP64-class with a filter of
-// tau / 1000: the residuals are small differences of O(1) terms.
+// perturbation).  The residual products are FP64-class with a filter well
+// below tau (rdm_params.correct_tau, by default tau / 100): the residuals are
+// small differences of O(1) terms.
 int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
     if (!h->prm.correct) return run_solve(h, info_out);
     for (const auto &y : h->hs)
@@ -1558,9 +1559,18 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
     int status = run_solve(h, nullptr);
     if (status < 0) return status;
     const auto t0 = std::chrono::steady_clock::now();
+    auto tprev = t0;
+    auto phase = [&](const char *what) {   // verbose: wall time of each phase
+        if (!h->prm.verbose) return;
+        sync(h);
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "[rdm] correction: %s %.1f ms\n", what,
+                std::chrono::duration<double, std::milli>(t - tprev).count());
+        tprev = t;
+    };
     const int S = h->S, NB = h->NB, nd = h->nd;
     const int dirs0[3] = {h->dirs[0], h->dirs[1], h->dirs[2]};
-    const double tc = h->prm.tau * 1e-3;
+    const double tc = h->prm.correct_tau > 0 ? h->prm.correct_tau : h->prm.tau * 1e-2;
     const std::vector<rdm_info> info0 = h->info;
     const std::vector<rdm_iter_log> log0 = h->log;
     h->solved = false;
@@ -1591,6 +1601,7 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
     fp64_class_products(h, A, jt, c2, cm1, tc, H0p);
     G0.release();
     std::vector<double> lam = scale_to(h, H0p, ref);
+    phase("perturbation of P0 (2 products)");
     h->H1 = std::move(H0p);
     h->nd = 1;
     h->dirs[0] = 0;
@@ -1606,10 +1617,12 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
             fprintf(stderr, "[rdm] correction of P0, system %d: scale 2^%d, largest block of the response %.3e\n", s,
                     (int)std::lround(std::log2(lam[s])), e[s] / lam[s]);
     }
+    phase("response solve for P0");
     concat(h, {{&I, 0, 1}, {&Pt, 0, 1}, {&h->X[h->cur], 1, 1}}, A);
     for (int s = 0; s < S; ++s) cq[s] = 0.5 / lam[s];
     jt.job[0] = sym_job(0, 1, 0, 2);
     fp64_class_products(h, A, jt, c1, cq, tc, P0c);
+    phase("corrected P0");
 
     if (nd) {
         // P1: H'1_d = U_d + {I, V_d} / 2, U_d = 2 G_d - {P0, G_d}, G_d = {P0, H1_d},
@@ -1637,6 +1650,7 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
         U.release();
         V.release();
         lam = scale_to(h, H1p, ref);
+        phase("perturbations of P1 (1 + 4 nd products)");
         h->H1 = std::move(H1p);
         h->nd = nd;
         for (int d = 0; d < 3; ++d) h->dirs[d] = dirs0[d];
@@ -1649,6 +1663,7 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
                 fprintf(stderr, "[rdm] correction of P1, system %d: scale 2^%d, largest block of the response %.3e\n",
                         s, (int)std::lround(std::log2(lam[s])), e[s] / lam[s]);
         }
+        phase("response solve for P1");
         // P1 = projection of P1~ + {I, E} / (2 lam)
         concat(h, {{&I, 0, 1}, {&Pt, 1, nd}, {&h->X[h->cur], 1, nd}}, A);
         for (int s = 0; s < S; ++s) cq[s] = 0.5 / lam[s];
@@ -1660,6 +1675,7 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
         concat(h, {{&P0c, 0, 1}, {&W, 0, nd}}, A);
         for (int d = 0; d < nd; ++d) jt.job[d] = sym_job(d, 1 + d, 0, 1 + d);
         fp64_class_products(h, A, jt, c2, cm1, tc, P1c);
+        phase("corrected P1 (nd + 2 nd products)");
     }
     A.release();
     Pt.release();
@@ -2078,7 +2094,8 @@ int rdm_set_params(rdm_handle *h, const rdm_params *p) {
         p->refine_x0 < 0 || p->refine_x0 > 5 || p->refine_x0 == RDM_REFINE_SPLIT || p->chunk_mb < 0 ||
         p->use_graphs != 0 || p->stall_window < 0 || p->block_size < 0 || p->block_size > 64 ||
         (p->block_size & (p->block_size - 1)) || p->autotune < 0 || p->autotune > 1 || p->split_directions < 0 ||
-        p->split_directions > 1 || p->correct < 0 || p->correct > 1 || (p->correct && p->split_directions))
+        p->split_directions > 1 || p->correct < 0 || p->correct > 1 || (p->correct && p->split_directions) ||
+        !(p->correct_tau <= 0 || p->correct_tau >= 0))
         return fail(h, RDM_EINVAL, "invalid parameters (tau >= 0, tol >= 0, max_iter >= 1, mode 0..3, "
                                    "refine_x1 0..4, refine_x0 0, 1, 3, 4 or 5, chunk_mb >= 0, use_graphs 0, "
                                    "stall_window >= 0, block_size 0 or a power of two <= 64, autotune, "

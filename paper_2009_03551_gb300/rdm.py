@@ -65,7 +65,8 @@ class rdm_params(C.Structure):
                 ("use_graphs", C.c_int32), ("verbose", C.c_int32), ("refine_x1", C.c_int32),
                 ("symbolic_hash", C.c_int32), ("chunk_mb", C.c_int32), ("refine_x0", C.c_int32),
                 ("stall_window", C.c_int32), ("block_size", C.c_int32), ("autotune", C.c_int32),
-                ("split_directions", C.c_int32), ("correct", C.c_int32)]
+                ("split_directions", C.c_int32), ("correct", C.c_int32),
+                ("correct_tau", C.c_double)]
 
 
 class rdm_info(C.Structure):

@@ -58,8 +58,8 @@ int main(void) {
          offsetof(rdm_info, eps_min), offsetof(rdm_iter_log, nnzb0));
   printf("%zu %zu %zu %zu\n", sizeof(rdm_test_knobs), offsetof(rdm_test_knobs, tc_hold),
          offsetof(rdm_test_knobs, tc_window_cols), offsetof(rdm_test_knobs, tc_block_copies));
-  printf("%zu %zu %zu %zu\n", offsetof(rdm_params, split_directions), offsetof(rdm_params, correct),
-         offsetof(rdm_info, oz_launches), offsetof(rdm_info, correction_ms));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(rdm_params, split_directions), offsetof(rdm_params, correct),
+         offsetof(rdm_info, oz_launches), offsetof(rdm_info, correction_ms), offsetof(rdm_params, correct_tau));
   return 0;
 }
 """
@@ -80,7 +80,8 @@ int main(void) {
                      rdm.rdm_test_knobs.tc_window_cols.offset, rdm.rdm_test_knobs.tc_block_copies.offset]
     tail = [int(x) for x in lines[3].split()]
     assert tail == [rdm.rdm_params.split_directions.offset, rdm.rdm_params.correct.offset,
-                    rdm.rdm_info.oz_launches.offset, rdm.rdm_info.correction_ms.offset]
+                    rdm.rdm_info.oz_launches.offset, rdm.rdm_info.correction_ms.offset,
+                    rdm.rdm_params.correct_tau.offset]
 
 
 def test_default_params_without_gpu(rdm):

@@ -54,7 +54,7 @@ def test_correction_closes_the_bf16_chain_gap(rdm):
     16-bit split products rotate the occupied subspace, and the dipole range
     amplifies that in alpha).  With the correction alpha comes within 1e-9
     of the exact value, closer than the FP64 solve at the same filter (the
-    residuals are formed with a filter a thousand times finer), and so does
+    residuals are formed with a filter a hundred times finer), and so does
     P1 element by element (what remains of its error, 3e-7 here, is the
     filter's truncation of the responses)."""
     s = chain40()
@@ -133,4 +133,19 @@ def test_correction_refuses_an_overlap_matrix(rdm):
     sol.load(s)
     with pytest.raises(rdm.RdmError) as e:
         sol.solve()
+    assert e.value.code == rdm.RDM_EINVAL
+
+
+def test_correction_filter_parameter(rdm):
+    """correct_tau sets the filter of the correction's products: the default
+    (tau / 100) and tau / 1000 agree to far below the target on the chain,
+    and NaN is refused."""
+    s = chain40()
+    _, _, ax = exact(s)
+    a, _, _ = solve(rdm, s, mode="mixed_bf16", correct=1)
+    b, _, _ = solve(rdm, s, mode="mixed_bf16", correct=1, correct_tau=1e-9)
+    assert rel(a.alpha(), ax) <= 1e-9 and rel(b.alpha(), ax) <= 1e-9
+    sol = rdm.Solver(0)
+    with pytest.raises(rdm.RdmError) as e:
+        sol.set_params(mode="mixed_bf16", correct=1, correct_tau=float("nan"))
     assert e.value.code == rdm.RDM_EINVAL
