@@ -1685,6 +1685,7 @@ int run_solve_corr(rdm_handle *h, rdm_info *info_out) {
     h->keep_assembled = false;
     h->stop_at.clear();
     if (nd) h->H1 = std::move(H1s);
+    else h->H1.release();
     h->nd = nd;
     for (int d = 0; d < 3; ++d) h->dirs[d] = dirs0[d];
     h->X[1 - h->cur].release();

@@ -149,3 +149,17 @@ def test_correction_filter_parameter(rdm):
     with pytest.raises(rdm.RdmError) as e:
         sol.set_params(mode="mixed_bf16", correct=1, correct_tau=float("nan"))
     assert e.value.code == rdm.RDM_EINVAL
+
+
+def test_correction_of_p0_alone(rdm):
+    """Without field directions only P0 is corrected (one response solve, to
+    H'0 scaled to H0's size): P0 of the bf16 ladder comes closer to the exact
+    projector, idempotent and with the right trace."""
+    s = make_chain(40, opa=8, b=32, spacing=2.8, cutoff=8.0, seed=21, dirs=())
+    p0x, _, _, _ = exact_response(s.h0.to_dense(), [], s.n_occ)
+    plain, _, _ = solve(rdm, s, mode="mixed_bf16")
+    corr, code, info = solve(rdm, s, mode="mixed_bf16", correct=1)
+    assert code == rdm.RDM_OK and info.correction_ms > 0
+    assert max_rel_err(corr.p0().to_dense(), p0x) < 0.5 * max_rel_err(plain.p0().to_dense(), p0x)
+    assert abs(info.idempotency) < 1e-8 and abs(info.trace_error) < 1e-8
+    assert np.all(np.isnan(corr.alpha()))
