@@ -537,9 +537,9 @@ def run_ours(args, systems, wname, rank, world, torch, dist):
                "MEASURED_PEAKS.json bf16_tflops; fp16 has the same nominal rate)"),
         "fp64": ("k_numeric_simt<32,double> (FP64 block SpGEMM + fused truncation)", f64_ms, kfl[1], 1.26e12,
                  "alu", FP64_PEAK_NOTE + " (derived from unit counts and clock)"),
-        "fp32": ("k_numeric_f32_b32 (FP32 block SpGEMM + fused truncation)", f32_ms, kfl[2], 80.5e12, "alu",
+        "fp32": ("k_numeric_f32_t84 (FP32 block SpGEMM + fused truncation)", f32_ms, kfl[2], 80.5e12, "alu",
                  FP32_PEAK_NOTE + " (derived from unit counts and clock)"),
-        "ff": ("k_numeric_f32_b32<double-FP32> (error-free FP32 block SpGEMM + fused truncation)", ff_ms, kfl[3],
+        "ff": ("k_numeric_ff_b32 (double-FP32 block SpGEMM, error-free transformations, + fused truncation)", ff_ms, kfl[3],
                80.5e12 / 12.0, "alu", FP32_PEAK_NOTE + "; 12 FP32-pipe operations per multiply-add "
                "(2 useful flops) -> 6.7 TFLOP/s (derived from unit counts and clock)"),
         "oz": ("k_tc_oz (tcgen05 exact bf16 slice products, FP64-class, + fused truncation)", oz_ms, kfl[4],

@@ -142,11 +142,12 @@ __global__ void __launch_bounds__(Cfg<B>::NT) k_numeric_simt(NumArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 products of 32 x 32 blocks, tuned: 64 threads per output block, each a
+// Double-FP32 products of 32 x 32 blocks: 64 threads per output block, each a
 // 4 x 4 register tile at rows r0 + 8i and columns c0 + 8j (r0 = t/8,
 // c0 = t%8), so that the 16-byte shared-memory reads of a quarter warp hit 8
 // different banks (B rows) or broadcast (A rows).  Operand blocks come from
-// the FP32 copy of the master values, double-buffered with cp.async.
+// the FP32 (hi, lo) copies of the master values, double-buffered with
+// cp.async.
 // ---------------------------------------------------------------------------
 constexpr int kF32Ld = 36;   // padded row stride in floats (144 B, 16-byte aligned)
 
@@ -159,21 +160,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// FF = false: FP32 products.  FF = true: double-FP32 ("float-float")
-// products of the FP64 masters split as x = hi + lo (two FP32 planes): the
+// Double-FP32 ("float-float") products of the FP64 masters split as
+// x = hi + lo (two FP32 planes): the
 // hi*hi products are accumulated without rounding loss by the error-free
 // transformations of Ogita, Rump and Oishi (2005) -- the exact product
 // p + e = hi_a hi_b from one multiply and one fused multiply-add, the exact
 // sum s + t = acc + p from six additions -- and the small cross terms hi*lo
 // and lo*hi are added in plain FP32 into the low word.  The result carries
 // about 46 bits, enough for FP64-class refinement of X0^2, on the FP32 pipe.
-template <bool FF>
-__global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
-    constexpr int NP = FF ? 2 : 1;                 // operand planes (hi, lo)
+__global__ void __launch_bounds__(64) k_numeric_ff_b32(NumArgs a) {
+    constexpr int NP = 2;                          // operand planes (hi, lo)
     __shared__ __align__(16) float sA[2][NP][32 * kF32Ld];
     __shared__ __align__(16) float sB[2][NP][32 * kF32Ld];
-    using CT = typename std::conditional<FF, double, float>::type;
-    __shared__ CT sC[32 * 33];
+    __shared__ double sC[32 * 33];
     __shared__ float red[2];
     const int tid = threadIdx.x;
     const int r0 = tid >> 3, c0 = tid & 7;
@@ -231,27 +230,14 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
             const float *B_ = sB[buf][0];
             // the double-FP32 body is large: not unrolled over kk, so that the
             // loop stays in the instruction cache
-            constexpr int kUnrollKK = FF ? 1 : 8;
-#pragma unroll kUnrollKK
+#pragma unroll 1
             for (int kk = 0; kk < 32; kk += 4) {
                 float4 av[4], bv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const float4 *>(&A_[(r0 + 8 * u) * kF32Ld + kk]);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) bv[v] = *reinterpret_cast<const float4 *>(&B_[(c0 + 8 * v) * kF32Ld + kk]);
-                if (!FF) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            float t = acc[u][v];
-                            t = fmaf(av[u].x, bv[v].x, t);
-                            t = fmaf(av[u].y, bv[v].y, t);
-                            t = fmaf(av[u].z, bv[v].z, t);
-                            t = fmaf(av[u].w, bv[v].w, t);
-                            acc[u][v] = t;
-                        }
-                } else {
+                {
                     const float *Al = sA[buf][NP - 1];
                     const float *Bl = sB[buf][NP - 1];
                     float4 al[4], bl[4];
@@ -290,8 +276,8 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
             __syncthreads();
         }
 
-        // epilogue: C = c_lin X + c_sq acc (FP64 for FF), symmetrised on the diagonal,
-        // norm, truncation
+        // epilogue: C = c_lin X + c_sq acc in FP64, symmetrised on the
+        // diagonal, norm, truncation
         const double *gx = sx >= 0 ? a.in_val + (size_t)sx * 1024 : nullptr;
         const bool diag = (st == s);
         const double cl = a.c_lin[sys], cq = a.c_sq[sys];
@@ -300,26 +286,20 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int r = r0 + 8 * u, c = c0 + 8 * v;
-                if (FF) {
-                    double x = cq * ((double)acc[u][v] + (double)accl[u][v]);
-                    if (gx) x = fma(cl, gx[r * 32 + c], x);
-                    sC[r * 33 + c] = (CT)x;
-                } else {
-                    float x = (float)cq * acc[u][v];
-                    if (gx) x = fmaf((float)cl, (float)gx[r * 32 + c], x);
-                    sC[r * 33 + c] = (CT)x;
-                }
+                double x = cq * ((double)acc[u][v] + (double)accl[u][v]);
+                if (gx) x = fma(cl, gx[r * 32 + c], x);
+                sC[r * 33 + c] = x;
             }
         __syncthreads();
         float ss = 0.f;
         if (diag) {
-            CT sym[4][4];
+            double sym[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const int r = r0 + 8 * u, c = c0 + 8 * v;
-                    sym[u][v] = (CT)0.5 * (sC[r * 33 + c] + sC[c * 33 + r]);
+                    sym[u][v] = 0.5 * (sC[r * 33 + c] + sC[c * 33 + r]);
                 }
             __syncthreads();
 #pragma unroll
@@ -335,6 +315,149 @@ __global__ void __launch_bounds__(64) k_numeric_f32_b32(NumArgs a) {
                 const float x = (float)sC[(r0 + 8 * u) * 33 + c0 + 8 * v];
                 ss = fmaf(x, x, ss);
             }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if ((tid & 31) == 0) red[tid >> 5] = ss;
+        __syncthreads();
+        const float nrm = sqrtf(red[0] + red[1]) * (1.0f + 1e-6f);
+        const bool keep = ((double)nrm >= tau) && (nrm > 0.f);
+        double *o = a.out_val + (size_t)(a.uidx[s] - a.u0) * 1024;
+        for (int e = tid; e < 1024; e += 64) o[e] = (double)sC[(e >> 5) * 33 + (e & 31)];
+        if (tid == 0) {
+            a.out_nrm[s] = nrm;
+            a.keep[s] = keep;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 products of 32 x 32 blocks with 8 x 4 register tiles.  A 4 x 4 tile
+// (the layout of k_numeric_ff_b32) reads 2 bytes of shared memory per FMA, and a warp's 16-byte read takes four
+// shared-memory cycles whatever it broadcasts, so the operand reads allow
+// about half of the SM's FMA rate (ncu on the 4 x 4 version: FMA pipe 54%,
+// short-scoreboard stalls first).  Here half-warp h of the CTA's four covers
+// the k-half kh = h % 2 (k = 16 kh .. 16 kh + 15 of every pair) and the
+// column half ch = h / 2, lane l of it rows r0 + 4u (u = 0..7) and columns
+// 16 ch + c0 + 4v (v = 0..3), r0 = l / 4, c0 = l % 4: 12 reads of 16 bytes per
+// 128 FMAs (1.5 bytes per FMA) within 128 registers, so that eight CTAs
+// share an SM (44.5 against 41.6 TFLOP/s for the 4 x 4 version; an 8 x 8
+// tile at 222 registers, four CTAs per SM, gained nothing).  A quarter warp reads two A rows (broadcast) and four B rows,
+// in distinct banks.  The two k-halves are added in a fixed order at the end.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(64, 8) k_numeric_f32_t84(NumArgs a) {
+    __shared__ __align__(16) float sA[2][32 * kF32Ld];
+    __shared__ __align__(16) float sB[2][32 * kF32Ld];
+    __shared__ float sC[32 * 33];
+    __shared__ float red[2];
+    __shared__ int s_w;
+    const int tid = threadIdx.x;
+    const int hw = tid >> 4, l = tid & 15;
+    const int kh = hw & 1, ch = hw >> 1;
+    const int r0 = l >> 2, c0 = 16 * ch + (l & 3);
+    const int k0 = 16 * kh;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = atomicAdd(a.work_next, 1);
+        __syncthreads();
+        const int w = s_w;
+        __syncthreads();
+        if (w >= a.nwork) break;
+        const int s = a.work[w];
+        const int i = a.slot_row[s];
+        const int sys = a.sys_of_row[i];
+        const int job = a.slot_job[s];
+        const double tau = a.job_tau_sel[job] ? a.tau1[sys] : a.tau0[sys];
+        const int64_t p0 = a.pair_off[s], p1 = a.pair_off[s + 1];
+        const int st = a.slot_t[s], sx = a.slot_x[s];
+
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+
+        auto issue = [&](int64_t q, int buf) {
+            const float *ga = a.in_f32 + (size_t)a.pair_a[q] * 1024;
+            const float *gb = a.in_f32 + (size_t)a.pair_b[q] * 1024;
+#pragma unroll
+            for (int c = tid; c < 256; c += 64) {
+                const int row = c >> 3, col4 = (c & 7) * 4;
+                cp_async16(&sA[buf][row * kF32Ld + col4], ga + row * 32 + col4);
+                cp_async16(&sB[buf][row * kF32Ld + col4], gb + row * 32 + col4);
+            }
+            cp_async_commit();
+        };
+        __syncthreads();
+        if (p0 < p1) issue(p0, 0);
+        for (int64_t q = p0; q < p1; ++q) {
+            const int buf = (int)((q - p0) & 1);
+            if (q + 1 < p1) {
+                issue(q + 1, buf ^ 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncthreads();
+            const float *A_ = sA[buf];
+            const float *B_ = sB[buf];
+#pragma unroll
+            for (int kk = 0; kk < 16; kk += 4) {
+                float4 av[8], bv[4];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    av[u] = *reinterpret_cast<const float4 *>(&A_[(r0 + 4 * u) * kF32Ld + k0 + kk]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    bv[v] = *reinterpret_cast<const float4 *>(&B_[(c0 + 4 * v) * kF32Ld + k0 + kk]);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float t = acc[u][v];
+                        t = fmaf(av[u].x, bv[v].x, t);
+                        t = fmaf(av[u].y, bv[v].y, t);
+                        t = fmaf(av[u].z, bv[v].z, t);
+                        t = fmaf(av[u].w, bv[v].w, t);
+                        acc[u][v] = t;
+                    }
+            }
+            __syncthreads();
+        }
+
+        // the two k-halves' partial blocks into the free operand buffers, then
+        // C = c_lin X + c_sq (P_0 + P_1)
+        float *part = sA[kh];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part[(r0 + 4 * u) * kF32Ld + c0 + 4 * v] = acc[u][v];
+        __syncthreads();
+        const double *gx = sx >= 0 ? a.in_val + (size_t)sx * 1024 : nullptr;
+        const bool diag = (st == s);
+        const float cl = (float)a.c_lin[sys], cq = (float)a.c_sq[sys];
+        for (int e = tid; e < 1024; e += 64) {
+            const int r = e >> 5, c = e & 31, o = r * kF32Ld + c;
+            float x = cq * (sA[0][o] + sA[1][o]);
+            if (gx) x = fmaf(cl, (float)gx[e], x);
+            sC[r * 33 + c] = x;
+        }
+        __syncthreads();
+        float sym[16];
+        if (diag) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int e = tid + 64 * t, r = e >> 5, c = e & 31;
+                sym[t] = 0.5f * (sC[r * 33 + c] + sC[c * 33 + r]);
+            }
+        }
+        __syncthreads();
+        float ss = 0.f;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 64 * t, r = e >> 5, c = e & 31;
+            if (diag) sC[r * 33 + c] = sym[t];
+            const float x = diag ? sym[t] : sC[r * 33 + c];
+            ss = fmaf(x, x, ss);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if ((tid & 31) == 0) red[tid >> 5] = ss;
@@ -412,14 +535,14 @@ void launch_numeric_simt(const NumArgs &a, Arith ar, cudaStream_t st) {
     if (a.nwork == 0) return;
     if (ar == AR_FF) {
         if (a.b != 32 || !a.in_f32 || !a.in_f32lo) throw Error{-1, "double-FP32 products need 32 x 32 blocks"};
-        static const int res = resident_blocks(k_numeric_f32_b32<true>, 64);
-        k_numeric_f32_b32<true><<<std::min(a.nwork, res), 64, 0, st>>>(a);
+        static const int res = resident_blocks(k_numeric_ff_b32, 64);
+        k_numeric_ff_b32<<<std::min(a.nwork, res), 64, 0, st>>>(a);
         RDM_LAUNCH_CHECK();
     } else if (ar == AR_FP64) {
         dispatch<double>(a, st);
     } else if (a.b == 32 && a.in_f32) {
-        static const int res = resident_blocks(k_numeric_f32_b32<false>, 64);
-        k_numeric_f32_b32<false><<<std::min(a.nwork, res), 64, 0, st>>>(a);
+        static const int res = resident_blocks(k_numeric_f32_t84, 64);
+        k_numeric_f32_t84<<<std::min(a.nwork, res), 64, 0, st>>>(a);
         RDM_LAUNCH_CHECK();
     } else {
         dispatch<float>(a, st);
