@@ -163,3 +163,29 @@ def test_correction_of_p0_alone(rdm):
     assert max_rel_err(corr.p0().to_dense(), p0x) < 0.5 * max_rel_err(plain.p0().to_dense(), p0x)
     assert abs(info.idempotency) < 1e-8 and abs(info.trace_error) < 1e-8
     assert np.all(np.isnan(corr.alpha()))
+
+
+def test_correction_after_an_unconverged_solve(rdm):
+    """A solve stopped by max_iter stays NOT_CONVERGED with the correction;
+    its response solves take the same number of updates, and the corrected
+    results are readable and finite."""
+    s = chain40()
+    sol = rdm.Solver(0)
+    sol.set_params(tau=1e-6, tol=1e-9, max_iter=6, mode="mixed_bf16", correct=1)
+    sol.load(s)
+    code, info = sol.solve()
+    assert code == rdm.RDM_NOT_CONVERGED and info.iterations == 6 and info.correction_ms > 0
+    assert np.all(np.isfinite(sol.alpha())) and np.all(np.isfinite(sol.p0().vals))
+
+
+def test_correction_with_the_autotuner(rdm):
+    """Every probe solve of the autotuner includes the correction; the kept
+    block size then gives the corrected alpha within 1e-8 of the exact (the
+    filter acts on the blocks the products run at, so another block size
+    moves the corrected alpha at the 1e-9 level: 1.1e-9 measured)."""
+    s = make_cluster(40, opa=8, b=32, cutoff=10.0, seed=12, dirs=("x", "y"))
+    _, _, ax = exact(s)
+    sol, code, info = solve(rdm, s, mode="mixed_fp16", correct=1, autotune=1)
+    assert code == rdm.RDM_OK and all(p > 0 for p in info.probe_ms[:2])
+    assert info.correction_ms > 0
+    assert rel(sol.alpha()[:2, :2], ax[:2, :2]) <= 1e-8
